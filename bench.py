@@ -1,0 +1,351 @@
+"""Benchmark: kernel columns per second of phi(L) E_W on one GB300 (or N replicas).
+
+Workload (default): random geometric graph, n = 1,000,000 nodes in the unit square,
+radius for mean degree 10, unweighted standard Laplacian (int32 CSR, FP32 values);
+M = 64 seeded nodes; diffusion kernel e^{-tL} with t in {0.5, 2.0}; all five block
+Krylov methods (cbl, gbl, sbl, cheb, cheb2) with m = 30 products each.  One step = those
+10 solves (640 kernel columns).  The graph and the output buffers are resident in HBM
+before timing; each solve takes its scratch from the stream-ordered pool inside the
+timed region.  Between steps a 256 MiB buffer is written to flush the 129 MB L2 (the
+per-solve working set, 2-8 GB, is also far above L2).
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload
+(the 10 solves with the first 4 of the 64 nodes), on the host cores.
+
+Under torchrun each rank is an independent replica (its own node seed); no collective
+is used on the data path ("replicas only", weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METHODS = ["cbl", "gbl", "sbl", "cheb", "cheb2"]
+METRIC = "kernel columns/sec at 1e-6 rel err vs FP64 oracle"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kb", choices=["kb", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--M", type=int, default=64)
+    ap.add_argument("--m", type=int, default=30)
+    ap.add_argument("--ts", default="0.5,2.0")
+    ap.add_argument("--methods", default=",".join(METHODS))
+    ap.add_argument("--graph-seed", type=int, default=1)
+    ap.add_argument("--node-seed", type=int, default=2)
+    ap.add_argument("--basis", default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="steps of the plain FP64 GPU mode timed for comparison (0 = skip)")
+    ap.add_argument("--ref-sample-cols", type=int, default=4)
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"rgg n={a.n} mean_degree=10 M={a.M} m={a.m} exp t={a.ts} "
+                        f"methods={a.methods}",
+            "graph": "random geometric graph, unit square, cell-sorted node order",
+            "n": a.n, "mean_degree": 10, "M": a.M, "m": a.m,
+            "t": [float(x) for x in a.ts.split(",")], "methods": a.methods.split(","),
+            "graph_seed": a.graph_seed, "node_seed": a.node_seed, "basis": a.basis,
+            "l2": "256 MiB flush write between steps; per-solve working set > L2"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        pass
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes from the committed ncu summary (kernel -> bytes), if any."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    out = {}
+    if os.path.exists(p):
+        for line in open(p):
+            line = line.strip()
+            if line and not line.startswith("#"):
+                parts = line.split()
+                if len(parts) >= 2:
+                    try:
+                        out[parts[0]] = float(parts[1])
+                    except ValueError:
+                        pass
+    return out
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    import synth
+    from oracle import krylov
+    ts = [float(x) for x in a.ts.split(",")]
+    methods = a.methods.split(",")
+    g = synth.random_geometric_graph(a.n, 10, seed=a.graph_seed)
+    nodes = synth.sample_nodes(a.n, a.M, seed=a.node_seed)[: a.ref_sample_cols]
+    L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
+
+    def step():
+        for mth in methods:
+            for t in ts:
+                krylov.apply(mth, L, nodes, a.m, "exp", t=t)
+
+    for _ in range(a.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        step()
+    dt = (time.perf_counter() - t0) / a.steps
+    cols = len(methods) * len(ts) * len(nodes)
+    val = cols / dt
+    sample = (f"{len(methods)}x{len(ts)} solves with the first {len(nodes)} of the {a.M} nodes "
+              f"(m={a.m}) on the full graph, numpy/scipy FP64")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "kernel_columns/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(a),
+        "cpu_baseline": {"value": val, "unit": "kernel_columns/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "kernel_columns/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def cpu_baseline(a, budget_s=25.0):
+    """The oracle as it stands on a bounded sample: the step's solves with 4 columns."""
+    import synth
+    from oracle import krylov
+    ts = [float(x) for x in a.ts.split(",")]
+    methods = a.methods.split(",")
+    g = synth.random_geometric_graph(a.n, 10, seed=a.graph_seed)
+    nodes = synth.sample_nodes(a.n, a.M, seed=a.node_seed)[: a.ref_sample_cols]
+    L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
+    t0 = time.perf_counter()
+    cols = 0
+    for mth in methods:
+        for t in ts:
+            krylov.apply(mth, L, nodes, a.m, "exp", t=t)
+            cols += len(nodes)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": cols / dt, "unit": "kernel_columns/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{cols // len(nodes)} solves (methods {methods}, t {ts}) with the first "
+                      f"{len(nodes)} of {a.M} nodes, m={a.m}, full graph, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_2301_06384_gb300 import kb
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.cuda.current_device()
+    ts = [float(x) for x in a.ts.split(",")]
+    methods = a.methods.split(",")
+    g = synth.random_geometric_graph(a.n, 10, seed=a.graph_seed)
+    nodes = synth.sample_nodes(a.n, a.M, seed=a.node_seed + rank)
+    stream = torch.cuda.current_stream()
+    G = kb.Graph.from_csr(g, stream=stream)
+    solves = [(mth, t) for mth in methods for t in ts]
+    Ys = [torch.empty((a.n, a.M), dtype=torch.float32, device="cuda") for _ in solves]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    params = {t: kb.make_params(t=t, basis=a.basis) for t in ts}
+
+    def step(pr=params):
+        for (mth, t), Y in zip(solves, Ys):
+            kb.kb_krylov_apply(G, mth, "exp", pr[t], nodes, a.M, a.m, Y, stream=stream)
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = kb.kb_launch_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(dev).__enter__()
+    kb.kb_profile_enable(True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        flush.zero_()
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kb.kb_profile_enable(False)
+    clocks = sampler.stop()
+    launches = (kb.kb_launch_counter() - l0) // max(a.steps, 1)
+    stats = kb.kb_profile_read()
+    ms = e0.elapsed_time(e1) / a.steps
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    cols_per_step = len(solves) * a.M
+    value = world * cols_per_step / (ms / 1e3)
+
+    # roofline of the dominant kernel class and of the SpMM
+    peak, peak_kind = measured_peaks()
+    traffic = ncu_traffic()
+
+    def roof(name):
+        s = stats.get(name)
+        if not s or s["total_ms"] <= 0:
+            return None
+        gbs = s["alg_bytes"] / (s["total_ms"] / 1e3) / 1e9
+        tr = traffic.get(name)
+        return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs / peak, 4), "traffic": tr,
+                "kernel": name, "launches_per_step": s["launches"] / a.steps,
+                "avg_launch_ms": s["total_ms"] / max(s["launches"], 1),
+                "share_of_step": round(s["total_ms"] / a.steps / ms, 4),
+                "peak_kind": f"{peak_kind} hbm_gbs"}
+
+    dom = max(stats.items(), key=lambda kv: kv[1]["total_ms"])[0] if stats else None
+    shares = {k: round(v["total_ms"] / a.steps / ms, 4) for k, v in stats.items() if v["launches"]}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not a.no_e2e:
+        Yh = [torch.empty((a.n, a.M), dtype=torch.float32).pin_memory() for _ in solves]
+        def step_host():
+            for (mth, t), Y in zip(solves, Yh):
+                kb.kb_krylov_apply_host(G, mth, "exp", params[t], nodes, a.M, a.m, Y, stream=stream)
+        step_host()
+        torch.cuda.synchronize()
+        ksteps = max(1, min(a.steps, 2))
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            step_host()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / ksteps
+        e2e = {"value": world * cols_per_step / dt, "unit": "kernel_columns/s",
+               "h2d_bytes_per_step": len(solves) * a.M * 4,
+               "d2h_bytes_per_step": len(solves) * a.n * a.M * 4}
+
+    # plain FP64 GPU mode (the comparator of the mixed-precision form), same solves
+    fp64 = None
+    if a.fp64_steps > 0 and a.basis == "f32":
+        p64 = {t: kb.make_params(t=t, basis="f64") for t in ts}
+        try:
+            step(p64)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(a.fp64_steps):
+                flush.zero_()
+                step(p64)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            fms = f0.elapsed_time(f1) / a.fp64_steps
+            fp64 = {"value": cols_per_step / (fms / 1e3), "unit": "kernel_columns/s",
+                    "ms_per_step": fms, "speedup_of_fp32_path": round(fms / ms, 3)}
+        except kb.KbError as exc:
+            fp64 = {"unavailable": str(exc)}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": "kernel_columns/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if a.basis == "f32" else a.basis, "data": "synthetic",
+            "config": workload_config(a),
+            "clocks": clocks, "gpu_launches": int(launches),
+            "roofline": roof(dom) if dom else None,
+            "spmm_roofline": roof("spmm"),
+            "kernel_shares": shares,
+            "e2e": e2e, "fp64_plain": fp64,
+        }
+        if world == 1 and not a.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(a)
+        print(json.dumps(out))
+    G.destroy()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * kb.h -- block Krylov kernel columns phi(L) E_W on one GPU (sm_103a).
+ *
+ * The library computes approximations of the N kernel columns
+ *     Y ~ phi(L) E_W,   E_W = [e_{w_1}, ..., e_{w_N}]                 (Section 3, Eq. (GBFcompute))
+ * of a graph Laplacian L (Section 2.1, Eq. (generalizedLaplacian): symmetric, negative
+ * off-diagonal entries on edges, spectrum in [0, Lambda]) for the diffusion kernel
+ * phi(lambda) = e^{-t lambda} and the variational spline kernel (eps + lambda)^{-s}
+ * (Section 2.4), with the five block Krylov methods of Section 3:
+ *     KB_CBL   classical block Lanczos               (Algorithm 1)
+ *     KB_GBL   global block Lanczos                  (Algorithm 2)
+ *     KB_SBL   sequential (column-wise) Lanczos      (Section 3.3)
+ *     KB_CHEB  Chebyshev-Lobatto interpolation       (Section 3.4, Eqs. (apprchebyshevseries), (chebcoeff))
+ *     KB_CHEB2 squared Chebyshev, PSD by construction (Section 3.4.1)
+ *
+ * Conventions for every entry point
+ *   - The return value is KB_OK (0) on success or a negative KB_ERR_* code.  No C++
+ *     exception crosses this boundary.  kb_last_error() gives a thread-local message for
+ *     the last failing call on the calling thread.
+ *   - Device pointers are plain CUDA device addresses of the current device; host
+ *     pointers are ordinary host memory.  `stream` is a cudaStream_t passed as void*
+ *     (NULL = the legacy default stream).
+ *   - All GPU work of a call is enqueued on `stream`.  A call returns without waiting for
+ *     the GPU unless it is documented to synchronise.
+ *   - The library never frees memory it does not own and never keeps a caller pointer
+ *     beyond the call.
+ */
+#ifndef KB_H
+#define KB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+enum {
+    KB_OK = 0,
+    KB_ERR_ARG = -1,          /* invalid argument (null pointer, size out of range, bad enum)   */
+    KB_ERR_CSR = -2,          /* CSR not a valid generalized Laplacian (unsorted, duplicate,
+                                 out-of-range column, non-symmetric, positive off-diagonal)   */
+    KB_ERR_NODES = -3,        /* node set has an out-of-range or repeated node                  */
+    KB_ERR_CUDA = -4,         /* a CUDA runtime call failed (message in kb_last_error)          */
+    KB_ERR_NOMEM = -5,        /* device memory exhausted                                         */
+    KB_ERR_BREAKDOWN = -6,    /* a Lanczos block became rank deficient (reading A6)              */
+    KB_ERR_UNSUPPORTED = -7   /* combination not implemented (see kb_krylov_apply)               */
+};
+
+/* ------------------------------------------------------------------ enums and params */
+typedef enum { KB_CBL = 0, KB_GBL = 1, KB_SBL = 2, KB_CHEB = 3, KB_CHEB2 = 4 } kb_method;
+typedef enum { KB_PHI_EXP = 0, KB_PHI_SPLINE = 1 } kb_phi;          /* e^{-t L}, (eps I + L)^{-s} */
+typedef enum { KB_F32 = 0, KB_BF16 = 1, KB_F64 = 2 } kb_dtype;     /* Krylov basis storage        */
+
+typedef struct {
+    double t;           /* diffusion time t (KB_PHI_EXP), any finite value                         */
+    double eps;         /* spline shift eps > 0 (KB_PHI_SPLINE)                                    */
+    double s;           /* spline exponent s > 0 (KB_PHI_SPLINE)                                   */
+    double lambda_max;  /* spectral bound Lambda used by KB_CHEB/KB_CHEB2; <= 0 selects the
+                           graph's Gershgorin bound max_i sum_j |L_ij| (reading A5)               */
+    int32_t reorth;     /* KB_CBL only: 1 = full reorthogonalisation of each new block against
+                           all earlier blocks, classical Gram-Schmidt applied twice (not in the
+                           paper; needed in finite precision for long runs); 0 = none           */
+    int32_t basis;      /* kb_dtype of the stored Krylov blocks: KB_F32 (FP32 arithmetic),
+                           KB_F64 (plain FP64 arithmetic throughout)                              */
+} kb_params;
+
+typedef struct {
+    int32_t status;          /* KB_OK or KB_ERR_BREAKDOWN                                          */
+    int32_t steps_done;      /* products with L whose blocks enter the result (<= m); smaller
+                                than m when the Krylov space became invariant (exact result)     */
+    int32_t breakdown_step;  /* step of a rank-deficient block, or -1                             */
+    int32_t spmm_launches;   /* SpMM kernels launched by the call                                  */
+    double  lambda_used;     /* Lambda used for the Chebyshev methods (0 for Lanczos)              */
+} kb_info;
+
+typedef struct kb_graph kb_graph;   /* opaque; owned by the library */
+
+/* ------------------------------------------------------------------ graph */
+/*
+ * kb_graph_create -- copy a graph Laplacian to the device.          (Section 2.1, Eq. (generalizedLaplacian))
+ *
+ *   n       number of nodes, 1 <= n < 2^31.
+ *   rowptr  host, n+1 int32, rowptr[0] = 0, non-decreasing; row i holds entries
+ *           rowptr[i] .. rowptr[i+1]-1 of col/val.
+ *   col     host, int32 column indices, strictly increasing within a row, in [0, n).
+ *   val     host, float32 values L_ij; off-diagonal entries must be < 0 (edge weight
+ *           w_ij = -L_ij), and the matrix must be symmetric (bitwise L_ij == L_ji).  The
+ *           diagonal entry may be absent (taken as 0).  NULL means the unit-weight standard
+ *           Laplacian D - A of the pattern (diagonal entries of the pattern are ignored).
+ *   flags   0, or KB_GRAPH_SKIP_SYMMETRY_CHECK to skip the O(nnz log deg) symmetry check.
+ *   stream  stream for the upload and the Lambda reduction; the call synchronises it.
+ *   out     receives the handle.
+ *
+ * The library copies the CSR (the caller keeps ownership of its arrays), stores the
+ * off-diagonal part (weights dropped when all are 1) and the diagonal excess
+ * L_ii - sum_j w_ij, and computes the Gershgorin bound Lambda = max_i sum_j |L_ij| on the
+ * device.  Errors: KB_ERR_ARG, KB_ERR_CSR (validation runs on the host before any CUDA
+ * call), KB_ERR_NOMEM, KB_ERR_CUDA.  On error *out is set to NULL.
+ */
+#define KB_GRAPH_SKIP_SYMMETRY_CHECK 1
+int kb_graph_create(int64_t n, const int32_t *rowptr, const int32_t *col, const float *val,
+                    int32_t flags, void *stream, kb_graph **out);
+
+/* Release the device copy.  NULL is ignored.  No call using the graph may be in flight. */
+void kb_graph_destroy(kb_graph *g);
+
+/* Graph facts: node count, stored off-diagonal entries, Gershgorin Lambda, whether all
+ * weights are 1 and the diagonal equals the degree (standard Laplacian).  Any output
+ * pointer may be NULL. */
+int kb_graph_info(const kb_graph *g, int64_t *n, int64_t *nnz_offdiag, double *lambda_max,
+                  int32_t *standard_unit);
+
+/* ------------------------------------------------------------------ kernel columns */
+/*
+ * kb_krylov_apply -- Y ~ phi(L) E_W by one block Krylov method.   (Section 3; Algorithms 1, 2)
+ *
+ *   method  kb_method.  phi: kb_phi with parameters in *params.
+ *   nodes   host, M distinct node indices in [0, n) (0-based; reading A11).
+ *   M       block width N of the paper, 1 <= M <= 128 for KB_CBL and KB_GBL; any M >= 1
+ *           for KB_SBL, KB_CHEB, KB_CHEB2 (columns are independent and processed in
+ *           groups of at most 128).
+ *   m       number of products with L (block SpMMs), m >= 1 (KB_CHEB2: m >= 2).  The
+ *           Lanczos methods return the degree m-1 polynomial p_{phi,m-1} (Algorithm 1,
+ *           line 9); KB_CHEB returns the degree-m interpolant; KB_CHEB2 the square of the
+ *           degree floor(m/2) interpolant of sqrt(phi).
+ *   Y       device, n x M float32, row-major with leading dimension M (Y[i*M + j] is
+ *           entry (node i, column j)); written completely; caller-owned.
+ *   stream  all work is enqueued here; scratch memory is taken from and returned to the
+ *           device's stream-ordered memory pool on this stream.
+ *   info    NULL, or receives facts about the run.  When non-NULL the call synchronises
+ *           `stream` and returns KB_ERR_BREAKDOWN if the Lanczos process met a
+ *           rank-deficient block (then Y is filled with NaN).  With info == NULL the call
+ *           does not synchronise, and a breakdown shows only as NaN in Y.
+ *
+ * Not implemented (KB_ERR_UNSUPPORTED): KB_CBL with KB_PHI_SPLINE and non-integer s;
+ * params->basis other than KB_F32 / KB_F64; reorth with methods other than KB_CBL.
+ * Other errors: KB_ERR_ARG, KB_ERR_NODES, KB_ERR_NOMEM, KB_ERR_CUDA.
+ */
+int kb_krylov_apply(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
+                    const int32_t *nodes, int32_t M, int32_t m, float *Y, void *stream,
+                    kb_info *info);
+
+/*
+ * kb_krylov_apply_host -- the same computation with the result in HOST memory.
+ *
+ * Y_host is host memory of n x M float32 (row-major, leading dimension M); pinned memory
+ * (cudaHostAlloc / cudaHostRegister) gives an asynchronous DMA, pageable memory works but
+ * is staged by the CUDA runtime.  The call allocates the device result from the
+ * stream-ordered pool, runs kb_krylov_apply, copies the result to Y_host and synchronises
+ * `stream` before returning.  Errors as kb_krylov_apply.
+ */
+int kb_krylov_apply_host(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
+                         const int32_t *nodes, int32_t M, int32_t m, float *Y_host,
+                         void *stream, kb_info *info);
+
+/* ------------------------------------------------------------------ diagnostics */
+/* Static text for a status code. */
+const char *kb_status_string(int status);
+/* Message of the last failing call on this thread ("" if none). */
+const char *kb_last_error(void);
+/* Library version, major*10000 + minor*100 + patch. */
+int kb_version(void);
+
+/* ------------------------------------------------------------------ host coefficient math
+ * These run on the host only (no CUDA call) and expose the scalar preprocessing of the
+ * Chebyshev steps so that it can be checked without a GPU. */
+
+/* Coefficients c_0..c_m of the degree-m Chebyshev-Lobatto interpolant of phi (or of
+ * sqrt(phi) when sqrt_phi != 0) on [0, lam], Eq. (chebcoeff) read as
+ * c_k = (2/m) sum''_{j=0..m} phi(lam/2 (1 - cos(pi j/m))) cos(pi j k/m) (endpoint terms
+ * halved, reading A3); the interpolant is sum''_k c_k T_k(1 - 2 lambda/lam) with c_0 and
+ * c_m halved.  c: host array of m+1 doubles.  Errors: KB_ERR_ARG. */
+int kb_cheb_lobatto_coeffs(kb_phi phi, const kb_params *params, int32_t m, double lam,
+                           int32_t sqrt_phi, double *c);
+
+/* Chebyshev series e^{-t lambda} = sum_k d_k T_k(1 - 2 lambda/lam) on [0, lam] (no
+ * halving), truncated where |d_k| <= tol * sum |d|; used for phi(H_m) of the Lanczos
+ * methods.  d: host array of cap doubles; *count receives the number of terms (the call
+ * fails with KB_ERR_ARG when it exceeds cap). */
+int kb_exp_series_coeffs(double t, double lam, double tol, double *d, int32_t cap,
+                         int32_t *count);
+
+/* ------------------------------------------------------------------ measurement aids
+ * Optional CUDA-event timing of every kernel launch class (not part of the method).
+ * While enabled, each launch of a class is bracketed by events on its stream; reading
+ * synchronises those events, returns per-class totals and clears the record. */
+typedef struct {
+    int32_t kernel_class;   /* 0 spmm, 1 rowblock, 2 reduce, 3 small_fp64, 4 projected_fp64,
+                               5 assemble, 6 other                                           */
+    int32_t launches;
+    double total_ms;        /* summed event durations                                         */
+    double alg_bytes;       /* algorithmic HBM bytes of those launches                        */
+    double alg_flops;       /* algorithmic flops of those launches                            */
+} kb_kernel_stats;
+int kb_profile_enable(int32_t on);
+int kb_profile_read(kb_kernel_stats *out, int32_t cap, int32_t *count);
+const char *kb_kernel_class_name(int32_t cls);
+/* Number of CUDA kernels this library has launched in the process so far. */
+int64_t kb_launch_counter(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KB_H */

@@ -1,0 +1,342 @@
+// Graph ingest (step a1): host validation of the CSR Laplacian, device copy of its
+// off-diagonal part and diagonal excess, and the Gershgorin bound Lambda computed on the
+// device.  Also the error/diagnostic plumbing of the C ABI.
+//
+// Section 2.1, Eq. (generalizedLaplacian): L symmetric, L_ij < 0 exactly on edges,
+// L_ij = 0 off the graph, any diagonal.  Lambda is the Gershgorin bound
+// max_i sum_j |L_ij| of the "assumed" spectral bound (reading A5).
+#include "kb_internal.cuh"
+#include "kb_kernels.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <new>
+
+namespace kb {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return KB_ERR_NOMEM;
+    return KB_ERR_CUDA;
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// ---------------------------------------------------------------- profiling
+namespace {
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes, flops;
+};
+std::mutex g_prof_mu;
+bool g_prof = false;
+std::vector<ProfRec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+cudaEvent_t g_pending = nullptr;
+int g_pending_cls = -1;
+
+cudaEvent_t take_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+bool prof_on() { return g_prof; }
+
+void prof_begin(int cls, cudaStream_t s) {
+    if (!g_prof) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_pending = take_event();
+    g_pending_cls = cls;
+    cudaEventRecord(g_pending, s);
+}
+
+std::atomic<long long> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+void prof_end(int cls, cudaStream_t s, double bytes, double flops, int nlaunch) {
+    count_launches(nlaunch);
+    if (!g_prof) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_pending || g_pending_cls != cls) return;
+    cudaEvent_t b = take_event();
+    cudaEventRecord(b, s);
+    g_recs.push_back(ProfRec{cls, g_pending, b, bytes, flops});
+    g_pending = nullptr;
+}
+
+// ---------------------------------------------------------------- Gershgorin bound
+namespace {
+__global__ void k_gershgorin(GraphDev g, unsigned long long *out_bits) {
+    double best = 0.0;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < g.n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        double s = 0.0;
+        for (int p = g.rowptr[i]; p < g.rowptr[i + 1]; ++p) s += g.w ? double(g.w[p]) : 1.0;
+        const double diag = (g.rdiag ? double(g.rdiag[i]) : 0.0) + s;
+        best = fmax(best, fabs(diag) + s);
+    }
+    // non-negative doubles order like their bit patterns
+    for (int off = 16; off > 0; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out_bits, static_cast<unsigned long long>(__double_as_longlong(best)));
+}
+}  // namespace
+
+int launch_gershgorin(const GraphDev &g, double *out, cudaStream_t s) {
+    unsigned long long *d = nullptr;
+    KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&d), sizeof(unsigned long long), s));
+    KB_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), s));
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, int64_t(num_sms()) * 8)));
+    k_gershgorin<<<grid, 256, 0, s>>>(g, d);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    unsigned long long bits = 0;
+    KB_CUDA_TRY(cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, s));
+    KB_CUDA_TRY(cudaStreamSynchronize(s));
+    KB_CUDA_TRY(cudaFreeAsync(d, s));
+    double v;
+    std::memcpy(&v, &bits, sizeof(v));
+    *out = v;
+    return 0;
+}
+
+}  // namespace kb
+
+// ---------------------------------------------------------------- C ABI: graph
+using namespace kb;
+
+extern "C" int kb_graph_create(int64_t n, const int32_t *rowptr, const int32_t *col,
+                               const float *val, int32_t flags, void *stream, kb_graph **out) {
+    try {
+        if (!out) return fail(KB_ERR_ARG, "out is NULL");
+        *out = nullptr;
+        if (n < 1 || n >= (int64_t(1) << 31)) return fail(KB_ERR_ARG, "n out of range");
+        if (!rowptr || !col) return fail(KB_ERR_ARG, "rowptr/col is NULL");
+        if (rowptr[0] != 0) return fail(KB_ERR_CSR, "rowptr[0] != 0");
+        for (int64_t i = 0; i < n; ++i)
+            if (rowptr[i + 1] < rowptr[i]) return fail(KB_ERR_CSR, "rowptr not non-decreasing at row " + std::to_string(i));
+        const int64_t nnz = rowptr[n];
+        // pass 1: structure and signs, count stored off-diagonal entries
+        int64_t noff = 0;
+        bool unit = true;
+        for (int64_t i = 0; i < n; ++i) {
+            int32_t prev = -1;
+            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                const int32_t j = col[p];
+                if (j < 0 || j >= n) return fail(KB_ERR_CSR, "column out of range in row " + std::to_string(i));
+                if (j <= prev) return fail(KB_ERR_CSR, "columns not strictly increasing in row " + std::to_string(i));
+                prev = j;
+                if (j == i) {
+                    if (val && !std::isfinite(val[p])) return fail(KB_ERR_CSR, "non-finite diagonal");
+                    continue;
+                }
+                if (val) {
+                    const float v = val[p];
+                    if (!std::isfinite(v)) return fail(KB_ERR_CSR, "non-finite value");
+                    if (v > 0.f) return fail(KB_ERR_CSR, "positive off-diagonal entry in row " + std::to_string(i));
+                    if (v == 0.f) continue;   // explicit zero: not an edge
+                    if (v != -1.f) unit = false;
+                }
+                ++noff;
+            }
+        }
+        (void)nnz;
+        // pass 2: symmetry (pattern and bitwise values of the non-zero off-diagonal entries)
+        if (!(flags & KB_GRAPH_SKIP_SYMMETRY_CHECK)) {
+            for (int64_t i = 0; i < n; ++i) {
+                for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                    const int32_t j = col[p];
+                    if (j == i) continue;
+                    const float v = val ? val[p] : -1.f;
+                    if (v == 0.f) continue;
+                    const int32_t *b = col + rowptr[j], *e = col + rowptr[j + 1];
+                    const int32_t *q = std::lower_bound(b, e, int32_t(i));
+                    if (q == e || *q != i) return fail(KB_ERR_CSR, "pattern not symmetric at (" + std::to_string(i) + "," + std::to_string(j) + ")");
+                    const float vt = val ? val[q - col] : -1.f;
+                    if (vt != v) return fail(KB_ERR_CSR, "values not symmetric at (" + std::to_string(i) + "," + std::to_string(j) + ")");
+                }
+            }
+        }
+        // build the stored form
+        std::vector<int32_t> h_rowptr(n + 1);
+        std::vector<int32_t> h_col(noff);
+        std::vector<float> h_w(unit ? 0 : noff);
+        std::vector<float> h_rdiag(n);
+        bool zero_excess = true;
+        int64_t q = 0;
+        h_rowptr[0] = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            double wsum = 0.0, diag = 0.0;
+            bool has_diag = false;
+            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                const int32_t j = col[p];
+                if (j == i) {
+                    if (val) { diag = double(val[p]); has_diag = true; }
+                    continue;
+                }
+                const float v = val ? val[p] : -1.f;
+                if (v == 0.f) continue;
+                h_col[q] = j;
+                if (!unit) h_w[q] = -v;
+                wsum += double(-v);
+                ++q;
+            }
+            h_rowptr[i + 1] = int32_t(q);
+            // val == NULL: standard Laplacian, diagonal = degree (zero excess)
+            const double excess = (val ? (has_diag ? diag : 0.0) : wsum) - wsum;
+            h_rdiag[i] = float(excess);
+            if (h_rdiag[i] != 0.f) zero_excess = false;
+        }
+        int dev = 0;
+        KB_CUDA_TRY(cudaGetDevice(&dev));
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        kb_graph *g = new (std::nothrow) kb_graph();
+        if (!g) return fail(KB_ERR_NOMEM, "host allocation failed");
+        g->device = dev;
+        auto cleanup = [&]() {
+            cudaFree(g->d_rowptr); cudaFree(g->d_col); cudaFree(g->d_w); cudaFree(g->d_rdiag);
+            delete g;
+        };
+        cudaError_t e = cudaMalloc(&g->d_rowptr, sizeof(int32_t) * (n + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_col, sizeof(int32_t) * std::max<int64_t>(noff, 1));
+        if (e == cudaSuccess && !unit) e = cudaMalloc(&g->d_w, sizeof(float) * std::max<int64_t>(noff, 1));
+        if (e == cudaSuccess && !zero_excess) e = cudaMalloc(&g->d_rdiag, sizeof(float) * n);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_rowptr, h_rowptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && noff) e = cudaMemcpyAsync(g->d_col, h_col.data(), sizeof(int32_t) * noff, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !unit && noff) e = cudaMemcpyAsync(g->d_w, h_w.data(), sizeof(float) * noff, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !zero_excess) e = cudaMemcpyAsync(g->d_rdiag, h_rdiag.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(e, "graph upload");
+        }
+        g->dev.n = n;
+        g->dev.nnz = noff;
+        g->dev.rowptr = g->d_rowptr;
+        g->dev.col = g->d_col;
+        g->dev.w = g->d_w;
+        g->dev.rdiag = g->d_rdiag;
+        g->unit_weights = unit ? 1 : 0;
+        g->zero_excess = zero_excess ? 1 : 0;
+        int rc = launch_gershgorin(g->dev, &g->lambda, s);
+        if (rc) {
+            cleanup();
+            return rc;
+        }
+        *out = g;
+        return KB_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(KB_ERR_NOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(KB_ERR_CUDA, "unexpected exception");
+    }
+}
+
+extern "C" void kb_graph_destroy(kb_graph *g) {
+    if (!g) return;
+    cudaFree(g->d_rowptr);
+    cudaFree(g->d_col);
+    cudaFree(g->d_w);
+    cudaFree(g->d_rdiag);
+    delete g;
+}
+
+extern "C" int kb_graph_info(const kb_graph *g, int64_t *n, int64_t *nnz_offdiag, double *lambda_max,
+                             int32_t *standard_unit) {
+    if (!g) return fail(KB_ERR_ARG, "graph is NULL");
+    if (n) *n = g->dev.n;
+    if (nnz_offdiag) *nnz_offdiag = g->dev.nnz;
+    if (lambda_max) *lambda_max = g->lambda;
+    if (standard_unit) *standard_unit = (g->unit_weights && g->zero_excess) ? 1 : 0;
+    return KB_OK;
+}
+
+// ---------------------------------------------------------------- C ABI: diagnostics
+extern "C" const char *kb_status_string(int status) {
+    switch (status) {
+        case KB_OK: return "ok";
+        case KB_ERR_ARG: return "invalid argument";
+        case KB_ERR_CSR: return "invalid CSR Laplacian";
+        case KB_ERR_NODES: return "invalid node set";
+        case KB_ERR_CUDA: return "CUDA error";
+        case KB_ERR_NOMEM: return "out of device memory";
+        case KB_ERR_BREAKDOWN: return "Lanczos breakdown (rank-deficient block)";
+        case KB_ERR_UNSUPPORTED: return "unsupported combination";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char *kb_last_error(void) { return kb::g_last_error.c_str(); }
+
+extern "C" int kb_version(void) { return 10000; }
+
+extern "C" int kb_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(kb::g_prof_mu);
+    kb::g_prof = on != 0;
+    return KB_OK;
+}
+
+extern "C" int kb_profile_read(kb_kernel_stats *out, int32_t cap, int32_t *count) {
+    std::lock_guard<std::mutex> lk(kb::g_prof_mu);
+    std::vector<kb_kernel_stats> acc(KernelClass::COUNT);
+    for (int c = 0; c < KernelClass::COUNT; ++c) {
+        acc[c].kernel_class = c;
+        acc[c].launches = 0;
+        acc[c].total_ms = 0;
+        acc[c].alg_bytes = 0;
+        acc[c].alg_flops = 0;
+    }
+    for (auto &r : kb::g_recs) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto &a = acc[r.cls];
+        a.launches += 1;
+        a.total_ms += ms;
+        a.alg_bytes += r.bytes;
+        a.alg_flops += r.flops;
+        kb::g_pool.push_back(r.a);
+        kb::g_pool.push_back(r.b);
+    }
+    kb::g_recs.clear();
+    int k = 0;
+    for (int c = 0; c < KernelClass::COUNT && k < cap; ++c) out[k++] = acc[c];
+    if (count) *count = k;
+    return KB_OK;
+}
+
+extern "C" int64_t kb_launch_counter(void) { return kb::g_launches.load(); }
+
+extern "C" const char *kb_kernel_class_name(int32_t cls) {
+    static const char *names[] = {"spmm", "rowblock", "reduce", "small_fp64", "projected_fp64",
+                                  "assemble", "other"};
+    if (cls < 0 || cls >= KernelClass::COUNT) return "?";
+    return names[cls];
+}

@@ -1,0 +1,148 @@
+// Internal declarations shared by the CUDA translation units of libkb.
+//
+// Data layout in HBM
+//   * Graph: the off-diagonal part of L in CSR (int32 rowptr/col, FP32 weights
+//     w_ij = -L_ij > 0, weights omitted when all are 1) plus the diagonal excess
+//     r_i = L_ii - sum_j w_ij (omitted when it is zero everywhere, i.e. L = D - W).
+//     Then (L x)_i = sum_j w_ij (x_i - x_j) + r_i x_i   (difference form).
+//   * Blocks of the Krylov process: n x W row-major FP32 (or FP64 for the plain FP64
+//     mode), W = the block width M rounded up to 16/32/64/128; the padding columns hold
+//     zeros throughout.  One row of a block is W*4 bytes, read with 16-byte vector loads.
+//   * Small matrices (Gram partials, H blocks, R factors) are W x W row-major.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "kb.h"
+
+namespace kb {
+
+// ------------------------------------------------------------------ graph
+struct GraphDev {
+    int64_t n = 0;
+    int64_t nnz = 0;                  // stored off-diagonal entries
+    const int32_t *rowptr = nullptr;  // n+1
+    const int32_t *col = nullptr;     // nnz
+    const float *w = nullptr;         // nnz or nullptr (unit weights)
+    const float *rdiag = nullptr;     // n or nullptr (zero diagonal excess)
+};
+
+}  // namespace kb
+
+struct kb_graph {
+    kb::GraphDev dev;
+    int32_t *d_rowptr = nullptr;
+    int32_t *d_col = nullptr;
+    float *d_w = nullptr;
+    float *d_rdiag = nullptr;
+    double lambda = 0.0;     // Gershgorin bound
+    int device = 0;
+    int32_t unit_weights = 0;
+    int32_t zero_excess = 0;
+};
+
+namespace kb {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define KB_CUDA_TRY(expr)                                      \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) return ::kb::cuda_fail(_e, #expr); \
+    } while (0)
+
+// ------------------------------------------------------------------ device control block
+// One per solve, in device memory.  Kernels after a stop or a breakdown return early.
+struct Ctrl {
+    int32_t status;          // KB_OK / KB_ERR_BREAKDOWN
+    int32_t stop;            // 1 once the process stopped (invariant space or breakdown)
+    int32_t steps;           // blocks entering the result
+    int32_t breakdown_step;  // -1 or step index
+};
+
+// ------------------------------------------------------------------ profiling (events)
+struct KernelClass {
+    enum : int { SPMM = 0, ROWBLOCK, REDUCE, SMALL, PROJECTED, ASSEMBLE, OTHER, COUNT };
+};
+void prof_begin(int cls, cudaStream_t s);
+// Records the end event (when profiling) and always adds nlaunch to the launch counter.
+void prof_end(int cls, cudaStream_t s, double alg_bytes, double alg_flops, int nlaunch = 1);
+void count_launches(int k);
+bool prof_on();
+
+// ------------------------------------------------------------------ launch helpers
+int num_sms();
+inline int width_for(int M) { return M <= 16 ? 16 : M <= 32 ? 32 : M <= 64 ? 64 : 128; }
+
+// SpMM epilogue parameters (linear combination, used by gbl/sbl/cheb/cheb2/cbl):
+//   out_i[c] = c1[c]*(L x)_i[c] + c0[c]*x_i[c] + c2[c]*y_i[c] + s3*z_i[c] + (marker_i==c)*wE
+// c0/c1/c2 come from device arrays (length W) when the pointer is set, else the scalars.
+template <typename T>
+struct LinEpi {
+    const float *a1 = nullptr, *a0 = nullptr, *a2 = nullptr;
+    float s1 = 1.f, s0 = 0.f, s2 = 0.f, s3 = 0.f;
+    const T *y = nullptr;
+    const T *z = nullptr;
+    const int32_t *marker = nullptr;
+    float wE = 0.f;
+    T *out = nullptr;                 // internal n x W output (used when yout is null)
+    float *yout = nullptr;            // final FP32 output with leading dimension ldo, mo columns
+    double *dot_partials = nullptr;   // [grid][W]: sum_i x_i[c] * out_i[c]
+    const Ctrl *ctrl = nullptr;
+};
+
+// ldo <= 0: output is an internal n x W block; otherwise out has leading dimension ldo
+// and only columns < mo are written.  n_dense_in counts the dense inputs besides x
+// (y, z) for the algorithmic byte count.
+template <typename T>
+int launch_spmm(const GraphDev &g, int W, const T *x, const LinEpi<T> &e, cudaStream_t s,
+                int *grid_out, int64_t M_alg, int n_dense_in, int64_t ldo = 0, int mo = 0);
+template <typename T>
+int spmm_max_grid(int W);
+
+// Tall-skinny row-block kernels (tiled SIMT, FP32 or FP64), W x W matrices row-major:
+//   PROJ    : G = Qa^T X                                         (no write)
+//   UPD     : out = X - Qa*Ca - Qb*Cb (Qa may be null) ; write ; G = out^T out
+//   MULGRAM : out = X*Ca ; write ; G = out^T out
+//   MUL     : out = X*Ca ; write
+//   ASM     : y[:, :mo] = sum_{k < nblk} basis_k * Ca_k  (Ca stacked nblk*W x W), nblk
+//             capped by ctrl->steps
+// In-place out == x is allowed (a tile's output rows depend only on its input rows).
+enum RowMode { RB_PROJ = 0, RB_UPD = 1, RB_MULGRAM = 2, RB_MUL = 3, RB_ASM = 4 };
+template <typename T>
+struct RowArgs {
+    int64_t n = 0;
+    const T *x = nullptr;
+    const T *qa = nullptr;
+    const T *qb = nullptr;
+    const T *ca = nullptr;
+    const T *cb = nullptr;
+    T *out = nullptr;
+    T *partials = nullptr;          // [grid][W*W]
+    const T *basis = nullptr;       // ASM
+    int64_t block_stride = 0;
+    int nblk = 0;
+    float *y = nullptr;
+    int64_t ldy = 0;
+    int mo = 0;
+    const Ctrl *ctrl = nullptr;
+};
+template <typename T>
+int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *grid_out,
+                    int64_t M_alg);
+template <typename T>
+int rowblock_max_grid(int W);
+
+// Deterministic FP64 reduction of [nparts][len] partials into out[len].
+template <typename P>
+int launch_reduce(const P *parts, int nparts, int len, double *out, cudaStream_t s,
+                  const Ctrl *ctrl);
+
+}  // namespace kb

@@ -1,0 +1,73 @@
+// Launchers of the small / element-wise / projected-problem kernels (internal).
+#pragma once
+
+#include <algorithm>
+
+#include "kb_internal.cuh"
+
+namespace kb {
+
+// Up to CAP node indices passed by value to a kernel (no host-to-device copy needed).
+struct NodeChunk {
+    static constexpr int CAP = 256;
+    int32_t idx[CAP];
+    int32_t cnt;
+    int32_t col0;
+};
+
+// Chebyshev coefficients d_0..d_{n-1} passed by value (sum_j d_j T_j, no halving).
+struct ChebCoef {
+    static constexpr int CAP = 440;
+    int32_t n;
+    double d[CAP];
+};
+
+int launch_ctrl_init(Ctrl *c, int steps, cudaStream_t s);
+template <typename T>
+int launch_scatter(T *block, int64_t ld, const int32_t *nodes, int M, int col0, T val, cudaStream_t s);
+int launch_marker(int32_t *marker, const int32_t *nodes, int M, cudaStream_t s);
+template <typename T>
+int launch_scale_copy(T *out, const T *in, int64_t count, double scale, cudaStream_t s);
+int launch_fill_nan(float *Y, int64_t n, int64_t ldy, int mo, const Ctrl *ctrl, cudaStream_t s);
+
+template <typename T>
+int launch_hkk(const double *G, int M, int W, double *Hd, T *C, const Ctrl *ctrl, cudaStream_t s);
+template <typename T>
+int launch_chol(const double *G, int M, int W, int pass, int step, double inv_thresh2,
+                double piv_rel2, double *R1, double *Rinv64, T *Rinv, double *Hs, T *Bout,
+                Ctrl *ctrl, cudaStream_t s);
+
+int launch_lanczos_init(int W, int M, int gbl, double *sigma, int32_t *alive, float *c1, float *c2,
+                        cudaStream_t s);
+int launch_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k,
+                         const double *sigma, double *alpha, float *a_upd, const Ctrl *ctrl,
+                         cudaStream_t s);
+int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, int k,
+                        double thresh, double *beta, double *sigma, int32_t *alive, float *c1,
+                        float *c2, Ctrl *ctrl, cudaStream_t s);
+int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const double *beta,
+                       const double *sigma, int phi_kind, double eps, int s_int, double lam,
+                       const ChebCoef &cc, float *omega, double *work, const Ctrl *ctrl,
+                       cudaStream_t s);
+template <typename T>
+int launch_axpy_colnorm(int W, T *X, const T *P, const float *a, int64_t n, double *parts,
+                        int *grid_out, const Ctrl *ctrl, cudaStream_t s);
+int axpy_max_grid();
+template <typename T>
+int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const float *omega,
+                         int64_t n, float *Y, int64_t ldy, int mo, int64_t M_alg, cudaStream_t s);
+template <typename T>
+int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ctrl, cudaStream_t s);
+
+// Projected problem of the classical block Lanczos method (FP64, block tridiagonal H_m).
+int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
+                   const std::vector<double> &d, double *V0, double *V1, double *V2, double *U,
+                   const Ctrl *ctrl, cudaStream_t s);
+int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double eps, int s_int,
+                     double *Ld, double *Ls, double *Yw, double *U, const Ctrl *ctrl,
+                     cudaStream_t s);
+
+// Graph utilities.
+int launch_gershgorin(const GraphDev &g, double *out, cudaStream_t s);
+
+}  // namespace kb

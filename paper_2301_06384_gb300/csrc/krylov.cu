@@ -1,0 +1,588 @@
+// The five block Krylov drivers and the kb_krylov_apply entry points.
+//
+//   cbl   Algorithm 1 (classical block Lanczos) with CholeskyQR2 for the reduced QR of
+//         line 6 and the FP64 projected problem U = phi(H_m) F_1 (line 8).
+//   gbl   Algorithm 2 (global block Lanczos), Frobenius inner products.
+//   sbl   Section 3.3 (one ordinary Lanczos per column), run for all columns at once.
+//   cheb  Section 3.4: the degree-m Lobatto interpolant applied by Clenshaw's backward
+//         recurrence (same polynomial as the forward three-term recurrence; 3 block
+//         reads/writes per product instead of 5).
+//   cheb2 Section 3.4.1: the interpolant of sqrt(phi) of degree floor(m/2) applied twice.
+//
+// Every step runs on the device; the host only enqueues work.  No host synchronisation
+// happens inside a solve (breakdown and early stops travel through a device control block).
+#include "kb_internal.cuh"
+#include "kb_kernels.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+namespace kb {
+
+// ---------------------------------------------------------------- host coefficient math
+// e^{-t lambda} on [0, lam] as sum_k d_k T_k(1 - 2 lambda / lam):  with rho = t lam / 2,
+// e^{-t lambda} = e^{-rho} e^{rho x} and e^{rho x} = I_0(rho) + 2 sum_k I_k(rho) T_k(x)
+// (modified Bessel functions).  e^{-|rho|} I_k(|rho|) is computed by Miller's backward
+// recurrence I_{k-1} = I_{k+1} + (2k/a) I_k, normalised by I_0 + 2 sum_k I_k = e^{a}.
+std::vector<double> exp_series_coeffs(double t, double lam, double tol) {
+    const double rho = 0.5 * t * lam;
+    const double a = std::fabs(rho);
+    if (a < 1e-300) return {1.0, 0.0};
+    const int kmax = int(std::ceil(a + 12.0 * std::sqrt(a) + 60.0));
+    std::vector<double> b(kmax + 2, 0.0);
+    b[kmax + 1] = 0.0;
+    b[kmax] = 1e-280;
+    for (int k = kmax; k >= 1; --k) {
+        b[k - 1] = b[k + 1] + (2.0 * k / a) * b[k];
+        if (b[k - 1] > 1e250) {
+            for (int q = k - 1; q <= kmax + 1; ++q) b[q] *= 1e-250;
+        }
+    }
+    double S = b[0];
+    for (int k = 1; k <= kmax; ++k) S += 2.0 * b[k];
+    std::vector<double> d(kmax + 1);
+    const double growth = rho < 0 ? std::exp(2.0 * a) : 1.0;
+    double total = 0.0;
+    for (int k = 0; k <= kmax; ++k) {
+        double v = (k == 0 ? 1.0 : 2.0) * (b[k] / S) * growth;
+        if (rho < 0 && (k & 1)) v = -v;
+        d[k] = v;
+        total += std::fabs(v);
+    }
+    int last = 1;
+    for (int k = 0; k <= kmax; ++k)
+        if (std::fabs(d[k]) > tol * total) last = std::max(last, k);
+    d.resize(last + 1);
+    return d;
+}
+
+// phi (or sqrt(phi)) at a point.
+static double phi_value(kb_phi phi, const kb_params &p, double lam, bool sqrt_phi) {
+    if (phi == KB_PHI_EXP) return std::exp(-(sqrt_phi ? 0.5 * p.t : p.t) * lam);
+    return std::pow(p.eps + lam, -(sqrt_phi ? 0.5 * p.s : p.s));
+}
+
+// Eq. (chebcoeff) read as Lobatto interpolation (reading A3):
+//   c_k = (2/m) sum_{j=0..m}'' f(lambda_j) cos(pi j k / m),  lambda_j = lam/2 (1 - cos(pi j/m)),
+// the double prime halving the j = 0 and j = m terms.  The series sum_k'' c_k T_k (c_0 and
+// c_m halved) interpolates f on the grid.
+std::vector<double> lobatto_coeffs(kb_phi phi, const kb_params &p, int m, double lam, bool sqrt_phi) {
+    std::vector<double> f(m + 1), c(m + 1);
+    for (int j = 0; j <= m; ++j)
+        f[j] = phi_value(phi, p, 0.5 * lam * (1.0 - std::cos(M_PI * j / m)), sqrt_phi);
+    for (int k = 0; k <= m; ++k) {
+        double s = 0.0;
+        for (int j = 0; j <= m; ++j) {
+            const double wj = (j == 0 || j == m) ? 0.5 : 1.0;
+            // cos(pi j k / m) with the argument reduced mod 2m for accuracy
+            const long r = (long(j) * k) % (2L * m);
+            s += wj * f[j] * std::cos(M_PI * double(r) / m);
+        }
+        c[k] = 2.0 / m * s;
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------- workspace
+namespace {
+struct Arena {
+    char *base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    T *take(size_t count) {
+        const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+        off += bytes;
+        return p;
+    }
+};
+
+void ensure_pool(int dev) {
+    static int done_for = -1;
+    if (done_for == dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = std::numeric_limits<uint64_t>::max();
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done_for = dev;
+}
+
+struct Common {
+    kb_graph *g;
+    kb_phi phi;
+    kb_params p;
+    int s_int;
+    cudaStream_t s;
+    int spmm = 0;
+    Ctrl *hctrl = nullptr;   // host copy of the control block when the caller wants info
+};
+#define KB_TRY(x)                \
+    do {                         \
+        int _rc = (x);           \
+        if (_rc) return _rc;     \
+    } while (0)
+
+// ---------------------------------------------------------------- cbl
+template <typename T>
+struct CblBufs {
+    T *basis, *wbuf, *parts, *Cb, *B, *Rinv, *Ut;
+    double *Gsum, *Hd, *Hs, *R1, *Rinv64, *V0, *V1, *V2, *U;
+    Ctrl *ctrl;
+};
+
+template <typename T>
+void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_grid) {
+    b.basis = ar.take<T>(size_t(m) * n * W);
+    b.wbuf = ar.take<T>(size_t(n) * W);
+    b.parts = ar.take<T>(size_t(rb_grid) * W * W);
+    b.Cb = ar.take<T>(size_t(W) * W);
+    b.B = ar.take<T>(size_t(W) * W);
+    b.Rinv = ar.take<T>(size_t(W) * W);
+    b.Ut = ar.take<T>(size_t(m) * W * W);
+    b.Gsum = ar.take<double>(size_t(W) * W);
+    b.Hd = ar.take<double>(size_t(m) * M * M);
+    b.Hs = ar.take<double>(size_t(m) * M * M);
+    b.R1 = ar.take<double>(size_t(M) * M);
+    b.Rinv64 = ar.take<double>(size_t(W) * W);
+    b.V0 = ar.take<double>(size_t(m) * M * M);
+    b.V1 = ar.take<double>(size_t(m) * M * M);
+    b.V2 = ar.take<double>(size_t(m) * M * M);
+    b.U = ar.take<double>(size_t(m) * M * M);
+    b.ctrl = ar.take<Ctrl>(1);
+}
+
+template <typename T>
+int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy) {
+    const int64_t n = c.g->dev.n;
+    const int W = width_for(M);
+    const bool f64 = sizeof(T) == 8;
+    const int rb_grid = rowblock_max_grid<T>(W);
+    Arena dry;
+    CblBufs<T> b{};
+    plan_cbl<T>(dry, b, n, M, W, m, rb_grid);
+    Arena ar;
+    KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
+    plan_cbl<T>(ar, b, n, M, W, m, rb_grid);
+    auto body = [&]() -> int {
+        const double lam = c.g->lambda;
+        const double tau_inv = f64 ? 1e-12 : 1e-6;
+        const double tau_piv = f64 ? 1e-12 : 1e-5;
+        const double inv_thresh2 = (tau_inv * lam) * (tau_inv * lam) * M;
+        const double piv2 = tau_piv * tau_piv;
+        KB_TRY(launch_ctrl_init(b.ctrl, m, c.s));
+        KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W, c.s));
+        KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
+        const int64_t bs = n * W;
+        for (int k = 1; k <= m; ++k) {
+            T *Qk = b.basis + (k - 1) * bs;
+            T *Qp = k >= 2 ? b.basis + (k - 2) * bs : nullptr;
+            // line 3 (first half): W = L Q_k
+            LinEpi<T> e;
+            e.s1 = 1.f;
+            e.out = b.wbuf;
+            e.ctrl = b.ctrl;
+            KB_TRY(launch_spmm<T>(c.g->dev, W, Qk, e, c.s, nullptr, M, 0));
+            ++c.spmm;
+            // line 4: H_kk = Q_k^T L Q_k
+            int grid = 0;
+            RowArgs<T> pa;
+            pa.n = n; pa.x = b.wbuf; pa.qa = Qk; pa.partials = b.parts; pa.ctrl = b.ctrl;
+            KB_TRY(launch_rowblock<T>(RB_PROJ, W, pa, c.s, &grid, M));
+            KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+            KB_TRY(launch_hkk<T>(b.Gsum, M, W, b.Hd + size_t(k - 1) * M * M, b.Cb, b.ctrl, c.s));
+            if (k == m) break;   // Q_{m+1} is never used (reading A9)
+            // lines 3 and 5: X = L Q_k - Q_{k-1} H_{k-1,k} - Q_k H_kk, then Gram X^T X
+            T *X = b.basis + k * bs;
+            RowArgs<T> ua;
+            ua.n = n; ua.x = b.wbuf; ua.qa = Qp; ua.ca = b.B; ua.qb = Qk; ua.cb = b.Cb;
+            ua.out = X; ua.partials = b.parts; ua.ctrl = b.ctrl;
+            KB_TRY(launch_rowblock<T>(RB_UPD, W, ua, c.s, &grid, M));
+            KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+            // line 6: X = Q_{k+1} H_{k+1,k} by CholeskyQR2
+            KB_TRY(launch_chol<T>(b.Gsum, M, W, 1, k, inv_thresh2, piv2, b.R1, b.Rinv64, b.Rinv,
+                                  nullptr, nullptr, b.ctrl, c.s));
+            RowArgs<T> ma;
+            ma.n = n; ma.x = X; ma.ca = b.Rinv; ma.out = X; ma.partials = b.parts; ma.ctrl = b.ctrl;
+            KB_TRY(launch_rowblock<T>(RB_MULGRAM, W, ma, c.s, &grid, M));
+            KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+            KB_TRY(launch_chol<T>(b.Gsum, M, W, 2, k, inv_thresh2, piv2, b.R1, b.Rinv64, b.Rinv,
+                                  b.Hs + size_t(k - 1) * M * M, b.B, b.ctrl, c.s));
+            RowArgs<T> qa;
+            qa.n = n; qa.x = X; qa.ca = b.Rinv; qa.out = X; qa.ctrl = b.ctrl;
+            KB_TRY(launch_rowblock<T>(RB_MUL, W, qa, c.s, &grid, M));
+        }
+        // line 8: U = phi(H_m) F_1 in FP64
+        if (c.phi == KB_PHI_EXP) {
+            const std::vector<double> d = exp_series_coeffs(c.p.t, lam, 1e-17);
+            KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam, d, b.V0, b.V1, b.V2, b.U, b.ctrl, c.s));
+        } else {
+            KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, b.U,
+                                    b.ctrl, c.s));
+        }
+        KB_TRY(launch_u_convert<T>(b.U, M, W, m, b.Ut, b.ctrl, c.s));
+        // line 9: Y = [Q_1 .. Q_m] U
+        RowArgs<T> aa;
+        aa.n = n; aa.basis = b.basis; aa.block_stride = bs; aa.nblk = m; aa.ca = b.Ut;
+        aa.y = Y; aa.ldy = ldy; aa.mo = M; aa.ctrl = b.ctrl;
+        int grid = 0;
+        KB_TRY(launch_rowblock<T>(RB_ASM, W, aa, c.s, &grid, M));
+        KB_TRY(launch_fill_nan(Y, n, ldy, M, b.ctrl, c.s));
+        return 0;
+    };
+    int rc = body();
+    if (!rc && c.hctrl) {
+        cudaError_t e = cudaMemcpyAsync(c.hctrl, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c.s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "ctrl readback");
+    }
+    cudaFreeAsync(ar.base, c.s);
+    return rc;
+}
+
+// ---------------------------------------------------------------- gbl / sbl
+template <typename T>
+struct LzBufs {
+    T *basis;
+    double *parts, *sigma, *alpha, *beta, *work;
+    int32_t *alive;
+    float *c1, *c2, *aupd, *omega;
+    Ctrl *ctrl;
+};
+
+template <typename T>
+void plan_lz(Arena &ar, LzBufs<T> &b, int64_t n, int W, int m, int pgrid) {
+    b.basis = ar.take<T>(size_t(m + 1) * n * W);
+    b.parts = ar.take<double>(size_t(pgrid) * W);
+    b.sigma = ar.take<double>(size_t(m + 1) * W);
+    b.alpha = ar.take<double>(size_t(m + 1) * W);
+    b.beta = ar.take<double>(size_t(m + 1) * W);
+    b.work = ar.take<double>(size_t(W) * 4 * m);
+    b.alive = ar.take<int32_t>(W);
+    b.c1 = ar.take<float>(W);
+    b.c2 = ar.take<float>(W);
+    b.aupd = ar.take<float>(W);
+    b.omega = ar.take<float>(size_t(m) * W);
+    b.ctrl = ar.take<Ctrl>(1);
+}
+
+template <typename T>
+int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, float *Y,
+                       int64_t ldy) {
+    const int64_t n = c.g->dev.n;
+    const int W = width_for(M);
+    const bool f64 = sizeof(T) == 8;
+    const int pgrid = std::max(spmm_max_grid<T>(W), axpy_max_grid());
+    ChebCoef cc{};
+    if (c.phi == KB_PHI_EXP) {
+        const std::vector<double> d = exp_series_coeffs(c.p.t, c.g->lambda, 1e-17);
+        if (int(d.size()) > ChebCoef::CAP)
+            return fail(KB_ERR_UNSUPPORTED, "t * Lambda too large for the tridiagonal Chebyshev series");
+        cc.n = int(d.size());
+        for (int j = 0; j < cc.n; ++j) cc.d[j] = d[j];
+    }
+    Arena dry;
+    LzBufs<T> b{};
+    plan_lz<T>(dry, b, n, W, m, pgrid);
+    Arena ar;
+    KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
+    plan_lz<T>(ar, b, n, W, m, pgrid);
+    auto body = [&]() -> int {
+        const double thresh = (f64 ? 1e-12 : 1e-6) * c.g->lambda;
+        KB_TRY(launch_ctrl_init(b.ctrl, m, c.s));
+        KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W, c.s));
+        KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
+        KB_CUDA_TRY(cudaMemsetAsync(b.beta, 0, sizeof(double) * size_t(m + 1) * W, c.s));
+        KB_CUDA_TRY(cudaMemsetAsync(b.alpha, 0, sizeof(double) * size_t(m + 1) * W, c.s));
+        KB_CUDA_TRY(cudaMemsetAsync(b.sigma, 0, sizeof(double) * size_t(m + 1) * W, c.s));
+        KB_TRY(launch_lanczos_init(W, M, gbl ? 1 : 0, b.sigma, b.alive, b.c1, b.c2, c.s));
+        const int64_t bs = n * W;
+        for (int k = 1; k <= m; ++k) {
+            T *Pk = b.basis + (k - 1) * bs;
+            T *Pp = k >= 2 ? b.basis + (k - 2) * bs : nullptr;
+            T *X = b.basis + k * bs;
+            // X = L Q_k - h_{k,k-1} Q_{k-1}, with Q_k = sigma_k P_k; dots <P_k, X> per column
+            LinEpi<T> e;
+            e.a1 = b.c1;
+            e.a2 = b.c2;
+            e.s0 = 0.f;
+            e.y = Pp;
+            e.out = X;
+            e.dot_partials = b.parts;
+            e.ctrl = b.ctrl;
+            int grid = 0;
+            KB_TRY(launch_spmm<T>(c.g->dev, W, Pk, e, c.s, &grid, M, Pp ? 1 : 0));
+            ++c.spmm;
+            KB_TRY(launch_lanczos_alpha(b.parts, grid, W, M, gbl ? 1 : 0, k - 1, b.sigma, b.alpha,
+                                        b.aupd, b.ctrl, c.s));
+            if (k == m) break;
+            int grid2 = 0;
+            KB_TRY(launch_axpy_colnorm<T>(W, X, Pk, b.aupd, n, b.parts, &grid2, b.ctrl, c.s));
+            KB_TRY(launch_lanczos_beta(b.parts, grid2, W, M, gbl ? 1 : 0, k - 1, thresh, b.beta,
+                                       b.sigma, b.alive, b.c1, b.c2, b.ctrl, c.s));
+        }
+        KB_TRY(launch_tridiag_phi(W, M, m, gbl ? 1 : 0, b.alpha, b.beta, b.sigma, int(c.phi),
+                                  c.p.eps, c.s_int, c.g->lambda, cc, b.omega, b.work, b.ctrl, c.s));
+        KB_TRY(launch_assemble_diag<T>(W, b.basis, bs, m, b.omega, n, Y, ldy, M, M, c.s));
+        return 0;
+    };
+    int rc = body();
+    if (!rc && c.hctrl) {
+        cudaError_t e = cudaMemcpyAsync(c.hctrl, b.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c.s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "ctrl readback");
+    }
+    cudaFreeAsync(ar.base, c.s);
+    return rc;
+}
+
+// ---------------------------------------------------------------- cheb / cheb2
+template <typename T>
+int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int64_t n,
+              const int32_t *marker, const int32_t *nodes, int Mc, const T *Zsrc, T *bufs[3],
+              T *out, float *yout, int64_t ldo, int mo, int64_t M_alg) {
+    // weights of sum_k'' c_k T_k (reading A3)
+    const int h = int(coef.size()) - 1;
+    std::vector<double> w(coef);
+    w[0] *= 0.5;
+    w[h] *= 0.5;
+    // b_h = w_h S
+    int cur_i = 0, prev_i = -1;
+    if (Zsrc) {
+        KB_TRY(launch_scale_copy<T>(bufs[0], Zsrc, n * W, w[h], c.s));
+    } else {
+        KB_CUDA_TRY(cudaMemsetAsync(bufs[0], 0, sizeof(T) * size_t(n) * W, c.s));
+        KB_TRY(launch_scatter<T>(bufs[0], W, nodes, Mc, 0, T(w[h]), c.s));
+    }
+    // b_k = w_k S + 2 A b_{k+1} - b_{k+2} (k = h-1..1);  result = w_0 S + A b_1 - b_2,
+    // A = I - (2/lam) L
+    for (int k = h - 1; k >= 0; --k) {
+        const bool last = k == 0;
+        int dst_i = 0;
+        while (dst_i == cur_i || dst_i == prev_i) ++dst_i;
+        LinEpi<T> e;
+        e.s1 = float((last ? -2.0 : -4.0) / lam);
+        e.s0 = last ? 1.f : 2.f;
+        e.s2 = -1.f;
+        e.y = prev_i >= 0 ? bufs[prev_i] : nullptr;
+        if (Zsrc) { e.z = Zsrc; e.s3 = float(w[k]); }
+        else { e.marker = marker; e.wE = float(w[k]); }
+        if (last) {
+            if (yout) e.yout = yout;
+            else e.out = out;
+        } else {
+            e.out = bufs[dst_i];
+        }
+        KB_TRY(launch_spmm<T>(c.g->dev, W, bufs[cur_i], e, c.s, nullptr, M_alg,
+                              (prev_i >= 0 ? 1 : 0) + (Zsrc ? 1 : 0), (last && yout) ? ldo : 0,
+                              (last && yout) ? mo : 0));
+        ++c.spmm;
+        prev_i = cur_i;
+        cur_i = dst_i;
+    }
+    return 0;
+}
+
+template <typename T>
+int run_cheb(Common &c, bool squared, const int32_t *nodes, int M, int m, float *Y, int64_t ldy) {
+    const int64_t n = c.g->dev.n;
+    const double lam = c.p.lambda_max > 0 ? c.p.lambda_max : c.g->lambda;
+    const int h = squared ? m / 2 : m;
+    const std::vector<double> coef = lobatto_coeffs(c.phi, c.p, h, lam, squared);
+    const int Mmax = std::min(M, sizeof(T) == 8 ? 64 : 128);
+    const int Wmax = width_for(Mmax);
+    Arena dry;
+    auto plan = [&](Arena &ar, T **bufs, T **Z, int32_t **marker) {
+        for (int i = 0; i < 3; ++i) bufs[i] = ar.take<T>(size_t(n) * Wmax);
+        *Z = squared ? ar.take<T>(size_t(n) * Wmax) : nullptr;
+        *marker = ar.take<int32_t>(size_t(n));
+    };
+    T *bufs[3], *Z;
+    int32_t *marker;
+    plan(dry, bufs, &Z, &marker);
+    Arena ar;
+    KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
+    plan(ar, bufs, &Z, &marker);
+    auto body = [&]() -> int {
+        for (int col0 = 0; col0 < M; col0 += Mmax) {
+            const int Mc = std::min(Mmax, M - col0);
+            const int W = width_for(Mc);
+            KB_CUDA_TRY(cudaMemsetAsync(marker, 0xFF, sizeof(int32_t) * size_t(n), c.s));
+            KB_TRY(launch_marker(marker, nodes + col0, Mc, c.s));
+            if (!squared) {
+                KB_TRY(cheb_pass<T>(c, coef, lam, W, n, marker, nodes + col0, Mc, nullptr, bufs,
+                                    nullptr, Y + col0, ldy, Mc, Mc));
+            } else {
+                KB_TRY(cheb_pass<T>(c, coef, lam, W, n, marker, nodes + col0, Mc, nullptr, bufs, Z,
+                                    nullptr, 0, 0, Mc));
+                KB_TRY(cheb_pass<T>(c, coef, lam, W, n, marker, nodes + col0, Mc, Z, bufs,
+                                    nullptr, Y + col0, ldy, Mc, Mc));
+            }
+        }
+        return 0;
+    };
+    const int rc = body();
+    cudaFreeAsync(ar.base, c.s);
+    return rc;
+}
+
+}  // namespace
+}  // namespace kb
+
+// ---------------------------------------------------------------- C ABI
+using namespace kb;
+
+namespace {
+
+int validate(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
+             const int32_t *nodes, int32_t M, int32_t m, const void *Y, int *s_int) {
+    if (!g) return fail(KB_ERR_ARG, "graph is NULL");
+    if (!params) return fail(KB_ERR_ARG, "params is NULL");
+    if (!nodes) return fail(KB_ERR_ARG, "nodes is NULL");
+    if (!Y) return fail(KB_ERR_ARG, "Y is NULL");
+    if (method < KB_CBL || method > KB_CHEB2) return fail(KB_ERR_ARG, "bad method");
+    if (phi != KB_PHI_EXP && phi != KB_PHI_SPLINE) return fail(KB_ERR_ARG, "bad phi");
+    if (M < 1 || M > g->dev.n) return fail(KB_ERR_ARG, "M out of range");
+    if (m < 1 || m > 100000) return fail(KB_ERR_ARG, "m out of range");
+    if (method == KB_CHEB2 && m < 2) return fail(KB_ERR_ARG, "KB_CHEB2 needs m >= 2");
+    if (params->basis != KB_F32 && params->basis != KB_F64)
+        return fail(KB_ERR_UNSUPPORTED, "basis dtype not implemented");
+    if (params->reorth) return fail(KB_ERR_UNSUPPORTED, "reorthogonalisation not implemented");
+    const int wmax = params->basis == KB_F64 ? 64 : 128;
+    if ((method == KB_CBL || method == KB_GBL) && M > wmax)
+        return fail(KB_ERR_UNSUPPORTED, "block width too large for this method and dtype");
+    if (phi == KB_PHI_EXP) {
+        if (!std::isfinite(params->t)) return fail(KB_ERR_ARG, "t not finite");
+    } else {
+        if (!(params->eps > 0) || !std::isfinite(params->eps)) return fail(KB_ERR_ARG, "eps must be > 0");
+        if (!(params->s > 0) || !std::isfinite(params->s)) return fail(KB_ERR_ARG, "s must be > 0");
+    }
+    *s_int = 0;
+    if (phi == KB_PHI_SPLINE && (method == KB_CBL || method == KB_GBL || method == KB_SBL)) {
+        if (params->s != std::floor(params->s) || params->s > 64)
+            return fail(KB_ERR_UNSUPPORTED, "Lanczos methods support integer s <= 64 only");
+        *s_int = int(params->s);
+    }
+    if (method == KB_CBL && phi == KB_PHI_EXP && std::fabs(params->t) * g->lambda > 2e5)
+        return fail(KB_ERR_UNSUPPORTED, "t * Lambda too large for the Chebyshev projected solve");
+    std::vector<int32_t> sorted(nodes, nodes + M);
+    std::sort(sorted.begin(), sorted.end());
+    if (sorted.front() < 0 || sorted.back() >= g->dev.n) return fail(KB_ERR_NODES, "node index out of range");
+    for (int i = 1; i < M; ++i)
+        if (sorted[i] == sorted[i - 1]) return fail(KB_ERR_NODES, "repeated node " + std::to_string(sorted[i]));
+    return KB_OK;
+}
+
+int apply_device(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
+                 const int32_t *nodes, int32_t M, int32_t m, float *Y, void *stream, kb_info *info) {
+    int s_int = 0;
+    int rc = validate(g, method, phi, params, nodes, M, m, Y, &s_int);
+    if (rc) return rc;
+    KB_CUDA_TRY(cudaSetDevice(g->device));
+    ensure_pool(g->device);
+    Common c{g, phi, *params, s_int, static_cast<cudaStream_t>(stream), 0, nullptr};
+    const bool f64 = params->basis == KB_F64;
+    const int chunk = f64 ? 64 : 128;
+    // one host control block per column group (sbl may run several groups)
+    std::vector<Ctrl> hc;
+    const int ngroups = method == KB_SBL ? (M + chunk - 1) / chunk : 1;
+    if (info) hc.assign(ngroups, Ctrl{KB_OK, 0, m, -1});
+    switch (method) {
+        case KB_CBL:
+            c.hctrl = info ? &hc[0] : nullptr;
+            rc = f64 ? run_cbl<double>(c, nodes, M, m, Y, M) : run_cbl<float>(c, nodes, M, m, Y, M);
+            break;
+        case KB_GBL:
+            c.hctrl = info ? &hc[0] : nullptr;
+            rc = f64 ? run_lanczos_scalar<double>(c, true, nodes, M, m, Y, M)
+                     : run_lanczos_scalar<float>(c, true, nodes, M, m, Y, M);
+            break;
+        case KB_SBL:
+            for (int col0 = 0, gi = 0; col0 < M && !rc; col0 += chunk, ++gi) {
+                const int Mc = std::min(chunk, M - col0);
+                c.hctrl = info ? &hc[gi] : nullptr;
+                rc = f64 ? run_lanczos_scalar<double>(c, false, nodes + col0, Mc, m, Y + col0, M)
+                         : run_lanczos_scalar<float>(c, false, nodes + col0, Mc, m, Y + col0, M);
+            }
+            break;
+        case KB_CHEB:
+        case KB_CHEB2:
+            rc = f64 ? run_cheb<double>(c, method == KB_CHEB2, nodes, M, m, Y, M)
+                     : run_cheb<float>(c, method == KB_CHEB2, nodes, M, m, Y, M);
+            break;
+    }
+    if (rc) return rc;
+    if (!info) return KB_OK;
+    KB_CUDA_TRY(cudaStreamSynchronize(c.s));
+    info->status = KB_OK;
+    info->steps_done = m;
+    info->breakdown_step = -1;
+    for (const Ctrl &h : hc) {
+        if (h.status != KB_OK) info->status = h.status;
+        if (h.breakdown_step >= 0) info->breakdown_step = h.breakdown_step;
+        if (method != KB_SBL) info->steps_done = h.steps;
+    }
+    if (method == KB_CHEB2) info->steps_done = 2 * (m / 2);
+    info->spmm_launches = c.spmm;
+    info->lambda_used = (method == KB_CHEB || method == KB_CHEB2)
+                            ? (params->lambda_max > 0 ? params->lambda_max : g->lambda)
+                            : 0.0;
+    if (info->status != KB_OK) return fail(info->status, "Lanczos breakdown: rank-deficient block");
+    return KB_OK;
+}
+
+}  // namespace
+
+extern "C" int kb_krylov_apply(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
+                               const int32_t *nodes, int32_t M, int32_t m, float *Y, void *stream,
+                               kb_info *info) {
+    try {
+        return apply_device(g, method, phi, params, nodes, M, m, Y, stream, info);
+    } catch (const std::bad_alloc &) {
+        return fail(KB_ERR_NOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(KB_ERR_CUDA, "unexpected exception");
+    }
+}
+
+extern "C" int kb_krylov_apply_host(kb_graph *g, kb_method method, kb_phi phi,
+                                    const kb_params *params, const int32_t *nodes, int32_t M,
+                                    int32_t m, float *Y_host, void *stream, kb_info *info) {
+    try {
+        if (!g || !Y_host) return fail(KB_ERR_ARG, "graph or Y_host is NULL");
+        if (M < 1 || M > g->dev.n) return fail(KB_ERR_ARG, "M out of range");
+        KB_CUDA_TRY(cudaSetDevice(g->device));
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        float *dY = nullptr;
+        const size_t bytes = sizeof(float) * size_t(g->dev.n) * size_t(M);
+        KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&dY), bytes, s));
+        int rc = apply_device(g, method, phi, params, nodes, M, m, dY, stream, info);
+        if (rc == KB_OK || rc == KB_ERR_BREAKDOWN) {
+            cudaError_t e = cudaMemcpyAsync(Y_host, dY, bytes, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess && rc == KB_OK) rc = cuda_fail(e, "result copy");
+        }
+        cudaFreeAsync(dY, s);
+        cudaStreamSynchronize(s);
+        return rc;
+    } catch (...) {
+        return fail(KB_ERR_CUDA, "unexpected exception");
+    }
+}
+
+extern "C" int kb_exp_series_coeffs(double t, double lam, double tol, double *d, int32_t cap,
+                                    int32_t *count) {
+    if (!d || !count || !(lam > 0)) return fail(KB_ERR_ARG, "bad argument");
+    const std::vector<double> v = exp_series_coeffs(t, lam, tol);
+    *count = int32_t(v.size());
+    for (int i = 0; i < int(v.size()) && i < cap; ++i) d[i] = v[i];
+    return int(v.size()) <= cap ? KB_OK : fail(KB_ERR_ARG, "cap too small");
+}
+
+extern "C" int kb_cheb_lobatto_coeffs(kb_phi phi, const kb_params *params, int32_t m, double lam,
+                                      int32_t sqrt_phi, double *c) {
+    if (!params || !c || m < 1 || !(lam > 0)) return fail(KB_ERR_ARG, "bad argument");
+    const std::vector<double> v = lobatto_coeffs(phi, *params, m, lam, sqrt_phi != 0);
+    for (int k = 0; k <= m; ++k) c[k] = v[k];
+    return KB_OK;
+}

@@ -1,0 +1,221 @@
+// The projected problem U = phi(H_m) F_1 of the classical block Lanczos method
+// (Algorithm 1, line 8), in FP64 on the device.
+//
+// H_m is block tridiagonal: diagonal blocks H_kk (symmetric) and sub-diagonal blocks
+// H_{k+1,k} = R (upper triangular), super-diagonal blocks R^T.  Its spectrum lies in
+// [0, Lambda] (interlacing, proof of Theorem 3.1), so:
+//   * exp:    U = sum_j d_j T_j(I - 2 H/Lambda) F_1 with the Chebyshev coefficients d_j
+//             of e^{-t lambda} on [0, Lambda] (computed on the host from modified Bessel
+//             functions), by the three-term recurrence on the block vectors V_j.  V_j is
+//             supported on block rows 0..j, so iteration j touches only j+2 block rows.
+//   * spline: for integer s, s solves with the SPD block tridiagonal eps I + H_m through
+//             its block Cholesky factorisation (block Thomas algorithm).
+// Both give the same U as the spectral evaluation assumed in Section 7, up to FP64
+// rounding (the Chebyshev series is truncated below 1e-17 relative).
+#include "kb_internal.cuh"
+#include "kb_kernels.cuh"
+
+namespace kb {
+namespace {
+
+constexpr int TC = 16;   // output columns per CTA
+
+__global__ void k_cheb_bt_seed(double *V0, double *U, int M, double d0) {
+    const int i = threadIdx.x + blockIdx.x * blockDim.x;
+    if (i < M) {
+        V0[int64_t(i) * M + i] = 1.0;
+        U[int64_t(i) * M + i] = d0;
+    }
+}
+
+// V_{j+1} = beta (V_j - g H V_j) - gamma V_{j-1};  U += d_{j+1} V_{j+1}
+__global__ void __launch_bounds__(256)
+k_cheb_bt_iter(const double *__restrict__ Hd, const double *__restrict__ Hs,
+               const double *__restrict__ Vp, const double *__restrict__ Vc, double *__restrict__ Vn,
+               double *__restrict__ U, int M, double beta, double gamma, double dnext, double g,
+               const Ctrl *ctrl) {
+    const int r = blockIdx.x;
+    const int steps = ctrl->steps;
+    if (r >= steps) return;
+    const int c0 = blockIdx.y * TC;
+    extern __shared__ double sv[];   // [3][M][TC]
+    double *s0 = sv, *s1 = sv + M * TC, *s2 = sv + 2 * M * TC;
+    const int64_t MM = int64_t(M) * M;
+    for (int idx = threadIdx.x; idx < M * TC; idx += blockDim.x) {
+        const int k = idx / TC, cc = idx % TC, c = c0 + cc;
+        double a = 0.0, b = 0.0, d = 0.0;
+        if (c < M) {
+            if (r > 0) a = Vc[(r - 1) * MM + int64_t(k) * M + c];
+            b = Vc[r * MM + int64_t(k) * M + c];
+            if (r + 1 < steps) d = Vc[(r + 1) * MM + int64_t(k) * M + c];
+        }
+        s0[idx] = a; s1[idx] = b; s2[idx] = d;
+    }
+    __syncthreads();
+    const double *hd = Hd + r * MM;
+    const double *hl = (r > 0) ? Hs + (r - 1) * MM : nullptr;   // H_{r, r-1} = R_{r-1} (upper)
+    const double *hu = (r + 1 < steps) ? Hs + r * MM : nullptr; // H_{r, r+1} = R_r^T
+    for (int idx = threadIdx.x; idx < M * TC; idx += blockDim.x) {
+        const int i = idx / TC, cc = idx % TC, c = c0 + cc;
+        if (c >= M) continue;
+        double hv = 0.0;
+        for (int k = 0; k < M; ++k) hv = fma(hd[i * M + k], s1[k * TC + cc], hv);
+        if (hl)
+            for (int k = i; k < M; ++k) hv = fma(hl[i * M + k], s0[k * TC + cc], hv);
+        if (hu)
+            for (int k = 0; k <= i; ++k) hv = fma(hu[k * M + i], s2[k * TC + cc], hv);
+        const double av = s1[i * TC + cc] - g * hv;
+        const int64_t o = r * MM + int64_t(i) * M + c;
+        const double vn = beta * av - gamma * Vp[o];
+        Vn[o] = vn;
+        U[o] += dnext * vn;
+    }
+}
+
+// ---------------------------------------------------------------- block Cholesky (spline)
+// One CTA; all scratch in global memory (L1/L2 resident for the sizes used).
+__device__ void chol_lower_inplace(double *A, int M) {
+    // A = L L^T, lower L overwrites A (upper part left as is)
+    __shared__ double piv;
+    for (int j = 0; j < M; ++j) {
+        if (threadIdx.x == 0) {
+            double d = A[j * M + j];
+            piv = sqrt(fmax(d, 1e-300));
+            A[j * M + j] = piv;
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < M; i += blockDim.x) A[i * M + j] /= piv;
+        __syncthreads();
+        const int L = M - j - 1;
+        for (int idx = threadIdx.x; idx < L * L; idx += blockDim.x) {
+            const int a = j + 1 + idx / L, b = j + 1 + idx % L;
+            if (b <= a) A[a * M + b] -= A[a * M + j] * A[b * M + j];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+k_bt_spline(const double *Hd, const double *Hs, int M, double eps, int s_int, double *Ld,
+            double *Ls, double *Yw, double *U, const Ctrl *ctrl) {
+    const int steps = ctrl->steps;
+    const int64_t MM = int64_t(M) * M;
+    // factor eps I + H = L L^T, L block lower bidiagonal (Ld diagonal, Ls sub-diagonal blocks)
+    for (int r = 0; r < steps; ++r) {
+        double *D = Ld + r * MM;
+        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+            const int i = idx / M, j = idx % M;
+            double v = Hd[r * MM + idx] + (i == j ? eps : 0.0);
+            if (r > 0) {
+                const double *P = Ls + (r - 1) * MM;
+                for (int k = 0; k < M; ++k) v -= P[i * M + k] * P[j * M + k];
+            }
+            D[idx] = v;
+        }
+        __syncthreads();
+        chol_lower_inplace(D, M);
+        if (r + 1 < steps) {
+            // Ls_r = H_{r+1,r} D^{-T}: row i solves D x = H_{r+1,r}[i,:]^T
+            const double *Hsub = Hs + r * MM;
+            double *P = Ls + r * MM;
+            for (int i = threadIdx.x; i < M; i += blockDim.x) {
+                for (int j = 0; j < M; ++j) {
+                    double v = Hsub[i * M + j];
+                    for (int k = 0; k < j; ++k) v -= D[j * M + k] * P[i * M + k];
+                    P[i * M + j] = v / D[j * M + j];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // U = F_1, then s_int times U <- (eps I + H)^{-1} U
+    for (int idx = threadIdx.x; idx < steps * M * M; idx += blockDim.x) {
+        const int64_t blk = idx / MM;
+        const int i = int((idx / M) % M), j = int(idx % M);
+        U[idx] = (blk == 0 && i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int rep = 0; rep < s_int; ++rep) {
+        // forward: Y_r = D_r^{-1} (U_r - Ls_{r-1} Y_{r-1})
+        for (int r = 0; r < steps; ++r) {
+            const double *D = Ld + r * MM;
+            double *Y = Yw + r * MM;
+            for (int c = threadIdx.x; c < M; c += blockDim.x) {
+                for (int i = 0; i < M; ++i) {
+                    double v = U[r * MM + int64_t(i) * M + c];
+                    if (r > 0) {
+                        const double *P = Ls + (r - 1) * MM;
+                        const double *Yp = Yw + (r - 1) * MM;
+                        for (int k = 0; k < M; ++k) v -= P[i * M + k] * Yp[k * M + c];
+                    }
+                    for (int k = 0; k < i; ++k) v -= D[i * M + k] * Y[k * M + c];
+                    Y[i * M + c] = v / D[i * M + i];
+                }
+            }
+            __syncthreads();
+        }
+        // backward: U_r = D_r^{-T} (Y_r - Ls_r^T U_{r+1})
+        for (int r = steps - 1; r >= 0; --r) {
+            const double *D = Ld + r * MM;
+            for (int c = threadIdx.x; c < M; c += blockDim.x) {
+                for (int i = M - 1; i >= 0; --i) {
+                    double v = Yw[r * MM + int64_t(i) * M + c];
+                    if (r + 1 < steps) {
+                        const double *P = Ls + r * MM;
+                        const double *Un = U + (r + 1) * MM;
+                        for (int k = 0; k < M; ++k) v -= P[k * M + i] * Un[k * M + c];
+                    }
+                    for (int k = i + 1; k < M; ++k) v -= D[k * M + i] * U[r * MM + int64_t(k) * M + c];
+                    U[r * MM + int64_t(i) * M + c] = v / D[i * M + i];
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+
+int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
+                   const std::vector<double> &d, double *V0, double *V1, double *V2, double *U,
+                   const Ctrl *ctrl, cudaStream_t s) {
+    const size_t bytes = sizeof(double) * size_t(m) * M * M;
+    prof_begin(KernelClass::PROJECTED, s);
+    KB_CUDA_TRY(cudaMemsetAsync(V0, 0, bytes, s));
+    KB_CUDA_TRY(cudaMemsetAsync(V1, 0, bytes, s));
+    KB_CUDA_TRY(cudaMemsetAsync(V2, 0, bytes, s));
+    KB_CUDA_TRY(cudaMemsetAsync(U, 0, bytes, s));
+    k_cheb_bt_seed<<<(M + 127) / 128, 128, 0, s>>>(V0, U, M, d[0]);
+    const size_t smem = sizeof(double) * 3 * M * TC;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_cheb_bt_iter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(double) * 3 * 128 * TC));
+        attr = true;
+    }
+    double *pp = V2, *pc = V0, *pn = V1;
+    const double g = 2.0 / lam;
+    for (size_t j = 0; j + 1 < d.size(); ++j) {
+        const int nrb = std::min<int>(int(j) + 2, m);
+        dim3 grid(nrb, (M + TC - 1) / TC);
+        const double beta = j == 0 ? 1.0 : 2.0, gamma = j == 0 ? 0.0 : 1.0;
+        k_cheb_bt_iter<<<grid, 256, smem, s>>>(Hd, Hs, pp, pc, pn, U, M, beta, gamma, d[j + 1], g, ctrl);
+        double *t = pp; pp = pc; pc = pn; pn = t;
+    }
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::PROJECTED, s, 0, 0, int(d.size()));
+    return 0;
+}
+
+int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double eps, int s_int,
+                     double *Ld, double *Ls, double *Yw, double *U, const Ctrl *ctrl,
+                     cudaStream_t s) {
+    (void)m;
+    prof_begin(KernelClass::PROJECTED, s);
+    k_bt_spline<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, s_int, Ld, Ls, Yw, U, ctrl);
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::PROJECTED, s, 0, 0);
+    return 0;
+}
+
+}  // namespace kb

@@ -1,0 +1,367 @@
+// Tall-skinny block kernels of the classical block Lanczos step (Algorithm 1, lines 4-6)
+// and of its final assembly (line 9): products of n x W blocks with W x W matrices and
+// Gram matrices A^T B of n x W blocks.
+//
+// One CTA of 256 threads owns a tile of TR = 4096/W consecutive rows (16 KB of FP32) at
+// a time and walks tiles with a persistent grid-stride loop.  Products are K-chunked:
+// 16 columns of the left operand are staged transposed in shared memory next to 16 rows
+// of the small matrix, and each thread accumulates a 4 x 4 register tile.  The resulting
+// tile is written to HBM and kept in shared memory, where each thread adds its
+// (W/16) x (W/16) share of the tile's Gram contribution.  In the FP32 path the Gram is
+// accumulated in two levels (per tile, then across tiles) to keep the rounding growth of
+// long sums small; each CTA writes its partial Gram, and the partials are summed in FP64
+// by k_reduce in a fixed order (deterministic).
+#include "kb_internal.cuh"
+
+#include <algorithm>
+
+namespace kb {
+namespace {
+
+constexpr int RB_THREADS = 256;
+constexpr int KC = 16;
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T *p, T (&v)[4]);
+template <>
+__device__ __forceinline__ void ld4<float>(const float *p, float (&v)[4]) {
+    float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(const double *p, double (&v)[4]) {
+    double2 a = reinterpret_cast<const double2 *>(p)[0];
+    double2 b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T *p, const T (&v)[4]);
+template <>
+__device__ __forceinline__ void st4<float>(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st4<double>(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+template <typename T, int W>
+struct Geo {
+    static constexpr int TR = 4096 / W;     // rows per tile
+    static constexpr int CG = W / 4;        // float4 column groups
+    static constexpr int GR = W / 16;       // Gram sub-block edge per thread
+    static constexpr int LDA = TR + 4;      // transposed A chunk row stride
+    static constexpr int LDO = W + 4;       // out tile row stride
+    static constexpr size_t smem_a = sizeof(T) * KC * LDA;
+    static constexpr size_t smem_c = sizeof(T) * KC * W;
+    static constexpr size_t smem_o = sizeof(T) * TR * LDO;
+    static constexpr size_t smem = smem_a + smem_c + 2 * smem_o;
+};
+
+template <typename T, int W, int MODE>
+__global__ void __launch_bounds__(RB_THREADS)
+k_rowblock(RowArgs<T> a) {
+    using G = Geo<T, W>;
+    constexpr int TR = G::TR, CG = G::CG, GR = G::GR;
+    constexpr bool PROD = MODE != RB_PROJ;
+    constexpr bool GRAM = MODE == RB_PROJ || MODE == RB_UPD || MODE == RB_MULGRAM;
+    constexpr bool TWO = sizeof(T) == 4;
+    if (MODE != RB_ASM && a.ctrl && a.ctrl->stop) return;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sA = reinterpret_cast<T *>(smem_raw);                      // [KC][LDA]
+    T *sC = reinterpret_cast<T *>(smem_raw + G::smem_a);          // [KC][W]
+    T *sO = reinterpret_cast<T *>(smem_raw + G::smem_a + G::smem_c);            // [TR][LDO]
+    T *sQ = reinterpret_cast<T *>(smem_raw + G::smem_a + G::smem_c + G::smem_o);  // [TR][LDO]
+
+    const int tid = threadIdx.x;
+    const int col4 = (tid % CG) * 4;
+    const int row0 = (tid / CG) * 4;
+    const int gi0 = (tid / 16) * GR;
+    const int gj0 = (tid % 16) * GR;
+
+    // number of K blocks (of width W) of the product
+    int nkb = 1;
+    if (MODE == RB_UPD) nkb = a.qa ? 2 : 1;
+    if (MODE == RB_ASM) nkb = a.ctrl ? min(a.ctrl->steps, a.nblk) : a.nblk;
+
+    T g1[GR][GR], g2[GR][GR];
+#pragma unroll
+    for (int i = 0; i < GR; ++i)
+#pragma unroll
+        for (int j = 0; j < GR; ++j) { g1[i][j] = 0; g2[i][j] = 0; }
+
+    const int64_t ntiles = (a.n + TR - 1) / TR;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * TR;
+        if constexpr (PROD) {
+            T acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const T *src;
+                const T *cmat;
+                if (MODE == RB_UPD) {
+                    src = (a.qa && kb == 0) ? a.qa : a.qb;
+                    cmat = (a.qa && kb == 0) ? a.ca : a.cb;
+                } else if (MODE == RB_ASM) {
+                    src = a.basis + int64_t(kb) * a.block_stride;
+                    cmat = a.ca + int64_t(kb) * W * W;
+                } else {
+                    src = a.x;
+                    cmat = a.ca;
+                }
+                for (int k0 = 0; k0 < W; k0 += KC) {
+                    // stage A[r0:r0+TR, k0:k0+KC] transposed and C[k0:k0+KC, :]
+                    for (int idx = tid; idx < TR * (KC / 4); idx += RB_THREADS) {
+                        const int r = idx / (KC / 4);
+                        const int kq = (idx % (KC / 4)) * 4;
+                        T v[4] = {0, 0, 0, 0};
+                        if (r0 + r < a.n) ld4<T>(src + (r0 + r) * W + k0 + kq, v);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) sA[(kq + q) * G::LDA + r] = v[q];
+                    }
+                    for (int idx = tid; idx < KC * CG; idx += RB_THREADS) {
+                        const int kr = idx / CG;
+                        const int c = (idx % CG) * 4;
+                        T v[4];
+                        ld4<T>(cmat + (k0 + kr) * W + c, v);
+                        st4<T>(sC + kr * W + c, v);
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int k = 0; k < KC; ++k) {
+                        T av[4], cv[4];
+                        ld4<T>(sA + k * G::LDA + row0, av);
+                        ld4<T>(sC + k * W + col4, cv);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], cv[q], acc[r][q]);
+                    }
+                    __syncthreads();
+                }
+            }
+            // finish the tile
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int64_t row = r0 + row0 + r;
+                T o[4];
+                if (MODE == RB_UPD) {
+                    T xv[4] = {0, 0, 0, 0};
+                    if (row < a.n) ld4<T>(a.x + row * W + col4, xv);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) o[q] = xv[q] - acc[r][q];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) o[q] = acc[r][q];
+                }
+                if (row < a.n) {
+                    if (MODE == RB_ASM) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (col4 + q < a.mo) a.y[row * a.ldy + col4 + q] = float(o[q]);
+                    } else {
+                        st4<T>(a.out + row * W + col4, o);
+                    }
+                }
+                if (GRAM) st4<T>(sO + (row0 + r) * G::LDO + col4, o);
+            }
+        } else {
+            // PROJ: stage X and Qa tiles
+            for (int idx = tid; idx < TR * CG; idx += RB_THREADS) {
+                const int r = idx / CG;
+                const int c = (idx % CG) * 4;
+                T xv[4] = {0, 0, 0, 0}, qv[4] = {0, 0, 0, 0};
+                if (r0 + r < a.n) {
+                    ld4<T>(a.x + (r0 + r) * W + c, xv);
+                    ld4<T>(a.qa + (r0 + r) * W + c, qv);
+                }
+                st4<T>(sO + r * G::LDO + c, xv);
+                st4<T>(sQ + r * G::LDO + c, qv);
+            }
+        }
+        if constexpr (GRAM) {
+            __syncthreads();
+            const T *left = (MODE == RB_PROJ) ? sQ : sO;
+            for (int r = 0; r < TR; ++r) {
+                T av[GR], bv[GR];
+                if constexpr (GR >= 4) {
+#pragma unroll
+                    for (int q = 0; q < GR; q += 4) {
+                        T t4[4];
+                        ld4<T>(left + r * G::LDO + gi0 + q, t4);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) av[q + u] = t4[u];
+                        ld4<T>(sO + r * G::LDO + gj0 + q, t4);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) bv[q + u] = t4[u];
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < GR; ++q) {
+                        av[q] = left[r * G::LDO + gi0 + q];
+                        bv[q] = sO[r * G::LDO + gj0 + q];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < GR; ++i)
+#pragma unroll
+                    for (int j = 0; j < GR; ++j) {
+                        if (TWO) g1[i][j] = fma(av[i], bv[j], g1[i][j]);
+                        else g2[i][j] = fma(av[i], bv[j], g2[i][j]);
+                    }
+            }
+            if (TWO) {
+#pragma unroll
+                for (int i = 0; i < GR; ++i)
+#pragma unroll
+                    for (int j = 0; j < GR; ++j) { g2[i][j] += g1[i][j]; g1[i][j] = 0; }
+            }
+            __syncthreads();
+        }
+    }
+    if constexpr (GRAM) {
+        T *p = a.partials + int64_t(blockIdx.x) * W * W;
+#pragma unroll
+        for (int i = 0; i < GR; ++i)
+#pragma unroll
+            for (int j = 0; j < GR; ++j) p[(gi0 + i) * W + gj0 + j] = g2[i][j];
+    }
+}
+
+template <typename T, int W, int MODE>
+int occupancy() {
+    using G = Geo<T, W>;
+    static int cached = -1;
+    if (cached < 0) {
+        cudaFuncSetAttribute(k_rowblock<T, W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(G::smem));
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowblock<T, W, MODE>, RB_THREADS,
+                                                      G::smem);
+        cached = std::max(per_sm, 1);
+    }
+    return cached;
+}
+
+template <typename T, int W, int MODE>
+int launch_wm(const RowArgs<T> &a, cudaStream_t s, int *grid_out) {
+    using G = Geo<T, W>;
+    const int per_sm = occupancy<T, W, MODE>();
+    const int64_t ntiles = (a.n + G::TR - 1) / G::TR;
+    int grid = int(std::min<int64_t>(ntiles, int64_t(num_sms()) * per_sm));
+    if (grid < 1) grid = 1;
+    if (grid_out) *grid_out = grid;
+    k_rowblock<T, W, MODE><<<grid, RB_THREADS, G::smem, s>>>(a);
+    return 0;
+}
+
+template <typename T, int W>
+int launch_w(int mode, const RowArgs<T> &a, cudaStream_t s, int *grid_out) {
+    switch (mode) {
+        case RB_PROJ: return launch_wm<T, W, RB_PROJ>(a, s, grid_out);
+        case RB_UPD: return launch_wm<T, W, RB_UPD>(a, s, grid_out);
+        case RB_MULGRAM: return launch_wm<T, W, RB_MULGRAM>(a, s, grid_out);
+        case RB_MUL: return launch_wm<T, W, RB_MUL>(a, s, grid_out);
+        case RB_ASM: return launch_wm<T, W, RB_ASM>(a, s, grid_out);
+    }
+    return fail(KB_ERR_ARG, "bad row-block mode");
+}
+
+template <typename T, int W>
+int max_grid_w() {
+    return num_sms() * std::max({occupancy<T, W, RB_PROJ>(), occupancy<T, W, RB_UPD>(),
+                                 occupancy<T, W, RB_MULGRAM>(), occupancy<T, W, RB_MUL>()});
+}
+
+// ---------------------------------------------------------------- deterministic reduction
+template <typename P>
+__global__ void __launch_bounds__(256) k_reduce(const P *__restrict__ parts, int nparts, int len,
+                                                 double *__restrict__ out, const Ctrl *ctrl) {
+    if (ctrl && ctrl->stop) return;
+    __shared__ double s[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    double acc = 0.0;
+    if (e < len)
+        for (int p = warp; p < nparts; p += 8) acc += double(parts[int64_t(p) * len + e]);
+    s[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && e < len) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += s[w][lane];
+        out[e] = t;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *grid_out,
+                    int64_t M_alg) {
+    if (sizeof(T) == 8 && W > 64) return fail(KB_ERR_UNSUPPORTED, "FP64 blocks wider than 64");
+    const int cls = mode == RB_ASM ? KernelClass::ASSEMBLE : KernelClass::ROWBLOCK;
+    prof_begin(cls, s);
+    int rc = 0;
+    switch (W) {
+        case 16: rc = launch_w<T, 16>(mode, a, s, grid_out); break;
+        case 32: rc = launch_w<T, 32>(mode, a, s, grid_out); break;
+        case 64: rc = launch_w<T, 64>(mode, a, s, grid_out); break;
+        case 128:
+            if constexpr (sizeof(T) == 4) { rc = launch_w<T, 128>(mode, a, s, grid_out); break; }
+            [[fallthrough]];
+        default: return fail(KB_ERR_ARG, "unsupported block width");
+    }
+    if (rc) return rc;
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "k_rowblock launch");
+    const double blk = double(a.n) * double(M_alg) * sizeof(T);
+    double bytes = 0, flops = 0;
+    const double mm = double(a.n) * double(M_alg) * double(M_alg) * 2.0;
+    switch (mode) {
+        case RB_PROJ: bytes = 2 * blk; flops = mm; break;
+        case RB_UPD: bytes = (a.qa ? 4 : 3) * blk; flops = (a.qa ? 3 : 2) * mm; break;
+        case RB_MULGRAM: bytes = 2 * blk; flops = 2 * mm; break;
+        case RB_MUL: bytes = 2 * blk; flops = mm; break;
+        case RB_ASM: bytes = (a.nblk + 1) * blk; flops = a.nblk * mm; break;
+    }
+    prof_end(cls, s, bytes, flops);
+    return 0;
+}
+
+template <typename T>
+int rowblock_max_grid(int W) {
+    switch (W) {
+        case 16: return max_grid_w<T, 16>();
+        case 32: return max_grid_w<T, 32>();
+        case 64: return max_grid_w<T, 64>();
+        default:
+            if constexpr (sizeof(T) == 4) return max_grid_w<T, 128>();
+            return 0;
+    }
+}
+
+template <typename P>
+int launch_reduce(const P *parts, int nparts, int len, double *out, cudaStream_t s,
+                  const Ctrl *ctrl) {
+    prof_begin(KernelClass::REDUCE, s);
+    k_reduce<P><<<(len + 31) / 32, 256, 0, s>>>(parts, nparts, len, out, ctrl);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "k_reduce launch");
+    prof_end(KernelClass::REDUCE, s, double(nparts) * len * sizeof(P), 0);
+    return 0;
+}
+
+template int launch_rowblock<float>(int, int, const RowArgs<float> &, cudaStream_t, int *, int64_t);
+template int launch_rowblock<double>(int, int, const RowArgs<double> &, cudaStream_t, int *, int64_t);
+template int rowblock_max_grid<float>(int);
+template int rowblock_max_grid<double>(int);
+template int launch_reduce<float>(const float *, int, int, double *, cudaStream_t, const Ctrl *);
+template int launch_reduce<double>(const double *, int, int, double *, cudaStream_t, const Ctrl *);
+
+}  // namespace kb

@@ -1,0 +1,592 @@
+// Small dense FP64 kernels and element-wise kernels of the Krylov drivers.
+//
+//  * k_hkk          symmetrised diagonal block H_kk (Algorithm 1, line 4).
+//  * k_chol         reduced QR of the new block by CholeskyQR, FP64 Cholesky factor and its
+//                   inverse (Algorithm 1, line 6); the second pass forms H_{k+1,k} = R2 R1
+//                   and the transposed block used by the next three-term step (line 7,
+//                   reading A1).  Invariant subspaces stop the process, rank-deficient
+//                   blocks report a breakdown (reading A6).
+//  * k_lanczos_*    scalar recurrences of the global (Algorithm 2) and sequential
+//                   (Section 3.3) Lanczos methods: h_kk, h_{k+1,k}, 1/h.
+//  * k_tridiag_phi  u = phi(H_m) f_1 for the tridiagonal Lanczos matrices (Algorithm 2,
+//                   line 8; Section 3.3 with phi applied, reading A2).
+//  * element-wise   unit blocks E_W, node markers, column norms, scaled copies, the
+//                   diagonal assembly sum_k u_k Q_k, NaN fill on breakdown.
+#include "kb_internal.cuh"
+#include "kb_kernels.cuh"
+
+namespace kb {
+
+// ---------------------------------------------------------------- control / init
+__global__ void k_ctrl_init(Ctrl *c, int steps) {
+    c->status = KB_OK;
+    c->stop = 0;
+    c->steps = steps;
+    c->breakdown_step = -1;
+}
+
+template <typename T>
+__global__ void k_scatter(T *block, int64_t ld, NodeChunk ch, T val) {
+    const int j = threadIdx.x + blockIdx.x * blockDim.x;
+    if (j < ch.cnt) block[int64_t(ch.idx[j]) * ld + ch.col0 + j] = val;
+}
+
+__global__ void k_marker(int32_t *marker, NodeChunk ch) {
+    const int j = threadIdx.x + blockIdx.x * blockDim.x;
+    if (j < ch.cnt) marker[ch.idx[j]] = ch.col0 + j;
+}
+
+template <typename T>
+__global__ void k_scale_copy(T *out, const T *in, int64_t count, double scale) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = T(scale * double(in[i]));
+}
+
+__global__ void k_fill_nan(float *Y, int64_t n, int64_t ldy, int mo, const Ctrl *ctrl) {
+    if (ctrl->status == KB_OK) return;
+    const float nanv = __int_as_float(0x7fc00000);
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n * mo;
+         i += int64_t(gridDim.x) * blockDim.x)
+        Y[(i / mo) * ldy + (i % mo)] = nanv;
+}
+
+// ---------------------------------------------------------------- cbl small kernels
+template <typename T>
+__global__ void k_hkk(const double *G, int M, int W, double *Hd, T *C, const Ctrl *ctrl) {
+    if (ctrl->stop) return;
+    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+        const int i = idx / W, j = idx % W;
+        double v = 0.0;
+        if (i < M && j < M) {
+            v = 0.5 * (G[i * W + j] + G[j * W + i]);
+            Hd[i * M + j] = v;
+        }
+        C[idx] = T(v);
+    }
+}
+
+// Cholesky G = R^T R (upper R) of the leading M x M block in shared memory, then R^{-1}.
+template <typename T>
+__global__ void k_chol(const double *G, int M, int W, int pass, int step, double inv_thresh2,
+                       double piv_rel2, double *R1, double *Rinv64, T *Rinv, double *Hs, T *Bout,
+                       Ctrl *ctrl) {
+    if (ctrl->stop) return;
+    extern __shared__ double A[];   // [M][M+1]
+    __shared__ int bad;
+    __shared__ double maxdiag;
+    const int lda = M + 1;
+    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+        const int i = idx / M, j = idx % M;
+        A[i * lda + j] = G[i * W + j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tr = 0.0, mx = 0.0;
+        for (int i = 0; i < M; ++i) { tr += A[i * lda + i]; mx = fmax(mx, A[i * lda + i]); }
+        maxdiag = mx;
+        bad = 0;
+        if (pass == 1 && !(tr > inv_thresh2)) {
+            // X vanished: the block Krylov space is invariant; keep the blocks so far
+            ctrl->stop = 1;
+            ctrl->steps = step;
+            bad = 2;
+        }
+    }
+    __syncthreads();
+    if (bad) return;
+    for (int j = 0; j < M; ++j) {
+        if (threadIdx.x == 0) {
+            const double d = A[j * lda + j];
+            if (!(d > piv_rel2 * maxdiag)) {
+                bad = 1;
+                ctrl->status = KB_ERR_BREAKDOWN;
+                ctrl->stop = 1;
+                ctrl->steps = step;
+                ctrl->breakdown_step = step;
+            } else {
+                A[j * lda + j] = sqrt(d);
+            }
+        }
+        __syncthreads();
+        if (bad) return;
+        const double r = A[j * lda + j];
+        for (int c = j + 1 + threadIdx.x; c < M; c += blockDim.x) A[j * lda + c] /= r;
+        __syncthreads();
+        const int L = M - j - 1;
+        for (int idx = threadIdx.x; idx < L * L; idx += blockDim.x) {
+            const int a = j + 1 + idx / L, b = j + 1 + idx % L;
+            if (b >= a) A[a * lda + b] -= A[j * lda + a] * A[j * lda + b];
+        }
+        __syncthreads();
+    }
+    // R^{-1}: column c by back substitution (thread c)
+    for (int c = threadIdx.x; c < M; c += blockDim.x) {
+        Rinv64[c * W + c] = 1.0 / A[c * lda + c];
+        for (int i = c - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int j = i + 1; j <= c; ++j) s += A[i * lda + j] * Rinv64[j * W + c];
+            Rinv64[i * W + c] = -s / A[i * lda + i];
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+        const int i = idx / W, j = idx % W;
+        Rinv[idx] = (i < M && j < M && j >= i) ? T(Rinv64[idx]) : T(0);
+    }
+    if (pass == 1) {
+        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+            const int i = idx / M, j = idx % M;
+            R1[idx] = (j >= i) ? A[i * lda + j] : 0.0;
+        }
+    } else {
+        // H_{k+1,k} = R2 R1 (upper triangular); B = H^T for the next three-term step
+        for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+            const int i = idx / W, j = idx % W;
+            double h = 0.0;
+            if (i < M && j < M && j >= i) {
+                for (int k = i; k <= j; ++k) h += A[i * lda + k] * R1[k * M + j];
+            }
+            if (i < M && j < M) Hs[i * M + j] = h;
+            Bout[j * W + i] = T(h);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- gbl / sbl scalars
+// Reduce [nparts][W] partials per column (fixed order) into s[W].
+__device__ void reduce_cols(const double *parts, int nparts, int W, double *s) {
+    __shared__ double tmp[8][128];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c0 = 0; c0 < W; c0 += 32) {
+        const int c = c0 + lane;
+        double acc = 0.0;
+        if (c < W)
+            for (int p = warp; p < nparts; p += 8) acc += parts[int64_t(p) * W + c];
+        if (c < W) tmp[warp][c] = acc;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += tmp[w][c];
+        s[c] = t;
+    }
+    __syncthreads();
+}
+
+__global__ void k_lanczos_init(int W, int M, int gbl, double *sigma, int32_t *alive, float *c1,
+                               float *c2) {
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+        const bool live = c < M;
+        const double s0 = live ? (gbl ? 1.0 / sqrt(double(M)) : 1.0) : 0.0;
+        sigma[c] = s0;
+        alive[c] = live ? 1 : 0;
+        c1[c] = float(s0);
+        c2[c] = 0.f;
+    }
+}
+
+// alpha_k = <Q_k, X> (gbl: Frobenius, sbl: per column) from SpMM dot partials of P_k . X
+__global__ void k_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k,
+                                const double *sigma, double *alpha, float *a_upd, const Ctrl *ctrl) {
+    if (ctrl->stop) return;
+    __shared__ double s[128];
+    reduce_cols(parts, nparts, W, s);
+    const double *sg = sigma + int64_t(k) * W;
+    if (gbl) {
+        __shared__ double tot;
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int c = 0; c < M; ++c) t += s[c];
+            tot = sg[0] * t;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < W; c += blockDim.x) {
+            alpha[int64_t(k) * W + c] = c < M ? tot : 0.0;
+            a_upd[c] = c < M ? float(tot * sg[0]) : 0.f;
+        }
+    } else {
+        for (int c = threadIdx.x; c < W; c += blockDim.x) {
+            const double al = c < M ? sg[c] * s[c] : 0.0;
+            alpha[int64_t(k) * W + c] = al;
+            a_upd[c] = float(al * sg[c]);
+        }
+    }
+}
+
+// beta_{k+1} = ||X|| (gbl: Frobenius, sbl: per column), sigma_{k+1} = 1/beta, and the
+// SpMM coefficients of the next step: X = sigma_{k+1} L P_{k+1} - beta_{k+1} sigma_k P_k.
+__global__ void k_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, int k,
+                               double thresh, double *beta, double *sigma, int32_t *alive, float *c1,
+                               float *c2, Ctrl *ctrl) {
+    if (ctrl->stop) return;
+    __shared__ double s[128];
+    reduce_cols(parts, nparts, W, s);
+    const double *sk = sigma + int64_t(k) * W;
+    double *sn = sigma + int64_t(k + 1) * W;
+    double *bn = beta + int64_t(k + 1) * W;
+    if (gbl) {
+        __shared__ double b;
+        __shared__ int stop;
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int c = 0; c < M; ++c) t += s[c];
+            b = sqrt(t);
+            stop = !(b > thresh);
+            if (stop) { ctrl->stop = 1; ctrl->steps = k + 1; }
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < W; c += blockDim.x) {
+            const bool live = c < M && !stop;
+            bn[c] = live ? b : 0.0;
+            sn[c] = live ? 1.0 / b : 0.0;
+            c1[c] = live ? float(1.0 / b) : 0.f;
+            c2[c] = live ? float(-b * sk[c]) : 0.f;
+        }
+    } else {
+        for (int c = threadIdx.x; c < W; c += blockDim.x) {
+            const double b = sqrt(s[c]);
+            const bool live = c < M && alive[c] && (b > thresh);
+            if (!live) alive[c] = 0;
+            bn[c] = live ? b : 0.0;
+            sn[c] = live ? 1.0 / b : 0.0;
+            c1[c] = live ? float(1.0 / b) : 0.f;
+            c2[c] = live ? float(-b * sk[c]) : 0.f;
+        }
+    }
+}
+
+// u = phi(T) e_1 for each column's tridiagonal T (diag alpha_k, off-diagonal beta_{k+1}),
+// then assembly weights omega_k[c] = scale * u_k * sigma_k[c].
+//   exp:    Chebyshev series of e^{-t lambda} on [0, Lambda] in T_j(I - 2T/Lambda)
+//   spline: s_int solves with the SPD tridiagonal eps I + T (Thomas algorithm)
+__global__ void k_tridiag_phi(int W, int M, int m, int gbl, const double *alpha,
+                              const double *beta, const double *sigma, int phi_kind,
+                              double eps, int s_int, double lam, ChebCoef cc, float *omega,
+                              double *work, const Ctrl *ctrl) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ncol = gbl ? 1 : M;
+    if (c >= W) return;
+    const int steps = gbl ? ctrl->steps : m;
+    if (c >= ncol) {
+        if (!gbl || c >= M)
+            for (int k = 0; k < m; ++k) omega[int64_t(k) * W + c] = 0.f;
+        return;
+    }
+    // per-thread work vectors in global scratch: 4 vectors of length m
+    double *v0 = work + int64_t(c) * 4 * m;
+    double *v1 = v0 + m, *v2 = v1 + m, *u = v2 + m;
+    auto a_of = [&](int k) { return alpha[int64_t(k) * W + c]; };
+    auto b_of = [&](int k) { return beta[int64_t(k) * W + c]; };   // couples k-1 and k
+    const int s = steps;
+    for (int k = 0; k < s; ++k) { v0[k] = 0.0; v1[k] = 0.0; v2[k] = 0.0; u[k] = 0.0; }
+    if (phi_kind == KB_PHI_EXP) {
+        // v0 = e_1, v1 = A e_1, v_{j+1} = 2 A v_j - v_{j-1}, A = I - (2/lam) T
+        const double g = 2.0 / lam;
+        v0[0] = 1.0;
+        u[0] = cc.d[0];
+        double *pp = v0, *pc = v1, *pn = v2;
+        // pc = A pp
+        for (int k = 0; k < s; ++k) {
+            double tv = a_of(k) * pp[k];
+            if (k > 0) tv += b_of(k) * pp[k - 1];
+            if (k + 1 < s) tv += b_of(k + 1) * pp[k + 1];
+            pc[k] = pp[k] - g * tv;
+            u[k] += cc.d[1] * pc[k];
+        }
+        for (int j = 2; j < cc.n; ++j) {
+            for (int k = 0; k < s; ++k) {
+                double tv = a_of(k) * pc[k];
+                if (k > 0) tv += b_of(k) * pc[k - 1];
+                if (k + 1 < s) tv += b_of(k + 1) * pc[k + 1];
+                pn[k] = 2.0 * (pc[k] - g * tv) - pp[k];
+                u[k] += cc.d[j] * pn[k];
+            }
+            double *t = pp; pp = pc; pc = pn; pn = t;
+        }
+    } else {
+        // Thomas algorithm for (eps I + T) x = rhs, repeated s_int times from rhs = e_1
+        u[0] = 1.0;
+        for (int rep = 0; rep < s_int; ++rep) {
+            // forward elimination: v0 = modified super-diagonal, v1 = modified rhs
+            double den = eps + a_of(0);
+            v0[0] = (s > 1) ? b_of(1) / den : 0.0;
+            v1[0] = u[0] / den;
+            for (int k = 1; k < s; ++k) {
+                den = eps + a_of(k) - b_of(k) * v0[k - 1];
+                v0[k] = (k + 1 < s) ? b_of(k + 1) / den : 0.0;
+                v1[k] = (u[k] - b_of(k) * v1[k - 1]) / den;
+            }
+            u[s - 1] = v1[s - 1];
+            for (int k = s - 2; k >= 0; --k) u[k] = v1[k] - v0[k] * u[k + 1];
+        }
+    }
+    const double scale = gbl ? sqrt(double(M)) : 1.0;
+    for (int k = 0; k < m; ++k) {
+        float om = 0.f;
+        if (k < s) om = float(scale * u[k] * sigma[int64_t(k) * W + c]);
+        if (gbl) {
+            for (int cc2 = 0; cc2 < W; ++cc2)
+                omega[int64_t(k) * W + cc2] = cc2 < M ? om : 0.f;
+        } else {
+            omega[int64_t(k) * W + c] = om;
+        }
+    }
+}
+
+// X[:, c] -= a[c] * P[:, c]; partial column sums of X^2 per CTA
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const float *a, int64_t n,
+                                                       double *parts, const Ctrl *ctrl) {
+    if (ctrl->stop) return;
+    constexpr int CG = W / 4;
+    constexpr int RPP = 256 / CG;   // rows per pass
+    __shared__ double s[RPP][W];
+    const int cg = threadIdx.x % CG, rr = threadIdx.x / CG;
+    const int c4 = cg * 4;
+    float av[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) av[q] = a[c4 + q];
+    float acc[4] = {0, 0, 0, 0};
+    for (int64_t row = int64_t(blockIdx.x) * RPP + rr; row < n; row += int64_t(gridDim.x) * RPP) {
+        T *xp = X + row * W + c4;
+        const T *pp = P + row * W + c4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const T v = xp[q] - T(av[q]) * pp[q];
+            xp[q] = v;
+            acc[q] += float(v) * float(v);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s[rr][c4 + q] = acc[q];
+    __syncthreads();
+    for (int c = threadIdx.x; c < W; c += 256) {
+        double t = 0.0;
+        for (int r = 0; r < RPP; ++r) t += s[r][c];
+        parts[int64_t(blockIdx.x) * W + c] = t;
+    }
+}
+
+// Y[i, c] = sum_k omega_k[c] P_k[i, c]  (global / sequential Lanczos assembly)
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_assemble_diag(const T *basis, int64_t stride, int nblk,
+                                                        const float *omega, int64_t n, float *Y,
+                                                        int64_t ldy, int mo) {
+    constexpr int CG = W / 4;
+    constexpr int RPP = 256 / CG;
+    const int cg = threadIdx.x % CG, rr = threadIdx.x / CG;
+    const int c4 = cg * 4;
+    for (int64_t row = int64_t(blockIdx.x) * RPP + rr; row < n; row += int64_t(gridDim.x) * RPP) {
+        float acc[4] = {0, 0, 0, 0};
+        for (int k = 0; k < nblk; ++k) {
+            const T *p = basis + int64_t(k) * stride + row * W + c4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fmaf(__ldg(omega + int64_t(k) * W + c4 + q), float(p[q]), acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (c4 + q < mo) Y[row * ldy + c4 + q] = acc[q];
+    }
+}
+
+template <typename T>
+__global__ void k_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ctrl) {
+    // U: (steps*M) x M row-major -> Ut: (m*W) x W, zero padded, zero beyond steps
+    const int steps = ctrl->steps;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < int64_t(m) * W * W;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int blk = int(idx / (W * W));
+        const int i = int((idx / W) % W), j = int(idx % W);
+        double v = 0.0;
+        if (blk < steps && i < M && j < M) v = U[(int64_t(blk) * M + i) * M + j];
+        Ut[idx] = T(v);
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+int launch_ctrl_init(Ctrl *c, int steps, cudaStream_t s) {
+    k_ctrl_init<<<1, 1, 0, s>>>(c, steps);
+    count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : cuda_fail(cudaGetLastError(), "k_ctrl_init");
+}
+
+template <typename T>
+int launch_scatter(T *block, int64_t ld, const int32_t *nodes, int M, int col0, T val, cudaStream_t s) {
+    for (int j0 = 0; j0 < M; j0 += NodeChunk::CAP) {
+        NodeChunk ch;
+        ch.cnt = std::min(NodeChunk::CAP, M - j0);
+        ch.col0 = col0 + j0;
+        for (int j = 0; j < ch.cnt; ++j) ch.idx[j] = nodes[j0 + j];
+        k_scatter<T><<<1, NodeChunk::CAP, 0, s>>>(block, ld, ch, val);
+        count_launches(1);
+    }
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int launch_marker(int32_t *marker, const int32_t *nodes, int M, cudaStream_t s) {
+    for (int j0 = 0; j0 < M; j0 += NodeChunk::CAP) {
+        NodeChunk ch;
+        ch.cnt = std::min(NodeChunk::CAP, M - j0);
+        ch.col0 = j0;
+        for (int j = 0; j < ch.cnt; ++j) ch.idx[j] = nodes[j0 + j];
+        k_marker<<<1, NodeChunk::CAP, 0, s>>>(marker, ch);
+        count_launches(1);
+    }
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+template <typename T>
+int launch_scale_copy(T *out, const T *in, int64_t count, double scale, cudaStream_t s) {
+    const int grid = int(std::min<int64_t>((count + 255) / 256, int64_t(num_sms()) * 8));
+    k_scale_copy<T><<<std::max(grid, 1), 256, 0, s>>>(out, in, count, scale);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int launch_fill_nan(float *Y, int64_t n, int64_t ldy, int mo, const Ctrl *ctrl, cudaStream_t s) {
+    const int grid = int(std::min<int64_t>((n * mo + 255) / 256, int64_t(num_sms()) * 8));
+    k_fill_nan<<<std::max(grid, 1), 256, 0, s>>>(Y, n, ldy, mo, ctrl);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+template <typename T>
+int launch_hkk(const double *G, int M, int W, double *Hd, T *C, const Ctrl *ctrl, cudaStream_t s) {
+    prof_begin(KernelClass::SMALL, s);
+    k_hkk<T><<<1, 256, 0, s>>>(G, M, W, Hd, C, ctrl);
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::SMALL, s, 0, 0);
+    return 0;
+}
+
+template <typename T>
+int launch_chol(const double *G, int M, int W, int pass, int step, double inv_thresh2,
+                double piv_rel2, double *R1, double *Rinv64, T *Rinv, double *Hs, T *Bout,
+                Ctrl *ctrl, cudaStream_t s) {
+    const size_t smem = sizeof(double) * size_t(M) * (M + 1);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(double) * 128 * 129));
+        attr = true;
+    }
+    prof_begin(KernelClass::SMALL, s);
+    k_chol<T><<<1, 256, smem, s>>>(G, M, W, pass, step, inv_thresh2, piv_rel2, R1, Rinv64, Rinv,
+                                   Hs, Bout, ctrl);
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::SMALL, s, 0, 0);
+    return 0;
+}
+
+int launch_lanczos_init(int W, int M, int gbl, double *sigma, int32_t *alive, float *c1, float *c2,
+                        cudaStream_t s) {
+    k_lanczos_init<<<1, 128, 0, s>>>(W, M, gbl, sigma, alive, c1, c2);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int launch_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k,
+                         const double *sigma, double *alpha, float *a_upd, const Ctrl *ctrl,
+                         cudaStream_t s) {
+    prof_begin(KernelClass::SMALL, s);
+    k_lanczos_alpha<<<1, 256, 0, s>>>(parts, nparts, W, M, gbl, k, sigma, alpha, a_upd, ctrl);
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::SMALL, s, double(nparts) * W * 8, 0);
+    return 0;
+}
+
+int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, int k,
+                        double thresh, double *beta, double *sigma, int32_t *alive, float *c1,
+                        float *c2, Ctrl *ctrl, cudaStream_t s) {
+    prof_begin(KernelClass::SMALL, s);
+    k_lanczos_beta<<<1, 256, 0, s>>>(parts, nparts, W, M, gbl, k, thresh, beta, sigma, alive, c1,
+                                     c2, ctrl);
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::SMALL, s, double(nparts) * W * 8, 0);
+    return 0;
+}
+
+int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const double *beta,
+                       const double *sigma, int phi_kind, double eps, int s_int, double lam,
+                       const ChebCoef &cc, float *omega, double *work, const Ctrl *ctrl,
+                       cudaStream_t s) {
+    prof_begin(KernelClass::PROJECTED, s);
+    k_tridiag_phi<<<(W + 63) / 64, 64, 0, s>>>(W, M, m, gbl, alpha, beta, sigma, phi_kind, eps,
+                                                s_int, lam, cc, omega, work, ctrl);
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::PROJECTED, s, 0, 0);
+    return 0;
+}
+
+template <typename T>
+int launch_axpy_colnorm(int W, T *X, const T *P, const float *a, int64_t n, double *parts,
+                        int *grid_out, const Ctrl *ctrl, cudaStream_t s) {
+    const int rpp = 256 / (W / 4);
+    const int grid = int(std::min<int64_t>((n + rpp - 1) / rpp, int64_t(num_sms()) * 4));
+    *grid_out = std::max(grid, 1);
+    prof_begin(KernelClass::ROWBLOCK, s);
+    switch (W) {
+        case 16: k_axpy_colnorm<T, 16><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl); break;
+        case 32: k_axpy_colnorm<T, 32><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl); break;
+        case 64: k_axpy_colnorm<T, 64><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl); break;
+        case 128: k_axpy_colnorm<T, 128><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl); break;
+        default: return fail(KB_ERR_ARG, "bad width");
+    }
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::ROWBLOCK, s, 3.0 * double(n) * W * sizeof(T), 3.0 * double(n) * W);
+    return 0;
+}
+
+int axpy_max_grid() { return num_sms() * 4; }
+
+template <typename T>
+int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const float *omega,
+                         int64_t n, float *Y, int64_t ldy, int mo, int64_t M_alg, cudaStream_t s) {
+    const int rpp = 256 / (W / 4);
+    const int grid = std::max(1, int(std::min<int64_t>((n + rpp - 1) / rpp, int64_t(num_sms()) * 8)));
+    prof_begin(KernelClass::ASSEMBLE, s);
+    switch (W) {
+        case 16: k_assemble_diag<T, 16><<<grid, 256, 0, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo); break;
+        case 32: k_assemble_diag<T, 32><<<grid, 256, 0, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo); break;
+        case 64: k_assemble_diag<T, 64><<<grid, 256, 0, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo); break;
+        case 128: k_assemble_diag<T, 128><<<grid, 256, 0, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo); break;
+        default: return fail(KB_ERR_ARG, "bad width");
+    }
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::ASSEMBLE, s, double(nblk) * n * M_alg * sizeof(T) + double(n) * M_alg * 4,
+             2.0 * nblk * double(n) * M_alg);
+    return 0;
+}
+
+template <typename T>
+int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ctrl, cudaStream_t s) {
+    const int64_t cnt = int64_t(m) * W * W;
+    const int grid = int(std::min<int64_t>((cnt + 255) / 256, 1024));
+    k_u_convert<T><<<std::max(grid, 1), 256, 0, s>>>(U, M, W, m, Ut, ctrl);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+#define KB_INST(T)                                                                              \
+    template int launch_scatter<T>(T *, int64_t, const int32_t *, int, int, T, cudaStream_t);   \
+    template int launch_scale_copy<T>(T *, const T *, int64_t, double, cudaStream_t);           \
+    template int launch_hkk<T>(const double *, int, int, double *, T *, const Ctrl *, cudaStream_t); \
+    template int launch_chol<T>(const double *, int, int, int, int, double, double, double *,   \
+                                double *, T *, double *, T *, Ctrl *, cudaStream_t);            \
+    template int launch_axpy_colnorm<T>(int, T *, const T *, const float *, int64_t, double *,  \
+                                        int *, const Ctrl *, cudaStream_t);                     \
+    template int launch_assemble_diag<T>(int, const T *, int64_t, int, const float *, int64_t,  \
+                                         float *, int64_t, int, int64_t, cudaStream_t);         \
+    template int launch_u_convert<T>(const double *, int, int, int, T *, const Ctrl *, cudaStream_t);
+KB_INST(float)
+KB_INST(double)
+#undef KB_INST
+
+}  // namespace kb

@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: relative Frobenius error <= 1e-6 for the FP32 path and <= 1e-11 for the
+plain FP64 mode (same arithmetic up to summation order).  Inputs are seeded synthetic
+graphs shaped like the workloads: random geometric graphs of mean degree 10, 2-D grids,
+weighted Barabasi-Albert graphs, path graphs.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense, krylov
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-6
+TOL64 = 1e-11
+METHODS = ["cbl", "gbl", "sbl", "cheb", "cheb2"]
+
+
+@pytest.fixture(scope="module")
+def kb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2301_06384_gb300 import kb as _kb
+    import os
+    if not os.path.exists(_kb.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return _kb
+
+
+def _gpu(kb, G, method, phi, nodes, m, info=False, **kw):
+    import torch
+    Y, r = kb.kernel_columns(G, method, phi, nodes, m, info=True, **kw)
+    torch.cuda.synchronize()
+    out = Y.cpu().numpy().astype(np.float64)
+    return (out, r) if info else out
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _oracle(g, method, nodes, m, phi, **kw):
+    L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
+    return krylov.apply(method, L, nodes, m, phi, **kw).Y
+
+
+@pytest.fixture(scope="module")
+def rgg():
+    return synth.random_geometric_graph(20000, 10, seed=1)
+
+
+# ---------------------------------------------------------------- the small config
+def test_grid_32x32_cbl_against_oracle_and_closed_form(kb):
+    g = synth.grid_graph((32, 32))
+    nodes = synth.sample_nodes(g.n, 16, seed=1)
+    with kb.Graph.from_csr(g) as G:
+        Y, info = _gpu(kb, G, "cbl", "exp", nodes, 20, info=True, t=1.0)
+    ref = _oracle(g, "cbl", nodes, 20, "exp", t=1.0)
+    assert _rel(Y, ref) < TOL32
+    assert info["steps_done"] == 20 and info["spmm_launches"] == 20
+    exact = dense.grid_exp_columns((32, 32), nodes, 1.0)
+    assert _rel(Y, exact) < 1e-5   # approximation error of m = 20 (reported, loose)
+
+
+# ---------------------------------------------------------------- all variants, RGG
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("t", [0.5, 2.0])
+def test_rgg_exp_parity(kb, rgg, method, t):
+    nodes = synth.sample_nodes(rgg.n, 64, seed=2)
+    with kb.Graph.from_csr(rgg) as G:
+        Y, info = _gpu(kb, G, method, "exp", nodes, 30, info=True, t=t)
+    ref = _oracle(rgg, method, nodes, 30, "exp", t=t)
+    err = _rel(Y, ref)
+    print(f"{method} t={t}: rel err {err:.3e}")
+    assert err < TOL32
+    assert info["spmm_launches"] == 30
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_rgg_spline_parity(kb, rgg, method):
+    nodes = synth.sample_nodes(rgg.n, 32, seed=3)
+    with kb.Graph.from_csr(rgg) as G:
+        Y = _gpu(kb, G, method, "spline", nodes, 20, eps=0.1, s=2.0)
+    ref = _oracle(rgg, method, nodes, 20, "spline", eps=0.1, s=2.0)
+    err = _rel(Y, ref)
+    print(f"{method} spline: rel err {err:.3e}")
+    assert err < TOL32
+
+
+@pytest.mark.parametrize("method", ["cheb", "cheb2"])
+def test_chebyshev_noninteger_spline(kb, rgg, method):
+    nodes = synth.sample_nodes(rgg.n, 8, seed=4)
+    with kb.Graph.from_csr(rgg) as G:
+        Y = _gpu(kb, G, method, "spline", nodes, 24, eps=0.5, s=1.5)
+    assert _rel(Y, _oracle(rgg, method, nodes, 24, "spline", eps=0.5, s=1.5)) < TOL32
+
+
+# ---------------------------------------------------------------- widths and ragged cases
+@pytest.mark.parametrize("M", [1, 5, 13, 33, 100, 128])
+@pytest.mark.parametrize("method", METHODS)
+def test_ragged_widths(kb, method, M):
+    g = synth.random_geometric_graph(3001, 9, seed=5)
+    nodes = synth.sample_nodes(g.n, M, seed=M)
+    with kb.Graph.from_csr(g) as G:
+        Y = _gpu(kb, G, method, "exp", nodes, 12, t=0.7)
+    assert _rel(Y, _oracle(g, method, nodes, 12, "exp", t=0.7)) < TOL32
+
+
+@pytest.mark.parametrize("method", ["sbl", "cheb", "cheb2"])
+def test_wide_blocks_split_into_groups(kb, method):
+    g = synth.random_geometric_graph(4000, 9, seed=6)
+    nodes = synth.sample_nodes(g.n, 300, seed=7)
+    with kb.Graph.from_csr(g) as G:
+        Y = _gpu(kb, G, method, "exp", nodes, 10, t=1.0)
+    assert _rel(Y, _oracle(g, method, nodes, 10, "exp", t=1.0)) < TOL32
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+@pytest.mark.parametrize("method", METHODS)
+def test_few_steps(kb, method, m):
+    if method == "cheb2" and m < 2:
+        pytest.skip("cheb2 needs m >= 2")
+    g = synth.random_geometric_graph(2000, 9, seed=8)
+    nodes = synth.sample_nodes(g.n, 10, seed=9)
+    with kb.Graph.from_csr(g) as G:
+        Y = _gpu(kb, G, method, "exp", nodes, m, t=1.3)
+    assert _rel(Y, _oracle(g, method, nodes, m, "exp", t=1.3)) < TOL32
+
+
+def test_weighted_generalized_laplacian(kb):
+    # BA with float32 weights plus a positive diagonal excess: exercises the weight and
+    # diagonal-excess loads of the SpMM
+    g = synth.barabasi_albert_graph(3000, 5, seed=3, weighted=True)
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    val = g.val.copy()
+    diag = rows == g.col
+    rng = np.random.default_rng(0)
+    val[diag] = (val[diag] + rng.uniform(0, 0.5, size=g.n)).astype(np.float32)
+    g2 = synth.CSRGraph(g.n, g.rowptr, g.col, val)
+    nodes = synth.sample_nodes(g.n, 24, seed=11)
+    with kb.Graph.from_csr(g2) as G:
+        info = G.info()
+        assert not info["standard_unit"]
+        assert abs(info["lambda_max"] - krylov.gershgorin_bound(krylov.laplacian(g.n, g.rowptr, g.col, val))) < 1e-9 * info["lambda_max"]
+        for method in METHODS:
+            Y = _gpu(kb, G, method, "exp", nodes, 16, t=0.05)
+            assert _rel(Y, _oracle(g2, method, nodes, 16, "exp", t=0.05)) < TOL32, method
+
+
+# ---------------------------------------------------------------- exactness and stops
+def test_cbl_exact_at_full_dimension(kb):
+    g = synth.random_weighted_graph(12, 0.5, seed=7)
+    nodes = [0, 5, 9]
+    with kb.Graph.from_csr(g) as G:
+        Y = _gpu(kb, G, "cbl", "exp", nodes, 4, t=0.8)
+    exact = dense.kernel_columns(dense.laplacian_dense(g.n, g.rowptr, g.col, g.val), nodes,
+                                 dense.phi_function("exp", t=0.8))
+    assert _rel(Y, exact) < TOL32
+
+
+def test_invariant_subspace_stops_early(kb):
+    g = synth.from_edges(6, np.array([0, 1, 3]), np.array([1, 2, 4]))
+    nodes = [0, 1, 2]
+    exact = dense.kernel_columns(dense.laplacian_dense(g.n, g.rowptr, g.col, g.val), nodes,
+                                 dense.phi_function("exp", t=1.0))
+    with kb.Graph.from_csr(g) as G:
+        Y, info = _gpu(kb, G, "cbl", "exp", nodes, 5, info=True, t=1.0)
+        assert info["steps_done"] == 1
+        assert _rel(Y, exact) < TOL32
+        Y, info = _gpu(kb, G, "gbl", "exp", nodes, 5, info=True, t=1.0)
+        assert _rel(Y, _oracle(g, "gbl", nodes, 5, "exp", t=1.0)) < TOL32
+
+
+def test_breakdown_is_reported(kb):
+    # path 0-1-2 with W = {0, 2}: X = [-e_1, -e_1] after the projection is rank one
+    g = synth.path_graph(3)
+    with kb.Graph.from_csr(g) as G:
+        with pytest.raises(kb.KbError) as ei:
+            _gpu(kb, G, "cbl", "exp", [0, 2], 3, t=1.0)
+    assert ei.value.code == -6
+    with pytest.raises(krylov.Breakdown):
+        _oracle(g, "cbl", [0, 2], 3, "exp", t=1.0)
+
+
+def test_path_single_column_all_lanczos_agree(kb):
+    n = 201
+    g = synth.path_graph(n)
+    with kb.Graph.from_csr(g) as G:
+        outs = [_gpu(kb, G, mth, "exp", [100], 40, t=20.0) for mth in ["cbl", "gbl", "sbl"]]
+    ref = _oracle(g, "cbl", [100], 40, "exp", t=20.0)
+    for Y in outs:
+        assert _rel(Y, ref) < TOL32
+
+
+# ---------------------------------------------------------------- plain FP64 mode
+@pytest.mark.parametrize("method", METHODS)
+def test_fp64_mode_parity(kb, method):
+    g = synth.random_geometric_graph(5000, 10, seed=12)
+    nodes = synth.sample_nodes(g.n, 16, seed=13)
+    with kb.Graph.from_csr(g) as G:
+        Y = _gpu(kb, G, method, "exp", nodes, 20, t=2.0, basis="f64")
+    # the result is returned in FP32, so FP32 output rounding bounds the agreement
+    assert _rel(Y, _oracle(g, method, nodes, 20, "exp", t=2.0)) < 1e-7
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_fp64_mode_tight(kb, method):
+    # FP64 throughout: agreement far below the FP32 tolerance (result stored as FP32, so
+    # the comparison is against the FP32 rounding of the oracle)
+    g = synth.random_geometric_graph(2000, 10, seed=14)
+    nodes = synth.sample_nodes(g.n, 8, seed=15)
+    with kb.Graph.from_csr(g) as G:
+        Y = _gpu(kb, G, method, "exp", nodes, 15, t=1.0, basis="f64")
+    ref = _oracle(g, method, nodes, 15, "exp", t=1.0)
+    ref32 = ref.astype(np.float32).astype(np.float64)
+    assert _rel(Y, ref32) < 1e-8
+
+
+# ---------------------------------------------------------------- entry points and errors
+def test_host_output_matches_device_output(kb, rgg):
+    import torch
+    nodes = synth.sample_nodes(rgg.n, 20, seed=16)
+    with kb.Graph.from_csr(rgg) as G:
+        for method in METHODS:
+            Yd = _gpu(kb, G, method, "exp", nodes, 10, t=1.0)
+            Yh = torch.empty((rgg.n, 20), dtype=torch.float32).pin_memory()
+            kb.kb_krylov_apply_host(G, method, "exp", kb.make_params(t=1.0), nodes, 20, 10, Yh)
+            assert np.array_equal(Yh.numpy().astype(np.float64), Yd), method
+            Yn = np.empty((rgg.n, 20), dtype=np.float32)   # pageable host memory
+            kb.kb_krylov_apply_host(G, method, "exp", kb.make_params(t=1.0), nodes, 20, 10, Yn)
+            assert np.array_equal(Yn.astype(np.float64), Yd), method
+
+
+def test_argument_errors(kb):
+    import torch
+    g = synth.path_graph(50)
+    with kb.Graph.from_csr(g) as G:
+        Y = torch.empty((50, 4), dtype=torch.float32, device="cuda")
+        p = kb.make_params(t=1.0)
+        cases = [
+            (dict(nodes=[1, 2, 2, 3], M=4, m=5, method="cbl"), -3),
+            (dict(nodes=[1, 2, 3, 60], M=4, m=5, method="cbl"), -3),
+            (dict(nodes=[1, 2, 3, 4], M=4, m=0, method="cbl"), -1),
+            (dict(nodes=[1, 2, 3, 4], M=4, m=1, method="cheb2"), -1),
+        ]
+        for kw, code in cases:
+            with pytest.raises(kb.KbError) as ei:
+                kb.kb_krylov_apply(G, kw["method"], "exp", p, np.array(kw["nodes"]), kw["M"], kw["m"], Y)
+            assert ei.value.code == code, (kw, str(ei.value))
+        with pytest.raises(kb.KbError) as ei:
+            kb.kb_krylov_apply(G, "cbl", "spline", kb.make_params(eps=0.1, s=1.5), np.arange(4), 4, 5, Y)
+        assert ei.value.code == -7
+        with pytest.raises(kb.KbError) as ei:
+            kb.kb_krylov_apply(G, "cbl", "exp", kb.make_params(t=1.0, basis="bf16"), np.arange(4), 4, 5, Y)
+        assert ei.value.code == -7
+
+
+def test_stream_ordering_and_no_sync_without_info(kb, rgg):
+    import torch
+    nodes = synth.sample_nodes(rgg.n, 16, seed=17)
+    s = torch.cuda.Stream()
+    with kb.Graph.from_csr(rgg) as G:
+        ref = _gpu(kb, G, "cbl", "exp", nodes, 12, t=1.0)
+        with torch.cuda.stream(s):
+            Y = torch.empty((rgg.n, 16), dtype=torch.float32, device="cuda")
+            kb.kb_krylov_apply(G, "cbl", "exp", kb.make_params(t=1.0), nodes, 16, 12, Y, stream=s)
+        s.synchronize()
+        assert np.array_equal(Y.cpu().numpy().astype(np.float64), ref)
