@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="steps of the plain FP64 GPU mode timed for comparison (0 = skip)")
     ap.add_argument("--ref-sample-cols", type=int, default=4)
+    ap.add_argument("--streams", type=int, default=1,
+                    help="CUDA streams the independent solves of a step are spread over")
     return ap.parse_args()
 
 
@@ -63,7 +65,8 @@ def workload_config(a):
             "n": a.n, "mean_degree": 10, "M": a.M, "m": a.m,
             "t": [float(x) for x in a.ts.split(",")], "methods": a.methods.split(","),
             "graph_seed": a.graph_seed, "node_seed": a.node_seed, "basis": a.basis,
-            "l2": "256 MiB flush write between steps; per-solve working set > L2"}
+            "l2": "256 MiB flush write between steps; per-solve working set > L2",
+            "streams": a.streams}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -228,14 +231,24 @@ def main():
     nodes = synth.sample_nodes(a.n, a.M, seed=a.node_seed + rank)
     stream = torch.cuda.current_stream()
     G = kb.Graph.from_csr(g, stream=stream)
+    streams = [stream] + [torch.cuda.Stream() for _ in range(max(1, a.streams) - 1)]
     solves = [(mth, t) for mth in methods for t in ts]
     Ys = [torch.empty((a.n, a.M), dtype=torch.float32, device="cuda") for _ in solves]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     params = {t: kb.make_params(t=t, basis=a.basis) for t in ts}
 
     def step(pr=params):
-        for (mth, t), Y in zip(solves, Ys):
-            kb.kb_krylov_apply(G, mth, "exp", pr[t], nodes, a.M, a.m, Y, stream=stream)
+        # independent solves round-robin over the streams; every stream joins the main one
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        for s2 in streams[1:]:
+            s2.wait_event(ev)
+        for i, ((mth, t), Y) in enumerate(zip(solves, Ys)):
+            kb.kb_krylov_apply(G, mth, "exp", pr[t], nodes, a.M, a.m, Y, stream=streams[i % len(streams)])
+        for s2 in streams[1:]:
+            e2 = torch.cuda.Event()
+            e2.record(s2)
+            stream.wait_event(e2)
 
     for _ in range(a.warmup):
         flush.zero_()

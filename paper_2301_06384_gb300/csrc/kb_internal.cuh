@@ -86,12 +86,12 @@ inline int width_for(int M) { return M <= 16 ? 16 : M <= 32 ? 32 : M <= 64 ? 64 
 // c0/c1/c2 come from device arrays (length W) when the pointer is set, else the scalars.
 template <typename T>
 struct LinEpi {
-    const float *a1 = nullptr, *a0 = nullptr, *a2 = nullptr;
-    float s1 = 1.f, s0 = 0.f, s2 = 0.f, s3 = 0.f;
+    const double *a1 = nullptr, *a0 = nullptr, *a2 = nullptr;
+    double s1 = 1.0, s0 = 0.0, s2 = 0.0, s3 = 0.0;
     const T *y = nullptr;
     const T *z = nullptr;
     const int32_t *marker = nullptr;
-    float wE = 0.f;
+    double wE = 0.0;
     T *out = nullptr;                 // internal n x W output (used when yout is null)
     float *yout = nullptr;            // final FP32 output with leading dimension ldo, mo columns
     double *dot_partials = nullptr;   // [grid][W]: sum_i x_i[c] * out_i[c]

@@ -37,24 +37,24 @@ int launch_chol(const double *G, int M, int W, int pass, int step, double inv_th
                 double piv_rel2, double *R1, double *Rinv64, T *Rinv, double *Hs, T *Bout,
                 Ctrl *ctrl, cudaStream_t s);
 
-int launch_lanczos_init(int W, int M, int gbl, double *sigma, int32_t *alive, float *c1, float *c2,
-                        cudaStream_t s);
+int launch_lanczos_init(int W, int M, int gbl, int round32, double *sigma, int32_t *alive,
+                        double *c1, double *c2, cudaStream_t s);
 int launch_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k,
-                         const double *sigma, double *alpha, float *a_upd, const Ctrl *ctrl,
+                         const double *sigma, double *alpha, double *a_upd, const Ctrl *ctrl,
                          cudaStream_t s);
-int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, int k,
-                        double thresh, double *beta, double *sigma, int32_t *alive, float *c1,
-                        float *c2, Ctrl *ctrl, cudaStream_t s);
+int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, int k, int round32,
+                        double thresh, double *beta, double *sigma, int32_t *alive, double *c1,
+                        double *c2, Ctrl *ctrl, cudaStream_t s);
 int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const double *beta,
                        const double *sigma, int phi_kind, double eps, int s_int, double lam,
-                       const ChebCoef &cc, float *omega, double *work, const Ctrl *ctrl,
+                       const ChebCoef &cc, double *omega, double *work, const Ctrl *ctrl,
                        cudaStream_t s);
 template <typename T>
-int launch_axpy_colnorm(int W, T *X, const T *P, const float *a, int64_t n, double *parts,
+int launch_axpy_colnorm(int W, T *X, const T *P, const double *a, int64_t n, double *parts,
                         int *grid_out, const Ctrl *ctrl, cudaStream_t s);
 int axpy_max_grid();
 template <typename T>
-int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const float *omega,
+int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const double *omega,
                          int64_t n, float *Y, int64_t ldy, int mo, int64_t M_alg, cudaStream_t s);
 template <typename T>
 int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ctrl, cudaStream_t s);

@@ -181,7 +181,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             T *Qp = k >= 2 ? b.basis + (k - 2) * bs : nullptr;
             // line 3 (first half): W = L Q_k
             LinEpi<T> e;
-            e.s1 = 1.f;
+            e.s1 = 1.0;
             e.out = b.wbuf;
             e.ctrl = b.ctrl;
             KB_TRY(launch_spmm<T>(c.g->dev, W, Qk, e, c.s, nullptr, M, 0));
@@ -247,7 +247,7 @@ struct LzBufs {
     T *basis;
     double *parts, *sigma, *alpha, *beta, *work;
     int32_t *alive;
-    float *c1, *c2, *aupd, *omega;
+    double *c1, *c2, *aupd, *omega;
     Ctrl *ctrl;
 };
 
@@ -260,10 +260,10 @@ void plan_lz(Arena &ar, LzBufs<T> &b, int64_t n, int W, int m, int pgrid) {
     b.beta = ar.take<double>(size_t(m + 1) * W);
     b.work = ar.take<double>(size_t(W) * 4 * m);
     b.alive = ar.take<int32_t>(W);
-    b.c1 = ar.take<float>(W);
-    b.c2 = ar.take<float>(W);
-    b.aupd = ar.take<float>(W);
-    b.omega = ar.take<float>(size_t(m) * W);
+    b.c1 = ar.take<double>(W);
+    b.c2 = ar.take<double>(W);
+    b.aupd = ar.take<double>(W);
+    b.omega = ar.take<double>(size_t(m) * W);
     b.ctrl = ar.take<Ctrl>(1);
 }
 
@@ -296,7 +296,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
         KB_CUDA_TRY(cudaMemsetAsync(b.beta, 0, sizeof(double) * size_t(m + 1) * W, c.s));
         KB_CUDA_TRY(cudaMemsetAsync(b.alpha, 0, sizeof(double) * size_t(m + 1) * W, c.s));
         KB_CUDA_TRY(cudaMemsetAsync(b.sigma, 0, sizeof(double) * size_t(m + 1) * W, c.s));
-        KB_TRY(launch_lanczos_init(W, M, gbl ? 1 : 0, b.sigma, b.alive, b.c1, b.c2, c.s));
+        KB_TRY(launch_lanczos_init(W, M, gbl ? 1 : 0, f64 ? 0 : 1, b.sigma, b.alive, b.c1, b.c2, c.s));
         const int64_t bs = n * W;
         for (int k = 1; k <= m; ++k) {
             T *Pk = b.basis + (k - 1) * bs;
@@ -306,7 +306,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
             LinEpi<T> e;
             e.a1 = b.c1;
             e.a2 = b.c2;
-            e.s0 = 0.f;
+            e.s0 = 0.0;
             e.y = Pp;
             e.out = X;
             e.dot_partials = b.parts;
@@ -319,7 +319,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
             if (k == m) break;
             int grid2 = 0;
             KB_TRY(launch_axpy_colnorm<T>(W, X, Pk, b.aupd, n, b.parts, &grid2, b.ctrl, c.s));
-            KB_TRY(launch_lanczos_beta(b.parts, grid2, W, M, gbl ? 1 : 0, k - 1, thresh, b.beta,
+            KB_TRY(launch_lanczos_beta(b.parts, grid2, W, M, gbl ? 1 : 0, k - 1, f64 ? 0 : 1, thresh, b.beta,
                                        b.sigma, b.alive, b.c1, b.c2, b.ctrl, c.s));
         }
         KB_TRY(launch_tridiag_phi(W, M, m, gbl ? 1 : 0, b.alpha, b.beta, b.sigma, int(c.phi),
@@ -361,12 +361,12 @@ int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int
         int dst_i = 0;
         while (dst_i == cur_i || dst_i == prev_i) ++dst_i;
         LinEpi<T> e;
-        e.s1 = float((last ? -2.0 : -4.0) / lam);
-        e.s0 = last ? 1.f : 2.f;
-        e.s2 = -1.f;
+        e.s1 = (last ? -2.0 : -4.0) / lam;
+        e.s0 = last ? 1.0 : 2.0;
+        e.s2 = -1.0;
         e.y = prev_i >= 0 ? bufs[prev_i] : nullptr;
-        if (Zsrc) { e.z = Zsrc; e.s3 = float(w[k]); }
-        else { e.marker = marker; e.wE = float(w[k]); }
+        if (Zsrc) { e.z = Zsrc; e.s3 = w[k]; }
+        else { e.marker = marker; e.wE = w[k]; }
         if (last) {
             if (yout) e.yout = yout;
             else e.out = out;

@@ -58,11 +58,25 @@ __global__ void k_hkk(const double *G, int M, int W, double *Hd, T *C, const Ctr
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
         const int i = idx / W, j = idx % W;
         double v = 0.0;
-        if (i < M && j < M) {
-            v = 0.5 * (G[i * W + j] + G[j * W + i]);
-            Hd[i * M + j] = v;
+        if (i < M && j < M) v = 0.5 * (G[i * W + j] + G[j * W + i]);
+        // recorded exactly as the update subtracts it (rounded to the basis precision)
+        const T vt = T(v);
+        if (i < M && j < M) Hd[i * M + j] = double(vt);
+        C[idx] = vt;
+    }
+}
+
+// X = U^{-1} for an upper triangular M x M matrix U (ld ldu), X with ld ldx; thread c
+// computes column c by back substitution (the sum for row i uses rows i+1..c).
+__device__ void tri_inv_upper(const double *U, int ldu, double *X, int ldx, int M) {
+    for (int c = threadIdx.x; c < M; c += blockDim.x) {
+        X[c * ldx + c] = 1.0 / U[c * ldu + c];
+        for (int i = c - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int j = i + 1; j <= c; ++j) s += U[i * ldu + j] * X[j * ldx + c];
+            X[i * ldx + c] = -s / U[i * ldu + i];
         }
-        C[idx] = T(v);
+        for (int i = c + 1; i < M; ++i) X[i * ldx + c] = 0.0;
     }
 }
 
@@ -120,19 +134,25 @@ __global__ void k_chol(const double *G, int M, int W, int pass, int step, double
         }
         __syncthreads();
     }
-    // R^{-1}: column c by back substitution (thread c)
-    for (int c = threadIdx.x; c < M; c += blockDim.x) {
-        Rinv64[c * W + c] = 1.0 / A[c * lda + c];
-        for (int i = c - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int j = i + 1; j <= c; ++j) s += A[i * lda + j] * Rinv64[j * W + c];
-            Rinv64[i * W + c] = -s / A[i * lda + i];
-        }
-    }
+    // R^{-1} (upper triangular): column c by back substitution (thread c)
+    tri_inv_upper(A, lda, Rinv64, W, M);
     __syncthreads();
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
         const int i = idx / W, j = idx % W;
         Rinv[idx] = (i < M && j < M && j >= i) ? T(Rinv64[idx]) : T(0);
+    }
+    __syncthreads();
+    if (sizeof(T) == 4) {
+        // The row-block kernels apply the FP32-rounded inverse.  Record the factor that is
+        // actually applied, the FP64 inverse of the rounded inverse, so that
+        // X = Q_{k+1} H_{k+1,k} holds for the stored blocks up to FP32 rounding of Q.
+        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+            const int i = idx / M, j = idx % M;
+            Rinv64[i * W + j] = (j >= i) ? double(float(Rinv64[i * W + j])) : 0.0;
+        }
+        __syncthreads();
+        tri_inv_upper(Rinv64, W, A, lda, M);
+        __syncthreads();
     }
     if (pass == 1) {
         for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
@@ -140,15 +160,17 @@ __global__ void k_chol(const double *G, int M, int W, int pass, int step, double
             R1[idx] = (j >= i) ? A[i * lda + j] : 0.0;
         }
     } else {
-        // H_{k+1,k} = R2 R1 (upper triangular); B = H^T for the next three-term step
+        // H_{k+1,k} = R2 R1 (upper triangular); B = H^T for the next three-term step.  H is
+        // recorded rounded to the basis precision, i.e. exactly as the next step subtracts it.
         for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
             const int i = idx / W, j = idx % W;
             double h = 0.0;
             if (i < M && j < M && j >= i) {
                 for (int k = i; k <= j; ++k) h += A[i * lda + k] * R1[k * M + j];
             }
-            if (i < M && j < M) Hs[i * M + j] = h;
-            Bout[j * W + i] = T(h);
+            const T ht = T(h);
+            if (i < M && j < M) Hs[i * M + j] = double(ht);
+            Bout[j * W + i] = ht;
         }
     }
 }
@@ -174,21 +196,27 @@ __device__ void reduce_cols(const double *parts, int nparts, int W, double *s) {
     __syncthreads();
 }
 
-__global__ void k_lanczos_init(int W, int M, int gbl, double *sigma, int32_t *alive, float *c1,
-                               float *c2) {
+// Scale factors sigma (Q_k = sigma_k P_k) are rounded to the basis precision when the
+// basis is FP32, so that the SpMM applies exactly the sigma the recurrence records.
+__device__ __forceinline__ double round_to(double v, int round32) {
+    return round32 ? double(float(v)) : v;
+}
+
+__global__ void k_lanczos_init(int W, int M, int gbl, int round32, double *sigma, int32_t *alive,
+                               double *c1, double *c2) {
     for (int c = threadIdx.x; c < W; c += blockDim.x) {
         const bool live = c < M;
-        const double s0 = live ? (gbl ? 1.0 / sqrt(double(M)) : 1.0) : 0.0;
+        const double s0 = live ? round_to(gbl ? 1.0 / sqrt(double(M)) : 1.0, round32) : 0.0;
         sigma[c] = s0;
         alive[c] = live ? 1 : 0;
-        c1[c] = float(s0);
-        c2[c] = 0.f;
+        c1[c] = s0;
+        c2[c] = 0.0;
     }
 }
 
 // alpha_k = <Q_k, X> (gbl: Frobenius, sbl: per column) from SpMM dot partials of P_k . X
 __global__ void k_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k,
-                                const double *sigma, double *alpha, float *a_upd, const Ctrl *ctrl) {
+                                const double *sigma, double *alpha, double *a_upd, const Ctrl *ctrl) {
     if (ctrl->stop) return;
     __shared__ double s[128];
     reduce_cols(parts, nparts, W, s);
@@ -203,22 +231,24 @@ __global__ void k_lanczos_alpha(const double *parts, int nparts, int W, int M, i
         __syncthreads();
         for (int c = threadIdx.x; c < W; c += blockDim.x) {
             alpha[int64_t(k) * W + c] = c < M ? tot : 0.0;
-            a_upd[c] = c < M ? float(tot * sg[0]) : 0.f;
+            a_upd[c] = c < M ? tot * sg[0] : 0.0;
         }
     } else {
         for (int c = threadIdx.x; c < W; c += blockDim.x) {
             const double al = c < M ? sg[c] * s[c] : 0.0;
             alpha[int64_t(k) * W + c] = al;
-            a_upd[c] = float(al * sg[c]);
+            a_upd[c] = al * sg[c];
         }
     }
 }
 
 // beta_{k+1} = ||X|| (gbl: Frobenius, sbl: per column), sigma_{k+1} = 1/beta, and the
 // SpMM coefficients of the next step: X = sigma_{k+1} L P_{k+1} - beta_{k+1} sigma_k P_k.
+// sigma_{k+1} is rounded to the basis precision and beta_{k+1} is recorded as its exact
+// reciprocal, so Q_{k+1} = sigma_{k+1} P_{k+1} = X / beta_{k+1} holds for the stored values.
 __global__ void k_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, int k,
-                               double thresh, double *beta, double *sigma, int32_t *alive, float *c1,
-                               float *c2, Ctrl *ctrl) {
+                               int round32, double thresh, double *beta, double *sigma,
+                               int32_t *alive, double *c1, double *c2, Ctrl *ctrl) {
     if (ctrl->stop) return;
     __shared__ double s[128];
     reduce_cols(parts, nparts, W, s);
@@ -236,22 +266,26 @@ __global__ void k_lanczos_beta(const double *parts, int nparts, int W, int M, in
             if (stop) { ctrl->stop = 1; ctrl->steps = k + 1; }
         }
         __syncthreads();
+        const double sg = round_to(1.0 / b, round32);
+        const double bt = 1.0 / sg;
         for (int c = threadIdx.x; c < W; c += blockDim.x) {
             const bool live = c < M && !stop;
-            bn[c] = live ? b : 0.0;
-            sn[c] = live ? 1.0 / b : 0.0;
-            c1[c] = live ? float(1.0 / b) : 0.f;
-            c2[c] = live ? float(-b * sk[c]) : 0.f;
+            bn[c] = live ? bt : 0.0;
+            sn[c] = live ? sg : 0.0;
+            c1[c] = live ? sg : 0.0;
+            c2[c] = live ? -bt * sk[c] : 0.0;
         }
     } else {
         for (int c = threadIdx.x; c < W; c += blockDim.x) {
             const double b = sqrt(s[c]);
             const bool live = c < M && alive[c] && (b > thresh);
             if (!live) alive[c] = 0;
-            bn[c] = live ? b : 0.0;
-            sn[c] = live ? 1.0 / b : 0.0;
-            c1[c] = live ? float(1.0 / b) : 0.f;
-            c2[c] = live ? float(-b * sk[c]) : 0.f;
+            const double sg = live ? round_to(1.0 / b, round32) : 0.0;
+            const double bt = live ? 1.0 / sg : 0.0;
+            bn[c] = bt;
+            sn[c] = sg;
+            c1[c] = sg;
+            c2[c] = live ? -bt * sk[c] : 0.0;
         }
     }
 }
@@ -262,15 +296,15 @@ __global__ void k_lanczos_beta(const double *parts, int nparts, int W, int M, in
 //   spline: s_int solves with the SPD tridiagonal eps I + T (Thomas algorithm)
 __global__ void k_tridiag_phi(int W, int M, int m, int gbl, const double *alpha,
                               const double *beta, const double *sigma, int phi_kind,
-                              double eps, int s_int, double lam, ChebCoef cc, float *omega,
+                              double eps, int s_int, double lam, ChebCoef cc, double *omega,
                               double *work, const Ctrl *ctrl) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int ncol = gbl ? 1 : M;
     if (c >= W) return;
     const int steps = gbl ? ctrl->steps : m;
     if (c >= ncol) {
-        if (!gbl || c >= M)
-            for (int k = 0; k < m; ++k) omega[int64_t(k) * W + c] = 0.f;
+        if (!gbl)
+            for (int k = 0; k < m; ++k) omega[int64_t(k) * W + c] = 0.0;
         return;
     }
     // per-thread work vectors in global scratch: 4 vectors of length m
@@ -321,13 +355,15 @@ __global__ void k_tridiag_phi(int W, int M, int m, int gbl, const double *alpha,
             for (int k = s - 2; k >= 0; --k) u[k] = v1[k] - v0[k] * u[k + 1];
         }
     }
-    const double scale = gbl ? sqrt(double(M)) : 1.0;
+    // E_W = P_1 and Q_1 = sigma_1 P_1, so Y = (1/sigma_1) [Q_1..Q_m] phi(T) e_1
+    // (sqrt(N) of Algorithm 2, line 8, for the global method)
+    const double scale = 1.0 / sigma[c];
     for (int k = 0; k < m; ++k) {
-        float om = 0.f;
-        if (k < s) om = float(scale * u[k] * sigma[int64_t(k) * W + c]);
+        double om = 0.0;
+        if (k < s) om = scale * u[k] * sigma[int64_t(k) * W + c];
         if (gbl) {
             for (int cc2 = 0; cc2 < W; ++cc2)
-                omega[int64_t(k) * W + cc2] = cc2 < M ? om : 0.f;
+                omega[int64_t(k) * W + cc2] = cc2 < M ? om : 0.0;
         } else {
             omega[int64_t(k) * W + c] = om;
         }
@@ -336,7 +372,7 @@ __global__ void k_tridiag_phi(int W, int M, int m, int gbl, const double *alpha,
 
 // X[:, c] -= a[c] * P[:, c]; partial column sums of X^2 per CTA
 template <typename T, int W>
-__global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const float *a, int64_t n,
+__global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const double *a, int64_t n,
                                                        double *parts, const Ctrl *ctrl) {
     if (ctrl->stop) return;
     constexpr int CG = W / 4;
@@ -344,18 +380,21 @@ __global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const fl
     __shared__ double s[RPP][W];
     const int cg = threadIdx.x % CG, rr = threadIdx.x / CG;
     const int c4 = cg * 4;
-    float av[4];
+    T ah[4], al[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) av[q] = a[c4 + q];
-    float acc[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 4; ++q) {
+        ah[q] = T(a[c4 + q]);
+        al[q] = T(a[c4 + q] - double(ah[q]));
+    }
+    T acc[4] = {0, 0, 0, 0};
     for (int64_t row = int64_t(blockIdx.x) * RPP + rr; row < n; row += int64_t(gridDim.x) * RPP) {
         T *xp = X + row * W + c4;
         const T *pp = P + row * W + c4;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const T v = xp[q] - T(av[q]) * pp[q];
+            const T v = xp[q] - fma(ah[q], pp[q], al[q] * pp[q]);
             xp[q] = v;
-            acc[q] += float(v) * float(v);
+            acc[q] = fma(v, v, acc[q]);
         }
     }
 #pragma unroll
@@ -371,18 +410,22 @@ __global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const fl
 // Y[i, c] = sum_k omega_k[c] P_k[i, c]  (global / sequential Lanczos assembly)
 template <typename T, int W>
 __global__ void __launch_bounds__(256) k_assemble_diag(const T *basis, int64_t stride, int nblk,
-                                                        const float *omega, int64_t n, float *Y,
+                                                        const double *omega, int64_t n, float *Y,
                                                         int64_t ldy, int mo) {
     constexpr int CG = W / 4;
     constexpr int RPP = 256 / CG;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *som = reinterpret_cast<T *>(sm_raw);     // [nblk][W]
+    for (int i = threadIdx.x; i < nblk * W; i += blockDim.x) som[i] = T(omega[i]);
+    __syncthreads();
     const int cg = threadIdx.x % CG, rr = threadIdx.x / CG;
     const int c4 = cg * 4;
     for (int64_t row = int64_t(blockIdx.x) * RPP + rr; row < n; row += int64_t(gridDim.x) * RPP) {
-        float acc[4] = {0, 0, 0, 0};
+        T acc[4] = {0, 0, 0, 0};
         for (int k = 0; k < nblk; ++k) {
             const T *p = basis + int64_t(k) * stride + row * W + c4;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fmaf(__ldg(omega + int64_t(k) * W + c4 + q), float(p[q]), acc[q]);
+            for (int q = 0; q < 4; ++q) acc[q] = fma(som[k * W + c4 + q], p[q], acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -483,16 +526,16 @@ int launch_chol(const double *G, int M, int W, int pass, int step, double inv_th
     return 0;
 }
 
-int launch_lanczos_init(int W, int M, int gbl, double *sigma, int32_t *alive, float *c1, float *c2,
-                        cudaStream_t s) {
-    k_lanczos_init<<<1, 128, 0, s>>>(W, M, gbl, sigma, alive, c1, c2);
+int launch_lanczos_init(int W, int M, int gbl, int round32, double *sigma, int32_t *alive,
+                        double *c1, double *c2, cudaStream_t s) {
+    k_lanczos_init<<<1, 128, 0, s>>>(W, M, gbl, round32, sigma, alive, c1, c2);
     count_launches(1);
     KB_CUDA_TRY(cudaGetLastError());
     return 0;
 }
 
 int launch_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k,
-                         const double *sigma, double *alpha, float *a_upd, const Ctrl *ctrl,
+                         const double *sigma, double *alpha, double *a_upd, const Ctrl *ctrl,
                          cudaStream_t s) {
     prof_begin(KernelClass::SMALL, s);
     k_lanczos_alpha<<<1, 256, 0, s>>>(parts, nparts, W, M, gbl, k, sigma, alpha, a_upd, ctrl);
@@ -501,12 +544,12 @@ int launch_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl,
     return 0;
 }
 
-int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, int k,
-                        double thresh, double *beta, double *sigma, int32_t *alive, float *c1,
-                        float *c2, Ctrl *ctrl, cudaStream_t s) {
+int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, int k, int round32,
+                        double thresh, double *beta, double *sigma, int32_t *alive, double *c1,
+                        double *c2, Ctrl *ctrl, cudaStream_t s) {
     prof_begin(KernelClass::SMALL, s);
-    k_lanczos_beta<<<1, 256, 0, s>>>(parts, nparts, W, M, gbl, k, thresh, beta, sigma, alive, c1,
-                                     c2, ctrl);
+    k_lanczos_beta<<<1, 256, 0, s>>>(parts, nparts, W, M, gbl, k, round32, thresh, beta, sigma,
+                                     alive, c1, c2, ctrl);
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::SMALL, s, double(nparts) * W * 8, 0);
     return 0;
@@ -514,7 +557,7 @@ int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, 
 
 int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const double *beta,
                        const double *sigma, int phi_kind, double eps, int s_int, double lam,
-                       const ChebCoef &cc, float *omega, double *work, const Ctrl *ctrl,
+                       const ChebCoef &cc, double *omega, double *work, const Ctrl *ctrl,
                        cudaStream_t s) {
     prof_begin(KernelClass::PROJECTED, s);
     k_tridiag_phi<<<(W + 63) / 64, 64, 0, s>>>(W, M, m, gbl, alpha, beta, sigma, phi_kind, eps,
@@ -525,7 +568,7 @@ int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const 
 }
 
 template <typename T>
-int launch_axpy_colnorm(int W, T *X, const T *P, const float *a, int64_t n, double *parts,
+int launch_axpy_colnorm(int W, T *X, const T *P, const double *a, int64_t n, double *parts,
                         int *grid_out, const Ctrl *ctrl, cudaStream_t s) {
     const int rpp = 256 / (W / 4);
     const int grid = int(std::min<int64_t>((n + rpp - 1) / rpp, int64_t(num_sms()) * 4));
@@ -545,17 +588,26 @@ int launch_axpy_colnorm(int W, T *X, const T *P, const float *a, int64_t n, doub
 
 int axpy_max_grid() { return num_sms() * 4; }
 
+#define KB_ASM_DIAG(WW)                                                                       \
+    do {                                                                                      \
+        cudaFuncSetAttribute(k_assemble_diag<T, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             int(smem));                                                      \
+        k_assemble_diag<T, WW><<<grid, 256, smem, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo); \
+    } while (0)
+
 template <typename T>
-int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const float *omega,
+int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const double *omega,
                          int64_t n, float *Y, int64_t ldy, int mo, int64_t M_alg, cudaStream_t s) {
     const int rpp = 256 / (W / 4);
     const int grid = std::max(1, int(std::min<int64_t>((n + rpp - 1) / rpp, int64_t(num_sms()) * 8)));
+    const size_t smem = sizeof(T) * size_t(nblk) * W;
+    if (smem > 200 * 1024) return fail(KB_ERR_UNSUPPORTED, "too many blocks for the diagonal assembly");
     prof_begin(KernelClass::ASSEMBLE, s);
     switch (W) {
-        case 16: k_assemble_diag<T, 16><<<grid, 256, 0, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo); break;
-        case 32: k_assemble_diag<T, 32><<<grid, 256, 0, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo); break;
-        case 64: k_assemble_diag<T, 64><<<grid, 256, 0, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo); break;
-        case 128: k_assemble_diag<T, 128><<<grid, 256, 0, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo); break;
+        case 16: KB_ASM_DIAG(16); break;
+        case 32: KB_ASM_DIAG(32); break;
+        case 64: KB_ASM_DIAG(64); break;
+        case 128: KB_ASM_DIAG(128); break;
         default: return fail(KB_ERR_ARG, "bad width");
     }
     KB_CUDA_TRY(cudaGetLastError());
@@ -580,9 +632,9 @@ int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ct
     template int launch_hkk<T>(const double *, int, int, double *, T *, const Ctrl *, cudaStream_t); \
     template int launch_chol<T>(const double *, int, int, int, int, double, double, double *,   \
                                 double *, T *, double *, T *, Ctrl *, cudaStream_t);            \
-    template int launch_axpy_colnorm<T>(int, T *, const T *, const float *, int64_t, double *,  \
+    template int launch_axpy_colnorm<T>(int, T *, const T *, const double *, int64_t, double *, \
                                         int *, const Ctrl *, cudaStream_t);                     \
-    template int launch_assemble_diag<T>(int, const T *, int64_t, int, const float *, int64_t,  \
+    template int launch_assemble_diag<T>(int, const T *, int64_t, int, const double *, int64_t, \
                                          float *, int64_t, int, int64_t, cudaStream_t);         \
     template int launch_u_convert<T>(const double *, int, int, int, T *, const Ctrl *, cudaStream_t);
 KB_INST(float)
