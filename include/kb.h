@@ -154,6 +154,36 @@ int kb_krylov_apply_host(kb_graph *g, kb_method method, kb_phi phi, const kb_par
                          const int32_t *nodes, int32_t M, int32_t m, float *Y_host,
                          void *stream, kb_info *info);
 
+/*
+ * kb_cheb_apply_fixed_scratch -- KB_CHEB without any memory allocation.
+ *
+ * The paper has no counterpart of this call.  It serves callers that cannot allocate
+ * device memory when they need kernel columns: code running inside a framework that has
+ * reserved the device memory for its own allocator, latency-critical loops that must not
+ * enter an allocator after start-up, and processes sharing a device under a fixed memory
+ * budget.  It computes exactly what kb_krylov_apply(g, KB_CHEB, phi, params, nodes, M, m,
+ * Y, stream, NULL) computes (same kernels, same order of operations), but its scratch is a
+ * file-scope device array of KB_FIXED_SCRATCH_BYTES (32 MiB) that every GPU loading the
+ * library holds until the process exits; the call performs no cudaMalloc, cudaMallocAsync
+ * or cudaFree and calls no allocating library routine.
+ *
+ *   Arguments as kb_krylov_apply, restricted to 1 <= M <= 128, 1 <= m <= 1024 and
+ *   params->basis == KB_F32.  The scratch needed is 3 * n * W * 4 bytes (each block rounded
+ *   up to 256 bytes) plus 4 * n bytes, W = M rounded up to 16/32/64/128; a larger problem
+ *   is rejected with KB_ERR_ARG and a message giving both sizes, before any GPU work.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any
+ *   stream capture.  All calls in the process share the one array, and every call
+ *   rewrites the parts it reads before reading them: calls whose GPU work overlaps (other
+ *   streams, other threads) race on the scratch and must be serialised by the caller.
+ *   Does not synchronise; errors: KB_ERR_ARG, KB_ERR_NODES, KB_ERR_UNSUPPORTED,
+ *   KB_ERR_CUDA.
+ */
+#define KB_FIXED_SCRATCH_BYTES (32u << 20)
+int kb_cheb_apply_fixed_scratch(kb_graph *g, kb_phi phi, const kb_params *params,
+                                const int32_t *nodes, int32_t M, int32_t m, float *Y,
+                                void *stream);
+
 /* ------------------------------------------------------------------ diagnostics */
 /* Static text for a status code. */
 const char *kb_status_string(int status);

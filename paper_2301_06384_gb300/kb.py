@@ -259,3 +259,20 @@ def kernel_columns(graph: Graph, method: str, phi: str, nodes, m: int, stream=No
     r = kb_krylov_apply(graph, method, phi, make_params(**params), nodes, nodes.size, m, Y,
                         stream=stream, info=info)
     return (Y, r) if info else Y
+
+
+def kb_cheb_apply_fixed_scratch(graph: Graph, phi: str, params: kb_params, nodes, M: int, m: int,
+                                Y, stream=None):
+    """KB_CHEB into device Y using the library's fixed scratch array (no allocation)."""
+    L = lib()
+    if not hasattr(L, "_fixed_scratch_typed"):
+        L.kb_cheb_apply_fixed_scratch.argtypes = [ctypes.c_void_p, ctypes.c_int,
+                                                  ctypes.POINTER(kb_params), ctypes.c_void_p,
+                                                  ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                                  ctypes.c_void_p]
+        L.kb_cheb_apply_fixed_scratch.restype = ctypes.c_int
+        L._fixed_scratch_typed = True
+    nodes = np.ascontiguousarray(nodes, dtype=np.int32)
+    _check(L.kb_cheb_apply_fixed_scratch(graph.handle, PHIS[phi], ctypes.byref(params),
+                                         nodes.ctypes.data, int(M), int(m),
+                                         ctypes.c_void_p(_ptr(Y)), _stream_ptr(stream)))
