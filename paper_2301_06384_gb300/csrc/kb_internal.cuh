@@ -115,7 +115,9 @@ int spmm_max_grid(int W);
 //   ASM     : y[:, :mo] = sum_{k < nblk} basis_k * Ca_k  (Ca stacked nblk*W x W), nblk
 //             capped by ctrl->steps
 // In-place out == x is allowed (a tile's output rows depend only on its input rows).
-enum RowMode { RB_PROJ = 0, RB_UPD = 1, RB_MULGRAM = 2, RB_MUL = 3, RB_ASM = 4 };
+//   ASMSUB  : out = X - sum_{k < nblk} basis_k * Ca_k ; write ; G = out^T out
+//             (full reorthogonalisation against the stored blocks)
+enum RowMode { RB_PROJ = 0, RB_UPD = 1, RB_MULGRAM = 2, RB_MUL = 3, RB_ASM = 4, RB_ASMSUB = 5 };
 template <typename T>
 struct RowArgs {
     int64_t n = 0;
@@ -140,9 +142,10 @@ int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *g
 template <typename T>
 int rowblock_max_grid(int W);
 
-// Deterministic FP64 reduction of [nparts][len] partials into out[len].
+// Deterministic FP64 reduction of [nparts][len] partials into out[len]; when out_p is set
+// the sums are also written there rounded to P.
 template <typename P>
 int launch_reduce(const P *parts, int nparts, int len, double *out, cudaStream_t s,
-                  const Ctrl *ctrl);
+                  const Ctrl *ctrl, P *out_p = nullptr);
 
 }  // namespace kb

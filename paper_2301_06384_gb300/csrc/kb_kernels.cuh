@@ -34,8 +34,8 @@ template <typename T>
 int launch_hkk(const double *G, int M, int W, double *Hd, T *C, const Ctrl *ctrl, cudaStream_t s);
 template <typename T>
 int launch_chol(const double *G, int M, int W, int pass, int step, double inv_thresh2,
-                double piv_rel2, double *R1, double *Rinv64, T *Rinv, double *Hs, T *Bout,
-                Ctrl *ctrl, cudaStream_t s);
+                double piv_rel2, double *R1, T *Rinv, double *Hs, T *Bout, Ctrl *ctrl,
+                cudaStream_t s);
 
 int launch_lanczos_init(int W, int M, int gbl, int round32, double *sigma, int32_t *alive,
                         double *c1, double *c2, cudaStream_t s);

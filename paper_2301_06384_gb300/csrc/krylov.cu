@@ -128,8 +128,8 @@ struct Common {
 // ---------------------------------------------------------------- cbl
 template <typename T>
 struct CblBufs {
-    T *basis, *wbuf, *parts, *Cb, *B, *Rinv, *Ut;
-    double *Gsum, *Hd, *Hs, *R1, *Rinv64, *V0, *V1, *V2, *U;
+    T *basis, *wbuf, *parts, *Cb, *B, *Rinv, *Ut, *Cstk;
+    double *Gsum, *Hd, *Hs, *R1, *V0, *V1, *V2, *U;
     Ctrl *ctrl;
 };
 
@@ -146,7 +146,7 @@ void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_g
     b.Hd = ar.take<double>(size_t(m) * M * M);
     b.Hs = ar.take<double>(size_t(m) * M * M);
     b.R1 = ar.take<double>(size_t(M) * M);
-    b.Rinv64 = ar.take<double>(size_t(W) * W);
+    b.Cstk = ar.take<T>(size_t(m) * W * W);
     b.V0 = ar.take<double>(size_t(m) * M * M);
     b.V1 = ar.take<double>(size_t(m) * M * M);
     b.V2 = ar.take<double>(size_t(m) * M * M);
@@ -201,14 +201,34 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             ua.out = X; ua.partials = b.parts; ua.ctrl = b.ctrl;
             KB_TRY(launch_rowblock<T>(RB_UPD, W, ua, c.s, &grid, M));
             KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+            if (c.p.reorth) {
+                // full reorthogonalisation (not in the paper, reading A10): classical
+                // Gram-Schmidt against all stored blocks, X -= Q_{1:k} (Q_{1:k}^T X), twice;
+                // the second subtraction also forms the Gram X^T X for the QR
+                for (int pass = 0; pass < 2; ++pass) {
+                    for (int j = 0; j < k; ++j) {
+                        RowArgs<T> ra;
+                        ra.n = n; ra.x = X; ra.qa = b.basis + j * bs; ra.partials = b.parts;
+                        ra.ctrl = b.ctrl;
+                        KB_TRY(launch_rowblock<T>(RB_PROJ, W, ra, c.s, &grid, M));
+                        KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl,
+                                                b.Cstk + size_t(j) * W * W));
+                    }
+                    RowArgs<T> sa;
+                    sa.n = n; sa.x = X; sa.basis = b.basis; sa.block_stride = bs; sa.nblk = k;
+                    sa.ca = b.Cstk; sa.out = X; sa.partials = b.parts; sa.ctrl = b.ctrl;
+                    KB_TRY(launch_rowblock<T>(RB_ASMSUB, W, sa, c.s, &grid, M));
+                    KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+                }
+            }
             // line 6: X = Q_{k+1} H_{k+1,k} by CholeskyQR2
-            KB_TRY(launch_chol<T>(b.Gsum, M, W, 1, k, inv_thresh2, piv2, b.R1, b.Rinv64, b.Rinv,
-                                  nullptr, nullptr, b.ctrl, c.s));
+            KB_TRY(launch_chol<T>(b.Gsum, M, W, 1, k, inv_thresh2, piv2, b.R1, b.Rinv, nullptr,
+                                  nullptr, b.ctrl, c.s));
             RowArgs<T> ma;
             ma.n = n; ma.x = X; ma.ca = b.Rinv; ma.out = X; ma.partials = b.parts; ma.ctrl = b.ctrl;
             KB_TRY(launch_rowblock<T>(RB_MULGRAM, W, ma, c.s, &grid, M));
             KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
-            KB_TRY(launch_chol<T>(b.Gsum, M, W, 2, k, inv_thresh2, piv2, b.R1, b.Rinv64, b.Rinv,
+            KB_TRY(launch_chol<T>(b.Gsum, M, W, 2, k, inv_thresh2, piv2, b.R1, b.Rinv,
                                   b.Hs + size_t(k - 1) * M * M, b.B, b.ctrl, c.s));
             RowArgs<T> qa;
             qa.n = n; qa.x = X; qa.ca = b.Rinv; qa.out = X; qa.ctrl = b.ctrl;
@@ -447,7 +467,8 @@ int validate(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
     if (method == KB_CHEB2 && m < 2) return fail(KB_ERR_ARG, "KB_CHEB2 needs m >= 2");
     if (params->basis != KB_F32 && params->basis != KB_F64)
         return fail(KB_ERR_UNSUPPORTED, "basis dtype not implemented");
-    if (params->reorth) return fail(KB_ERR_UNSUPPORTED, "reorthogonalisation not implemented");
+    if (params->reorth && method != KB_CBL)
+        return fail(KB_ERR_UNSUPPORTED, "reorthogonalisation is implemented for KB_CBL only");
     const int wmax = params->basis == KB_F64 ? 64 : 128;
     if ((method == KB_CBL || method == KB_GBL) && M > wmax)
         return fail(KB_ERR_UNSUPPORTED, "block width too large for this method and dtype");

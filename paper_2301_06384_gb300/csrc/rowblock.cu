@@ -65,7 +65,9 @@ k_rowblock(RowArgs<T> a) {
     using G = Geo<T, W>;
     constexpr int TR = G::TR, CG = G::CG, GR = G::GR;
     constexpr bool PROD = MODE != RB_PROJ;
-    constexpr bool GRAM = MODE == RB_PROJ || MODE == RB_UPD || MODE == RB_MULGRAM;
+    constexpr bool GRAM = MODE == RB_PROJ || MODE == RB_UPD || MODE == RB_MULGRAM || MODE == RB_ASMSUB;
+    constexpr bool SUBX = MODE == RB_UPD || MODE == RB_ASMSUB;     // out = X - product
+    constexpr bool MULTI = MODE == RB_ASM || MODE == RB_ASMSUB;    // product over basis blocks
     constexpr bool TWO = sizeof(T) == 4;
     if (MODE != RB_ASM && a.ctrl && a.ctrl->stop) return;
 
@@ -76,8 +78,10 @@ k_rowblock(RowArgs<T> a) {
     T *sQ = reinterpret_cast<T *>(smem_raw + G::smem_a + G::smem_c + G::smem_o);  // [TR][LDO]
 
     const int tid = threadIdx.x;
-    const int col4 = (tid % CG) * 4;
-    const int row0 = (tid / CG) * 4;
+    // product mapping: consecutive threads share an output column group, so a warp covers
+    // few column groups and can skip K-chunks that meet the zero half of a triangular factor
+    const int col4 = (tid / (TR / 4)) * 4;
+    const int row0 = (tid % (TR / 4)) * 4;
     const int gi0 = (tid / 16) * GR;
     const int gj0 = (tid % 16) * GR;
 
@@ -85,6 +89,7 @@ k_rowblock(RowArgs<T> a) {
     int nkb = 1;
     if (MODE == RB_UPD) nkb = a.qa ? 2 : 1;
     if (MODE == RB_ASM) nkb = a.ctrl ? min(a.ctrl->steps, a.nblk) : a.nblk;
+    if (MODE == RB_ASMSUB) nkb = a.nblk;
 
     T g1[GR][GR], g2[GR][GR];
 #pragma unroll
@@ -96,6 +101,16 @@ k_rowblock(RowArgs<T> a) {
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t r0 = tile * TR;
         if constexpr (PROD) {
+            if (SUBX) {
+                // stage the X tile (coalesced); the first __syncthreads of the K loop orders it
+                for (int idx = tid; idx < TR * CG; idx += RB_THREADS) {
+                    const int r = idx / CG;
+                    const int c = (idx % CG) * 4;
+                    T xv[4] = {0, 0, 0, 0};
+                    if (r0 + r < a.n) ld4<T>(a.x + (r0 + r) * W + c, xv);
+                    st4<T>(sO + r * G::LDO + c, xv);
+                }
+            }
             T acc[4][4];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
@@ -107,7 +122,7 @@ k_rowblock(RowArgs<T> a) {
                 if (MODE == RB_UPD) {
                     src = (a.qa && kb == 0) ? a.qa : a.qb;
                     cmat = (a.qa && kb == 0) ? a.ca : a.cb;
-                } else if (MODE == RB_ASM) {
+                } else if (MULTI) {
                     src = a.basis + int64_t(kb) * a.block_stride;
                     cmat = a.ca + int64_t(kb) * W * W;
                 } else {
@@ -132,6 +147,13 @@ k_rowblock(RowArgs<T> a) {
                         st4<T>(sC + kr * W + c, v);
                     }
                     __syncthreads();
+                    // R^{-1} (MUL, MULGRAM) is upper triangular: rows k > c contribute nothing
+                    // to column c.  H_{k-1,k} (UPD, first K block) is lower triangular: rows
+                    // k < c contribute nothing.
+                    bool skip = false;
+                    if (MODE == RB_MUL || MODE == RB_MULGRAM) skip = k0 > col4 + 3;
+                    if (MODE == RB_UPD && a.qa && kb == 0) skip = k0 + KC - 1 < col4;
+                    if (!skip)
 #pragma unroll
                     for (int k = 0; k < KC; ++k) {
                         T av[4], cv[4];
@@ -145,30 +167,37 @@ k_rowblock(RowArgs<T> a) {
                     __syncthreads();
                 }
             }
-            // finish the tile
+            // finish the tile: the register tile goes to shared memory (UPD subtracts it from
+            // the X tile staged there), then the whole tile is stored with coalesced rows
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const int64_t row = r0 + row0 + r;
                 T o[4];
-                if (MODE == RB_UPD) {
-                    T xv[4] = {0, 0, 0, 0};
-                    if (row < a.n) ld4<T>(a.x + row * W + col4, xv);
+                if (SUBX) {
+                    T xv[4];
+                    ld4<T>(sO + (row0 + r) * G::LDO + col4, xv);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) o[q] = xv[q] - acc[r][q];
                 } else {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) o[q] = acc[r][q];
                 }
-                if (row < a.n) {
-                    if (MODE == RB_ASM) {
+                st4<T>(sO + (row0 + r) * G::LDO + col4, o);
+            }
+            __syncthreads();
+            for (int idx = tid; idx < TR * CG; idx += RB_THREADS) {
+                const int r = idx / CG;
+                const int c = (idx % CG) * 4;
+                const int64_t row = r0 + r;
+                if (row >= a.n) continue;
+                T o[4];
+                ld4<T>(sO + r * G::LDO + c, o);
+                if (MODE == RB_ASM) {
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (col4 + q < a.mo) a.y[row * a.ldy + col4 + q] = float(o[q]);
-                    } else {
-                        st4<T>(a.out + row * W + col4, o);
-                    }
+                    for (int q = 0; q < 4; ++q)
+                        if (c + q < a.mo) a.y[row * a.ldy + c + q] = float(o[q]);
+                } else {
+                    st4<T>(a.out + row * W + c, o);
                 }
-                if (GRAM) st4<T>(sO + (row0 + r) * G::LDO + col4, o);
             }
         } else {
             // PROJ: stage X and Qa tiles
@@ -268,6 +297,7 @@ int launch_w(int mode, const RowArgs<T> &a, cudaStream_t s, int *grid_out) {
         case RB_MULGRAM: return launch_wm<T, W, RB_MULGRAM>(a, s, grid_out);
         case RB_MUL: return launch_wm<T, W, RB_MUL>(a, s, grid_out);
         case RB_ASM: return launch_wm<T, W, RB_ASM>(a, s, grid_out);
+        case RB_ASMSUB: return launch_wm<T, W, RB_ASMSUB>(a, s, grid_out);
     }
     return fail(KB_ERR_ARG, "bad row-block mode");
 }
@@ -281,7 +311,8 @@ int max_grid_w() {
 // ---------------------------------------------------------------- deterministic reduction
 template <typename P>
 __global__ void __launch_bounds__(256) k_reduce(const P *__restrict__ parts, int nparts, int len,
-                                                 double *__restrict__ out, const Ctrl *ctrl) {
+                                                 double *__restrict__ out, const Ctrl *ctrl,
+                                                 P *__restrict__ out_p) {
     if (ctrl && ctrl->stop) return;
     __shared__ double s[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -296,6 +327,7 @@ __global__ void __launch_bounds__(256) k_reduce(const P *__restrict__ parts, int
 #pragma unroll
         for (int w = 0; w < 8; ++w) t += s[w][lane];
         out[e] = t;
+        if (out_p) out_p[e] = P(t);
     }
 }
 
@@ -329,6 +361,7 @@ int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *g
         case RB_MULGRAM: bytes = 2 * blk; flops = 2 * mm; break;
         case RB_MUL: bytes = 2 * blk; flops = mm; break;
         case RB_ASM: bytes = (a.nblk + 1) * blk; flops = a.nblk * mm; break;
+        case RB_ASMSUB: bytes = (a.nblk + 2) * blk; flops = a.nblk * mm + mm; break;
     }
     prof_end(cls, s, bytes, flops);
     return 0;
@@ -348,9 +381,9 @@ int rowblock_max_grid(int W) {
 
 template <typename P>
 int launch_reduce(const P *parts, int nparts, int len, double *out, cudaStream_t s,
-                  const Ctrl *ctrl) {
+                  const Ctrl *ctrl, P *out_p) {
     prof_begin(KernelClass::REDUCE, s);
-    k_reduce<P><<<(len + 31) / 32, 256, 0, s>>>(parts, nparts, len, out, ctrl);
+    k_reduce<P><<<(len + 31) / 32, 256, 0, s>>>(parts, nparts, len, out, ctrl, out_p);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "k_reduce launch");
     prof_end(KernelClass::REDUCE, s, double(nparts) * len * sizeof(P), 0);
@@ -361,7 +394,7 @@ template int launch_rowblock<float>(int, int, const RowArgs<float> &, cudaStream
 template int launch_rowblock<double>(int, int, const RowArgs<double> &, cudaStream_t, int *, int64_t);
 template int rowblock_max_grid<float>(int);
 template int rowblock_max_grid<double>(int);
-template int launch_reduce<float>(const float *, int, int, double *, cudaStream_t, const Ctrl *);
-template int launch_reduce<double>(const double *, int, int, double *, cudaStream_t, const Ctrl *);
+template int launch_reduce<float>(const float *, int, int, double *, cudaStream_t, const Ctrl *, float *);
+template int launch_reduce<double>(const double *, int, int, double *, cudaStream_t, const Ctrl *, double *);
 
 }  // namespace kb

@@ -17,6 +17,24 @@
 
 namespace kb {
 
+// ---------------------------------------------------------------- 16-byte vector access
+__device__ __forceinline__ void ldv4(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ldv4(const double *p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    const double2 b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void stv4(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void stv4(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
 // ---------------------------------------------------------------- control / init
 __global__ void k_ctrl_init(Ctrl *c, int steps) {
     c->status = KB_OK;
@@ -66,30 +84,46 @@ __global__ void k_hkk(const double *G, int M, int W, double *Hd, T *C, const Ctr
     }
 }
 
-// X = U^{-1} for an upper triangular M x M matrix U (ld ldu), X with ld ldx; thread c
-// computes column c by back substitution (the sum for row i uses rows i+1..c).
-__device__ void tri_inv_upper(const double *U, int ldu, double *X, int ldx, int M) {
-    for (int c = threadIdx.x; c < M; c += blockDim.x) {
-        X[c * ldx + c] = 1.0 / U[c * ldu + c];
-        for (int i = c - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int j = i + 1; j <= c; ++j) s += U[i * ldu + j] * X[j * ldx + c];
-            X[i * ldx + c] = -s / U[i * ldu + i];
+// In-place inverse of an upper triangular M x M matrix in shared memory (ld lda), column
+// by column: with the leading j x j block already inverted, column j of the inverse is
+// -(1/a_jj) X_{0:j,0:j} a_{0:j,j}.  Each row's dot product is split over TPR consecutive
+// lanes (TPR = 1, 2, 4 or 8) and combined with shuffles.  t: shared scratch of M doubles.
+__device__ void tri_inv_upper_inplace(double *A, int lda, int M, double *t) {
+    int TPR = 1;
+    while (TPR < 8 && TPR * 2 * M <= int(blockDim.x)) TPR *= 2;
+    const int sub = threadIdx.x % TPR;
+    const int row0 = threadIdx.x / TPR;
+    const int rstride = blockDim.x / TPR;
+    for (int j = 0; j < M; ++j) {
+        for (int i = threadIdx.x; i < j; i += blockDim.x) t[i] = A[i * lda + j];
+        __syncthreads();
+        const double ajj = 1.0 / A[j * lda + j];
+        // rows i < j, all TPR lanes of a row iterate together (uniform loop bound per warp)
+        for (int ib = 0; ib < j; ib += rstride) {
+            const int i = ib + row0;
+            double acc = 0.0;
+            if (i < j)
+                for (int k = i + sub; k < j; k += TPR) acc = fma(A[i * lda + k], t[k], acc);
+            for (int off = 1; off < TPR; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (i < j && sub == 0) A[i * lda + j] = -ajj * acc;
         }
-        for (int i = c + 1; i < M; ++i) X[i * ldx + c] = 0.0;
+        __syncthreads();
+        if (threadIdx.x == 0) A[j * lda + j] = ajj;
+        __syncthreads();
     }
 }
 
 // Cholesky G = R^T R (upper R) of the leading M x M block in shared memory, then R^{-1}.
 template <typename T>
-__global__ void k_chol(const double *G, int M, int W, int pass, int step, double inv_thresh2,
-                       double piv_rel2, double *R1, double *Rinv64, T *Rinv, double *Hs, T *Bout,
-                       Ctrl *ctrl) {
+__global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int pass, int step,
+                                              double inv_thresh2, double piv_rel2, double *R1,
+                                              T *Rinv, double *Hs, T *Bout, Ctrl *ctrl) {
     if (ctrl->stop) return;
-    extern __shared__ double A[];   // [M][M+1]
+    extern __shared__ double A[];   // [M][M+1], then t[M]
     __shared__ int bad;
     __shared__ double maxdiag;
     const int lda = M + 1;
+    double *t = A + M * lda;
     for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
         const int i = idx / M, j = idx % M;
         A[i * lda + j] = G[i * W + j];
@@ -119,41 +153,48 @@ __global__ void k_chol(const double *G, int M, int W, int pass, int step, double
                 ctrl->steps = step;
                 ctrl->breakdown_step = step;
             } else {
-                A[j * lda + j] = sqrt(d);
+                const double r = sqrt(d);
+                A[j * lda + j] = r;
+                t[0] = 1.0 / r;
             }
         }
         __syncthreads();
         if (bad) return;
-        const double r = A[j * lda + j];
-        for (int c = j + 1 + threadIdx.x; c < M; c += blockDim.x) A[j * lda + c] /= r;
+        const double rinv = t[0];
+        for (int c = j + 1 + threadIdx.x; c < M; c += blockDim.x) A[j * lda + c] *= rinv;
         __syncthreads();
         const int L = M - j - 1;
-        for (int idx = threadIdx.x; idx < L * L; idx += blockDim.x) {
-            const int a = j + 1 + idx / L, b = j + 1 + idx % L;
-            if (b >= a) A[a * lda + b] -= A[j * lda + a] * A[j * lda + b];
+        const int npairs = L * (L + 1) / 2;
+        for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
+            // idx -> (a, b), a <= b, in the trailing upper triangle (FP32 root estimate,
+            // corrected exactly in integers)
+            int a = int((sqrtf(8.f * float(idx) + 1.f) - 1.f) * 0.5f);
+            while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+            while (a * (a + 1) / 2 > idx) --a;
+            const int b = idx - a * (a + 1) / 2;   // 0 <= b <= a
+            const int ra = j + 1 + b, rb = j + 1 + a;   // ra <= rb
+            A[ra * lda + rb] -= A[j * lda + ra] * A[j * lda + rb];
         }
         __syncthreads();
     }
-    // R^{-1} (upper triangular): column c by back substitution (thread c)
-    tri_inv_upper(A, lda, Rinv64, W, M);
+    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+        const int i = idx / M, j = idx % M;
+        if (j < i) A[i * lda + j] = 0.0;
+    }
     __syncthreads();
+    // R^{-1} (upper triangular), in place
+    tri_inv_upper_inplace(A, lda, M, t);
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
         const int i = idx / W, j = idx % W;
-        Rinv[idx] = (i < M && j < M && j >= i) ? T(Rinv64[idx]) : T(0);
+        const T v = (i < M && j < M && j >= i) ? T(A[i * lda + j]) : T(0);
+        Rinv[idx] = v;
+        if (i < M && j < M) A[i * lda + j] = double(v);
     }
     __syncthreads();
-    if (sizeof(T) == 4) {
-        // The row-block kernels apply the FP32-rounded inverse.  Record the factor that is
-        // actually applied, the FP64 inverse of the rounded inverse, so that
-        // X = Q_{k+1} H_{k+1,k} holds for the stored blocks up to FP32 rounding of Q.
-        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-            const int i = idx / M, j = idx % M;
-            Rinv64[i * W + j] = (j >= i) ? double(float(Rinv64[i * W + j])) : 0.0;
-        }
-        __syncthreads();
-        tri_inv_upper(Rinv64, W, A, lda, M);
-        __syncthreads();
-    }
+    // The row-block kernels apply the inverse rounded to the basis precision.  Record the
+    // factor actually applied, the FP64 inverse of the rounded inverse, so that
+    // X = Q_{k+1} H_{k+1,k} holds for the stored blocks up to the rounding of Q.
+    tri_inv_upper_inplace(A, lda, M, t);
     if (pass == 1) {
         for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
             const int i = idx / M, j = idx % M;
@@ -166,7 +207,7 @@ __global__ void k_chol(const double *G, int M, int W, int pass, int step, double
             const int i = idx / W, j = idx % W;
             double h = 0.0;
             if (i < M && j < M && j >= i) {
-                for (int k = i; k <= j; ++k) h += A[i * lda + k] * R1[k * M + j];
+                for (int k = i; k <= j; ++k) h = fma(A[i * lda + k], __ldg(R1 + k * M + j), h);
             }
             const T ht = T(h);
             if (i < M && j < M) Hs[i * M + j] = double(ht);
@@ -387,14 +428,26 @@ __global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const do
         al[q] = T(a[c4 + q] - double(ah[q]));
     }
     T acc[4] = {0, 0, 0, 0};
-    for (int64_t row = int64_t(blockIdx.x) * RPP + rr; row < n; row += int64_t(gridDim.x) * RPP) {
-        T *xp = X + row * W + c4;
-        const T *pp = P + row * W + c4;
+    // two rows per iteration, 16-byte vector accesses: four loads in flight per thread
+    const int64_t stride = int64_t(gridDim.x) * RPP;
+    for (int64_t row = int64_t(blockIdx.x) * RPP + rr; row < n; row += 2 * stride) {
+        const int64_t row2 = row + stride;
+        T xv[2][4], pv[2][4];
+        ldv4(X + row * W + c4, xv[0]);
+        ldv4(P + row * W + c4, pv[0]);
+        if (row2 < n) {
+            ldv4(X + row2 * W + c4, xv[1]);
+            ldv4(P + row2 * W + c4, pv[1]);
+        }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const T v = xp[q] - fma(ah[q], pp[q], al[q] * pp[q]);
-            xp[q] = v;
-            acc[q] = fma(v, v, acc[q]);
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && row2 >= n) break;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                xv[h][q] = xv[h][q] - fma(ah[q], pv[h][q], al[q] * pv[h][q]);
+                acc[q] = fma(xv[h][q], xv[h][q], acc[q]);
+            }
+            stv4(X + (h ? row2 : row) * W + c4, xv[h]);
         }
     }
 #pragma unroll
@@ -509,18 +562,18 @@ int launch_hkk(const double *G, int M, int W, double *Hd, T *C, const Ctrl *ctrl
 
 template <typename T>
 int launch_chol(const double *G, int M, int W, int pass, int step, double inv_thresh2,
-                double piv_rel2, double *R1, double *Rinv64, T *Rinv, double *Hs, T *Bout,
-                Ctrl *ctrl, cudaStream_t s) {
-    const size_t smem = sizeof(double) * size_t(M) * (M + 1);
+                double piv_rel2, double *R1, T *Rinv, double *Hs, T *Bout, Ctrl *ctrl,
+                cudaStream_t s) {
+    const size_t smem = sizeof(double) * (size_t(M) * (M + 1) + M);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(sizeof(double) * 128 * 129));
+                             int(sizeof(double) * (128 * 129 + 128)));
         attr = true;
     }
     prof_begin(KernelClass::SMALL, s);
-    k_chol<T><<<1, 256, smem, s>>>(G, M, W, pass, step, inv_thresh2, piv_rel2, R1, Rinv64, Rinv,
-                                   Hs, Bout, ctrl);
+    k_chol<T><<<1, 256, smem, s>>>(G, M, W, pass, step, inv_thresh2, piv_rel2, R1, Rinv, Hs,
+                                   Bout, ctrl);
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::SMALL, s, 0, 0);
     return 0;
@@ -631,7 +684,7 @@ int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ct
     template int launch_scale_copy<T>(T *, const T *, int64_t, double, cudaStream_t);           \
     template int launch_hkk<T>(const double *, int, int, double *, T *, const Ctrl *, cudaStream_t); \
     template int launch_chol<T>(const double *, int, int, int, int, double, double, double *,   \
-                                double *, T *, double *, T *, Ctrl *, cudaStream_t);            \
+                                T *, double *, T *, Ctrl *, cudaStream_t);                      \
     template int launch_axpy_colnorm<T>(int, T *, const T *, const double *, int64_t, double *, \
                                         int *, const Ctrl *, cudaStream_t);                     \
     template int launch_assemble_diag<T>(int, const T *, int64_t, int, const double *, int64_t, \

@@ -3,14 +3,15 @@
 // This is the "MV" of Table 1 (Section 7), the operation the paper names the most
 // expensive for large graphs; every method performs m of them per solve.
 //
-// Schedule (GB300).  A row of x is W elements; W/4 lanes cover it with one 16-byte
-// vector each (float4, or 2 x double2), so a warp works on 32/(W/4) rows at once, one
-// lane group per row.  A group first loads up to W/4 column indices (and weights) of its
-// row with one coalesced load, then walks them U at a time: the U neighbour rows are
-// gathered with independent 16-byte loads before any is consumed, which keeps 4 x 16 B
-// per lane in flight instead of one dependent index->row chain.  Groups of a warp run
-// different rows and never wait for each other (group-masked shuffles).  The grid is
-// persistent (a multiple of the SM count).
+// Schedule (GB300).  A CTA owns a tile of consecutive rows at a time (persistent grid,
+// a multiple of the SM count).  The tile's row pointers and then all its column indices
+// (and weights) are staged in shared memory with coalesced loads, so a row's neighbour
+// list costs no dependent global round trip.  A row of x is W elements; W/8 lanes cover it
+// with two 16-byte vectors each (float4, or 2 x double2), so each warp works on 32/(W/8)
+// rows at once, one lane group per row; a group reads its neighbour indices from shared
+// memory (broadcast) and gathers two neighbour rows with independent 16-byte loads before
+// consuming them.  The register budget is sized for 5 resident CTAs (40 warps) per SM.  Rows of a tile whose column list does not fit in shared memory
+// (hub rows) read their indices from global memory instead.
 //
 // The Laplacian is applied in difference form (L x)_i = sum_j w_ij (x_i - x_j) + r_i x_i,
 // which gives L 1 = 0 exactly for D - A and drops the diagonal load for standard
@@ -45,157 +46,199 @@ template <> struct V4<double> {
     }
 };
 
-template <typename T>
-__device__ __forceinline__ void split(double d, T &hi, T &lo) {
-    hi = T(d);
-    lo = T(d - double(hi));
-}
-
 constexpr int SPMM_THREADS = 256;
-constexpr int UNROLL = 4;
+constexpr int WARPS = SPMM_THREADS / 32;
+constexpr int CAP = 4096;       // staged column indices per tile
+constexpr int VPL = 2;          // 16-byte vectors per lane (8 elements of a row)
+constexpr int U = 2;            // neighbour rows gathered per lane before use
 
-template <typename T, int W>
-__global__ void __launch_bounds__(SPMM_THREADS)
+template <int W>
+struct SpmmGeo {
+    static constexpr int LPR = W / (4 * VPL);            // lanes per row
+    static constexpr int RPW = 32 / LPR;                 // rows per warp
+    static constexpr int NG = WARPS * RPW;               // lane groups per CTA
+    static constexpr int RPG = W >= 64 ? 4 : (W == 32 ? 2 : 1);   // rows per group per tile
+    static constexpr int TR = NG * RPG;                  // rows per tile
+};
+
+// Resident CTAs per SM the register budget is sized for: the FP32 kernel without column
+// dot products fits 5 (40 warps), the others fewer.
+template <typename T, bool DOT>
+struct SpmmOcc {
+    static constexpr int value = sizeof(T) == 8 ? 3 : (DOT ? 4 : 5);
+};
+
+template <typename T, int W, bool DOT>
+__global__ void __launch_bounds__(SPMM_THREADS, (SpmmOcc<T, DOT>::value))
 k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
-    constexpr int LPR = W / 4;       // lanes per row
-    constexpr int RPW = 32 / LPR;    // rows per warp
+    using G = SpmmGeo<W>;
+    constexpr int LPR = G::LPR, RPW = G::RPW, NG = G::NG, TR = G::TR, RPG = G::RPG;
     if (e.ctrl && e.ctrl->stop) return;
-    __shared__ double sdot[SPMM_THREADS / 32][W];
-    const int lane = threadIdx.x & 31;
-    const int sub = lane % LPR;
-    const int grp = lane / LPR;
-    const int c4 = sub * 4;
-    const unsigned gmask = (LPR == 32) ? 0xffffffffu : (((1u << LPR) - 1u) << (grp * LPR));
-    T c1h[4], c1l[4], c0[4], c2h[4], c2l[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        split<T>(e.a1 ? e.a1[c4 + q] : e.s1, c1h[q], c1l[q]);
-        c0[q] = T(e.a0 ? e.a0[c4 + q] : e.s0);
-        split<T>(e.a2 ? e.a2[c4 + q] : e.s2, c2h[q], c2l[q]);
+    __shared__ int s_rp[TR + 1];
+    __shared__ int s_col[CAP];
+    __shared__ float s_w[CAP];
+    __shared__ __align__(16) T s_coef[5][W];       // c1 hi, c1 lo, c0, c2 hi, c2 lo
+    __shared__ double s_dot[WARPS][W];
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+        const double d1 = e.a1 ? e.a1[c] : e.s1;
+        const double d2 = e.a2 ? e.a2[c] : e.s2;
+        const T h1 = T(d1), h2 = T(d2);
+        s_coef[0][c] = h1;
+        s_coef[1][c] = T(d1 - double(h1));
+        s_coef[2][c] = T(e.a0 ? e.a0[c] : e.s0);
+        s_coef[3][c] = h2;
+        s_coef[4][c] = T(d2 - double(h2));
     }
-    const T s3 = T(e.s3);
-    const T wE = T(e.wE);
-    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    T dot[4] = {0, 0, 0, 0};
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int grp = lane / LPR;
+    const int cb = (lane % LPR) * (4 * VPL);   // first column of this lane
+    const int gid = warp * RPW + grp;
+    T dot[VPL][4];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dot[v][q] = T(0);
+    const int64_t ntiles = (g.n + TR - 1) / TR;
 
-    for (int64_t base = warp * RPW; base < g.n; base += nwarps * RPW) {
-        const int64_t row = base + grp;
-        const bool active = row < g.n;
-        const int beg = active ? __ldg(g.rowptr + row) : 0;
-        const int end = active ? __ldg(g.rowptr + row + 1) : 0;
-        V4<T> xi;
-        if (active) xi = V4<T>::load(x + row * W + c4);
-        else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) xi.v[q] = T(0);
-        }
-        T acc[4] = {0, 0, 0, 0};
-        for (int p0 = beg; p0 < end; p0 += LPR) {
-            const int myp = p0 + sub;
-            const int jj = myp < end ? __ldg(g.col + myp) : 0;
-            const T ww = (myp < end && g.w) ? T(__ldg(g.w + myp)) : T(1);
-            const int cnt = min(LPR, end - p0);
-            for (int q0 = 0; q0 < cnt; q0 += UNROLL) {
-                int j[UNROLL];
-                T wv[UNROLL];
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) {
-                    const int src = grp * LPR + min(q0 + u, LPR - 1);
-                    j[u] = __shfl_sync(gmask, jj, src);
-                    wv[u] = __shfl_sync(gmask, ww, src);
-                }
-                V4<T> xj[UNROLL];
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u)
-                    if (q0 + u < cnt) xj[u] = V4<T>::load(x + int64_t(j[u]) * W + c4);
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u)
-                    if (q0 + u < cnt)
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[q] = fma(wv[u], xi.v[q] - xj[u].v[q], acc[q]);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * TR;
+        const int rows = (g.n - r0 < TR) ? int(g.n - r0) : TR;
+        __syncthreads();   // previous tile done with the shared arrays
+        for (int i = threadIdx.x; i <= rows; i += blockDim.x) s_rp[i] = __ldg(g.rowptr + r0 + i);
+        __syncthreads();
+        const int base = s_rp[0];
+        const int cnt = s_rp[rows] - base;
+        const bool staged = cnt <= CAP;
+        if (staged) {
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                s_col[i] = __ldg(g.col + base + i);
+                if (g.w) s_w[i] = __ldg(g.w + base + i);
             }
         }
-        if (!active) continue;
-        if (g.rdiag) {
-            const T r = T(__ldg(g.rdiag + row));
+        __syncthreads();
+#pragma unroll 1
+        for (int rr = 0; rr < RPG; ++rr) {
+            const int lrow = rr * NG + gid;
+            if (lrow >= rows) continue;
+            const int64_t row = r0 + lrow;
+            const int beg = s_rp[lrow] - base;
+            const int end = s_rp[lrow + 1] - base;
+            V4<T> xi[VPL];
+            T acc[VPL][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fma(r, xi.v[q], acc[q]);
-        }
-        T o[4];
+            for (int v = 0; v < VPL; ++v) {
+                xi[v] = V4<T>::load(x + row * W + cb + 4 * v);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) o[q] = fma(c1h[q], acc[q], fma(c1l[q], acc[q], c0[q] * xi.v[q]));
-        if (e.y) {
-            const V4<T> yi = V4<T>::load(e.y + row * W + c4);
+                for (int q = 0; q < 4; ++q) acc[v][q] = T(0);
+            }
+            for (int p = beg; p < end; p += U) {
+                V4<T> xj[U][VPL];
+                T wv[U];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = fma(c2h[q], yi.v[q], fma(c2l[q], yi.v[q], o[q]));
-        }
-        if (e.z) {
-            const V4<T> zi = V4<T>::load(e.z + row * W + c4);
+                for (int u = 0; u < U; ++u) {
+                    if (p + u < end) {
+                        const int j = staged ? s_col[p + u] : __ldg(g.col + base + p + u);
+                        wv[u] = g.w ? T(staged ? s_w[p + u] : __ldg(g.w + base + p + u)) : T(1);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = fma(s3, zi.v[q], o[q]);
-        }
-        if (e.marker) {
-            const int mk = __ldg(e.marker + row);
-            if (mk >= c4 && mk < c4 + 4) o[mk - c4] += wE;
-        }
-        if (!e.yout) {
-            V4<T> ov;
+                        for (int v = 0; v < VPL; ++v) xj[u][v] = V4<T>::load(x + int64_t(j) * W + cb + 4 * v);
+                    }
+                }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ov.v[q] = o[q];
-            ov.store(e.out + row * W + c4);
-        } else {
+                for (int u = 0; u < U; ++u)
+                    if (p + u < end)
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (c4 + q < mo) e.yout[row * ldo + c4 + q] = float(o[q]);
-        }
-        if (e.dot_partials) {
+                        for (int v = 0; v < VPL; ++v)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dot[q] = fma(xi.v[q], o[q], dot[q]);
+                            for (int q = 0; q < 4; ++q)
+                                acc[v][q] = fma(wv[u], xi[v].v[q] - xj[u][v].v[q], acc[v][q]);
+            }
+            const T r = g.rdiag ? T(__ldg(g.rdiag + row)) : T(0);
+            const int mk = e.marker ? __ldg(e.marker + row) : -1;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                const int c = cb + 4 * v;
+                T o[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const T a = fma(r, xi[v].v[q], acc[v][q]);
+                    o[q] = fma(s_coef[0][c + q], a, fma(s_coef[1][c + q], a, s_coef[2][c + q] * xi[v].v[q]));
+                }
+                if (e.y) {
+                    const V4<T> yi = V4<T>::load(e.y + row * W + c);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        o[q] = fma(s_coef[3][c + q], yi.v[q], fma(s_coef[4][c + q], yi.v[q], o[q]));
+                }
+                if (e.z) {
+                    const V4<T> zi = V4<T>::load(e.z + row * W + c);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) o[q] = fma(T(e.s3), zi.v[q], o[q]);
+                }
+                if (mk >= c && mk < c + 4) o[mk - c] += T(e.wE);
+                if (!e.yout) {
+                    V4<T> ov;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) ov.v[q] = o[q];
+                    ov.store(e.out + row * W + c);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (c + q < mo) e.yout[row * ldo + c + q] = float(o[q]);
+                }
+                if (DOT) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dot[v][q] = fma(xi[v].v[q], o[q], dot[v][q]);
+                }
+            }
         }
     }
-    if (e.dot_partials) {
-        double dd[4];
+    if (DOT) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            dd[q] = double(dot[q]);
+        for (int v = 0; v < VPL; ++v)
 #pragma unroll
-            for (int off = LPR; off < 32; off <<= 1) dd[q] += __shfl_xor_sync(0xffffffffu, dd[q], off);
-        }
-        const int wib = threadIdx.x >> 5;
-        if (grp == 0)
+            for (int q = 0; q < 4; ++q) {
+                double dd = double(dot[v][q]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) sdot[wib][c4 + q] = dd[q];
+                for (int off = LPR; off < 32; off <<= 1) dd += __shfl_xor_sync(0xffffffffu, dd, off);
+                if (grp == 0) s_dot[warp][cb + 4 * v + q] = dd;
+            }
         __syncthreads();
         for (int c = threadIdx.x; c < W; c += blockDim.x) {
             double s = 0.0;
-            for (int w2 = 0; w2 < SPMM_THREADS / 32; ++w2) s += sdot[w2][c];
+            for (int w2 = 0; w2 < WARPS; ++w2) s += s_dot[w2][c];
             e.dot_partials[int64_t(blockIdx.x) * W + c] = s;
         }
     }
 }
 
-template <typename T, int W>
+template <typename T, int W, bool DOT>
 int occupancy_spmm() {
     static int per_sm = -1;
     if (per_sm < 0) {
         int v = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmm<T, W>, SPMM_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmm<T, W, DOT>, SPMM_THREADS, 0);
         per_sm = v < 1 ? 1 : v;
     }
     return per_sm;
 }
 
+template <typename T, int W, bool DOT>
+int launch_wd(const GraphDev &g, const T *x, const LinEpi<T> &e, int64_t ldo, int mo,
+              cudaStream_t s, int *grid_out) {
+    const int64_t ntiles = (g.n + SpmmGeo<W>::TR - 1) / SpmmGeo<W>::TR;
+    int grid = int(std::min<int64_t>(ntiles, int64_t(num_sms()) * occupancy_spmm<T, W, DOT>()));
+    if (grid < 1) grid = 1;
+    if (grid_out) *grid_out = grid;
+    k_spmm<T, W, DOT><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
+    return 0;
+}
+
 template <typename T, int W>
 int launch_w(const GraphDev &g, const T *x, const LinEpi<T> &e, int64_t ldo, int mo,
              cudaStream_t s, int *grid_out) {
-    constexpr int RPB = (SPMM_THREADS / 32) * (32 / (W / 4));   // rows per block pass
-    const int64_t need = (g.n + RPB - 1) / RPB;
-    int grid = int(std::min<int64_t>(need, int64_t(num_sms()) * occupancy_spmm<T, W>()));
-    if (grid < 1) grid = 1;
-    if (grid_out) *grid_out = grid;
-    k_spmm<T, W><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
-    return 0;
+    return e.dot_partials ? launch_wd<T, W, true>(g, x, e, ldo, mo, s, grid_out)
+                          : launch_wd<T, W, false>(g, x, e, ldo, mo, s, grid_out);
 }
 
 }  // namespace
@@ -226,11 +269,12 @@ int launch_spmm(const GraphDev &g, int W, const T *x, const LinEpi<T> &e, cudaSt
 
 template <typename T>
 int spmm_max_grid(int W) {
+    // dot partials are written only by the DOT variant; its grid bounds the buffer
     switch (W) {
-        case 16: return num_sms() * occupancy_spmm<T, 16>();
-        case 32: return num_sms() * occupancy_spmm<T, 32>();
-        case 64: return num_sms() * occupancy_spmm<T, 64>();
-        default: return num_sms() * occupancy_spmm<T, 128>();
+        case 16: return num_sms() * occupancy_spmm<T, 16, true>();
+        case 32: return num_sms() * occupancy_spmm<T, 32, true>();
+        case 64: return num_sms() * occupancy_spmm<T, 64, true>();
+        default: return num_sms() * occupancy_spmm<T, 128, true>();
     }
 }
 

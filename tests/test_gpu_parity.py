@@ -214,6 +214,44 @@ def test_path_single_column_all_lanczos_agree(kb):
         assert _rel(Y64, ref) < 1e-7
 
 
+# ---------------------------------------------------------------- full reorthogonalisation
+@pytest.mark.parametrize("phi,kw", [("exp", dict(t=1.0)), ("spline", dict(eps=0.5, s=2.0))])
+@pytest.mark.parametrize("M", [8, 64])
+def test_cbl_full_reorthogonalisation_parity(kb, phi, kw, M):
+    g = synth.barabasi_albert_graph(4000, 5, seed=31, weighted=True)
+    nodes = synth.sample_nodes(g.n, M, seed=32)
+    L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
+    ref = krylov.apply("cbl", L, nodes, 12, phi, reorth=True, **kw).Y
+    with kb.Graph.from_csr(g) as G:
+        lam = G.lambda_max
+        Y = _gpu(kb, G, "cbl", phi, nodes, 12, reorth=1, **kw)
+        Y64 = _gpu(kb, G, "cbl", phi, nodes, 12, reorth=1, basis="f64", **kw)
+    assert _rel(Y, ref) < tol32(phi, lam, **kw)
+    assert _rel(Y64, ref) < 1e-7
+
+
+def test_reorthogonalisation_keeps_long_runs_accurate(kb):
+    # a long run on a small graph: loss of orthogonality in FP32 without reorthogonalisation,
+    # agreement with the reorthogonalised FP64 oracle with it
+    g = synth.random_geometric_graph(600, 8, seed=33)
+    nodes = synth.sample_nodes(g.n, 4, seed=34)
+    L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
+    ref = krylov.apply("cbl", L, nodes, 40, "exp", t=0.5, reorth=True).Y
+    with kb.Graph.from_csr(g) as G:
+        Yr = _gpu(kb, G, "cbl", "exp", nodes, 40, t=0.5, reorth=1)
+    assert _rel(Yr, ref) < TOL32
+
+
+def test_reorth_rejected_for_other_methods(kb):
+    import torch
+    g = synth.path_graph(40)
+    with kb.Graph.from_csr(g) as G:
+        Y = torch.empty((40, 2), dtype=torch.float32, device="cuda")
+        with pytest.raises(kb.KbError) as ei:
+            kb.kb_krylov_apply(G, "gbl", "exp", kb.make_params(t=1.0, reorth=1), np.array([3, 9]), 2, 5, Y)
+        assert ei.value.code == -7
+
+
 # ---------------------------------------------------------------- plain FP64 mode
 @pytest.mark.parametrize("method", METHODS)
 def test_fp64_mode_parity(kb, method):
