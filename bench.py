@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="steps of the plain FP64 GPU mode timed for comparison (0 = skip)")
     ap.add_argument("--ref-sample-cols", type=int, default=4)
+    ap.add_argument("--no-frontier", action="store_true",
+                    help="touch all n rows at every step (disables the exact frontier restriction)")
     ap.add_argument("--streams", type=int, default=1,
                     help="CUDA streams the independent solves of a step are spread over")
     return ap.parse_args()
@@ -66,7 +68,8 @@ def workload_config(a):
             "t": [float(x) for x in a.ts.split(",")], "methods": a.methods.split(","),
             "graph_seed": a.graph_seed, "node_seed": a.node_seed, "basis": a.basis,
             "l2": "256 MiB flush write between steps; per-solve working set > L2",
-            "streams": a.streams}
+            "streams": a.streams,
+            "frontier": not a.no_frontier}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -235,7 +238,7 @@ def main():
     solves = [(mth, t) for mth in methods for t in ts]
     Ys = [torch.empty((a.n, a.M), dtype=torch.float32, device="cuda") for _ in solves]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    params = {t: kb.make_params(t=t, basis=a.basis) for t in ts}
+    params = {t: kb.make_params(t=t, basis=a.basis, no_frontier=int(a.no_frontier)) for t in ts}
 
     def step(pr=params):
         # independent solves round-robin over the streams; every stream joins the main one
@@ -322,7 +325,7 @@ def main():
     # plain FP64 GPU mode (the comparator of the mixed-precision form), same solves
     fp64 = None
     if a.fp64_steps > 0 and a.basis == "f32":
-        p64 = {t: kb.make_params(t=t, basis="f64") for t in ts}
+        p64 = {t: kb.make_params(t=t, basis="f64", no_frontier=int(a.no_frontier)) for t in ts}
         try:
             step(p64)
             torch.cuda.synchronize()

@@ -62,7 +62,13 @@ typedef struct {
                            all earlier blocks, classical Gram-Schmidt applied twice (not in the
                            paper; needed in finite precision for long runs); 0 = none           */
     int32_t basis;      /* kb_dtype of the stored Krylov blocks: KB_F32 (FP32 arithmetic),
-                           KB_F64 (plain FP64 arithmetic throughout)                              */
+                           KB_BF16 (blocks stored in bfloat16, arithmetic in FP32, small
+                           matrices as for KB_F32; relative error of order 1e-3 to 1e-2, set
+                           by the bfloat16 rounding of every stored element), KB_F64 (plain
+                           FP64 arithmetic throughout); any other value is KB_ERR_ARG         */
+    int32_t no_frontier;/* 0 (default): the products and block updates of step k touch only
+                           rows within k hops of W (the Krylov blocks are exactly zero
+                           elsewhere); 1: every step touches all n rows                           */
 } kb_params;
 
 typedef struct {
@@ -133,8 +139,9 @@ int kb_graph_info(const kb_graph *g, int64_t *n, int64_t *nnz_offdiag, double *l
  *           rank-deficient block (then Y is filled with NaN).  With info == NULL the call
  *           does not synchronise, and a breakdown shows only as NaN in Y.
  *
- * Not implemented (KB_ERR_UNSUPPORTED): KB_CBL with KB_PHI_SPLINE and non-integer s;
- * params->basis other than KB_F32 / KB_F64; reorth with methods other than KB_CBL.
+ * Not implemented (KB_ERR_UNSUPPORTED): the Lanczos methods with KB_PHI_SPLINE and
+ * non-integer s (or s > 64); reorth with methods other than KB_CBL; KB_CBL / KB_GBL with
+ * M > 128 (M > 64 for KB_F64).
  * Other errors: KB_ERR_ARG, KB_ERR_NODES, KB_ERR_NOMEM, KB_ERR_CUDA.
  */
 int kb_krylov_apply(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,

@@ -44,10 +44,13 @@ int num_sms() {
 
 // ---------------------------------------------------------------- profiling
 namespace {
+constexpr int PROF_SLOTS = 1 << 16;   // device work counters available per profile read
 struct ProfRec {
     int cls;
     cudaEvent_t a, b;
-    double bytes, flops;
+    double bytes, flops;        // full-size values (used when the slot has no counter)
+    int slot;                   // -1: no device counter
+    double per_row, per_nnz, flops_per_row, fixed;
 };
 std::mutex g_prof_mu;
 bool g_prof = false;
@@ -55,6 +58,9 @@ std::vector<ProfRec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 cudaEvent_t g_pending = nullptr;
 int g_pending_cls = -1;
+int g_pending_slot = -1;
+unsigned long long *g_counters = nullptr;   // [PROF_SLOTS][2] rows, nnz (device)
+int g_next_slot = 0;
 
 cudaEvent_t take_event() {
     if (!g_pool.empty()) {
@@ -70,25 +76,36 @@ cudaEvent_t take_event() {
 
 bool prof_on() { return g_prof; }
 
-void prof_begin(int cls, cudaStream_t s) {
-    if (!g_prof) return;
+ProfCount prof_begin(int cls, cudaStream_t s) {
+    ProfCount pc;
+    if (!g_prof) return pc;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_pending = take_event();
     g_pending_cls = cls;
+    g_pending_slot = -1;
+    if (g_counters && g_next_slot < PROF_SLOTS) {
+        g_pending_slot = g_next_slot++;
+        pc.rows = g_counters + 2 * size_t(g_pending_slot);
+        pc.nnz = pc.rows + 1;
+    }
     cudaEventRecord(g_pending, s);
+    return pc;
 }
 
 std::atomic<long long> g_launches{0};
 void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
-void prof_end(int cls, cudaStream_t s, double bytes, double flops, int nlaunch) {
+void prof_end(int cls, cudaStream_t s, double bytes, double flops, int nlaunch, double per_row,
+              double per_nnz, double flops_per_row, double fixed) {
     count_launches(nlaunch);
     if (!g_prof) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_pending || g_pending_cls != cls) return;
     cudaEvent_t b = take_event();
     cudaEventRecord(b, s);
-    g_recs.push_back(ProfRec{cls, g_pending, b, bytes, flops});
+    const bool counted = per_row > 0.0 || per_nnz > 0.0 || flops_per_row > 0.0;
+    g_recs.push_back(ProfRec{cls, g_pending, b, bytes, flops, counted ? g_pending_slot : -1,
+                             per_row, per_nnz, flops_per_row, fixed});
     g_pending = nullptr;
 }
 
@@ -299,6 +316,15 @@ extern "C" int kb_version(void) { return 10000; }
 
 extern "C" int kb_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> lk(kb::g_prof_mu);
+    if (on && !kb::g_counters) {
+        const size_t bytes = sizeof(unsigned long long) * 2 * kb::PROF_SLOTS;
+        if (cudaMalloc(&kb::g_counters, bytes) != cudaSuccess) {
+            kb::g_counters = nullptr;
+        } else {
+            cudaMemset(kb::g_counters, 0, bytes);
+        }
+        kb::g_next_slot = 0;
+    }
     kb::g_prof = on != 0;
     return KB_OK;
 }
@@ -313,6 +339,14 @@ extern "C" int kb_profile_read(kb_kernel_stats *out, int32_t cap, int32_t *count
         acc[c].alg_bytes = 0;
         acc[c].alg_flops = 0;
     }
+    std::vector<unsigned long long> cnt;
+    if (kb::g_counters && kb::g_next_slot > 0) {
+        cudaDeviceSynchronize();
+        cnt.resize(2 * size_t(kb::g_next_slot));
+        cudaMemcpy(cnt.data(), kb::g_counters, sizeof(unsigned long long) * cnt.size(),
+                   cudaMemcpyDeviceToHost);
+        cudaMemset(kb::g_counters, 0, sizeof(unsigned long long) * cnt.size());
+    }
     for (auto &r : kb::g_recs) {
         cudaEventSynchronize(r.b);
         float ms = 0.f;
@@ -320,12 +354,19 @@ extern "C" int kb_profile_read(kb_kernel_stats *out, int32_t cap, int32_t *count
         auto &a = acc[r.cls];
         a.launches += 1;
         a.total_ms += ms;
-        a.alg_bytes += r.bytes;
-        a.alg_flops += r.flops;
+        if (r.slot >= 0 && size_t(2 * r.slot + 1) < cnt.size()) {
+            const double rows = double(cnt[2 * r.slot]), nnz = double(cnt[2 * r.slot + 1]);
+            a.alg_bytes += r.fixed + rows * r.per_row + nnz * r.per_nnz;
+            a.alg_flops += rows * r.flops_per_row;
+        } else {
+            a.alg_bytes += r.bytes;
+            a.alg_flops += r.flops;
+        }
         kb::g_pool.push_back(r.a);
         kb::g_pool.push_back(r.b);
     }
     kb::g_recs.clear();
+    kb::g_next_slot = 0;
     int k = 0;
     for (int c = 0; c < KernelClass::COUNT && k < cap; ++c) out[k++] = acc[c];
     if (count) *count = k;

@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <cstddef>
 #include <string>
@@ -71,11 +72,43 @@ struct Ctrl {
 struct KernelClass {
     enum : int { SPMM = 0, ROWBLOCK, REDUCE, SMALL, PROJECTED, ASSEMBLE, OTHER, COUNT };
 };
-void prof_begin(int cls, cudaStream_t s);
+// Work counters a profiled launch fills on the device: rows it processed and, for the
+// SpMM, stored nonzeros of those rows (one atomicAdd per CTA).  nullptr when not profiling.
+struct ProfCount {
+    unsigned long long *rows = nullptr;
+    unsigned long long *nnz = nullptr;
+};
+// prof_begin returns the counters of this launch (nullptr fields when not profiling).
+ProfCount prof_begin(int cls, cudaStream_t s);
 // Records the end event (when profiling) and always adds nlaunch to the launch counter.
-void prof_end(int cls, cudaStream_t s, double alg_bytes, double alg_flops, int nlaunch = 1);
+// With work counters, the launch's algorithmic bytes are fixed + rows * per_row +
+// nnz * per_nnz and its flops rows * flops_per_row, rows/nnz read from the device counters
+// when the profile is read; otherwise the full-size alg_bytes / alg_flops are used.
+void prof_end(int cls, cudaStream_t s, double alg_bytes, double alg_flops, int nlaunch = 1,
+              double per_row = 0.0, double per_nnz = 0.0, double flops_per_row = 0.0,
+              double fixed = 0.0);
 void count_launches(int k);
 bool prof_on();
+
+// ------------------------------------------------------------------ frontier restriction
+// Krylov blocks started from E_W are exactly zero outside the (k-1)-hop ball of W at step
+// k.  gen[i] (uint8) is the hop distance of row i from W (255 = not reached yet); tgen[t]
+// is the minimum over the 32-row activity tile t.  Kernels given tgen skip tiles whose
+// minimum exceeds their limit.
+constexpr int ACT_ROWS = 32;
+constexpr int FRONTIER_MAX_HOPS = 250;
+__device__ __forceinline__ int tile_min_gen(const int32_t *tgen, int64_t r0, int rows) {
+    int m = 0x7fffffff;
+    for (int64_t t = r0 / ACT_ROWS; t <= (r0 + rows - 1) / ACT_ROWS; ++t) m = min(m, __ldg(tgen + t));
+    return m;
+}
+
+// ------------------------------------------------------------------ storage / compute types
+// Blocks are stored as T and computed in Cmp<T>::type: FP32 blocks in FP32, FP64 blocks in
+// FP64, BF16 blocks in FP32 (the BF16 basis mode: half the bytes per block row, FP32
+// accumulation).  Small matrices and Gram partials are always of the compute type.
+template <typename T> struct Cmp { using type = T; };
+template <> struct Cmp<__nv_bfloat16> { using type = float; };
 
 // ------------------------------------------------------------------ launch helpers
 int num_sms();
@@ -96,6 +129,10 @@ struct LinEpi {
     float *yout = nullptr;            // final FP32 output with leading dimension ldo, mo columns
     double *dot_partials = nullptr;   // [grid][W]: sum_i x_i[c] * out_i[c]
     const Ctrl *ctrl = nullptr;
+    const int32_t *tgen = nullptr;    // frontier tiles (nullptr: all rows)
+    int limit = 0;                    // process tiles with tgen <= limit
+    int zero_inactive = 0;            // write zeros for skipped tiles (final output)
+    ProfCount prof;
 };
 
 // ldo <= 0: output is an internal n x W block; otherwise out has leading dimension ldo
@@ -120,14 +157,15 @@ int spmm_max_grid(int W);
 enum RowMode { RB_PROJ = 0, RB_UPD = 1, RB_MULGRAM = 2, RB_MUL = 3, RB_ASM = 4, RB_ASMSUB = 5 };
 template <typename T>
 struct RowArgs {
+    using C = typename Cmp<T>::type;
     int64_t n = 0;
     const T *x = nullptr;
     const T *qa = nullptr;
     const T *qb = nullptr;
-    const T *ca = nullptr;
-    const T *cb = nullptr;
+    const C *ca = nullptr;
+    const C *cb = nullptr;
     T *out = nullptr;
-    T *partials = nullptr;          // [grid][W*W]
+    C *partials = nullptr;          // [grid][W*W]
     const T *basis = nullptr;       // ASM
     int64_t block_stride = 0;
     int nblk = 0;
@@ -135,6 +173,9 @@ struct RowArgs {
     int64_t ldy = 0;
     int mo = 0;
     const Ctrl *ctrl = nullptr;
+    const int32_t *tgen = nullptr;    // frontier tiles (nullptr: all rows)
+    int limit = 0;                    // process tiles with tgen <= limit (ASM: all tiles)
+    ProfCount prof;
 };
 template <typename T>
 int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *grid_out,

@@ -51,11 +51,19 @@ int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const 
                        cudaStream_t s);
 template <typename T>
 int launch_axpy_colnorm(int W, T *X, const T *P, const double *a, int64_t n, double *parts,
-                        int *grid_out, const Ctrl *ctrl, cudaStream_t s);
+                        int *grid_out, const Ctrl *ctrl, const int32_t *tgen, int limit,
+                        int64_t M_alg, cudaStream_t s);
 int axpy_max_grid();
 template <typename T>
 int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const double *omega,
-                         int64_t n, float *Y, int64_t ldy, int mo, int64_t M_alg, cudaStream_t s);
+                         int64_t n, float *Y, int64_t ldy, int mo, int64_t M_alg,
+                         const int32_t *tgen, cudaStream_t s);
+
+// Frontier restriction: hop distances from the node set (uint8, 255 = not reached) and
+// per-32-row tile minima; expand(k) marks the rows at distance k.
+int launch_frontier_init(uint8_t *gen, int32_t *tgen, int64_t n, const int32_t *nodes, int M,
+                         cudaStream_t s);
+int launch_frontier_expand(const GraphDev &g, uint8_t *gen, int32_t *tgen, int k, cudaStream_t s);
 template <typename T>
 int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ctrl, cudaStream_t s);
 

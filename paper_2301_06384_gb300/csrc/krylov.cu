@@ -118,6 +118,7 @@ struct Common {
     cudaStream_t s;
     int spmm = 0;
     Ctrl *hctrl = nullptr;   // host copy of the control block when the caller wants info
+    bool frontier = true;    // restrict the per-step kernels to the reached rows
 };
 #define KB_TRY(x)                \
     do {                         \
@@ -128,37 +129,45 @@ struct Common {
 // ---------------------------------------------------------------- cbl
 template <typename T>
 struct CblBufs {
-    T *basis, *wbuf, *parts, *Cb, *B, *Rinv, *Ut, *Cstk;
+    using C = typename Cmp<T>::type;   // small matrices and Gram partials
+    T *basis, *wbuf;
+    C *parts, *Cb, *B, *Rinv, *Ut, *Cstk;
     double *Gsum, *Hd, *Hs, *R1, *V0, *V1, *V2, *U;
     Ctrl *ctrl;
+    uint8_t *gen;
+    int32_t *tgen;
 };
 
 template <typename T>
 void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_grid) {
     b.basis = ar.take<T>(size_t(m) * n * W);
     b.wbuf = ar.take<T>(size_t(n) * W);
-    b.parts = ar.take<T>(size_t(rb_grid) * W * W);
-    b.Cb = ar.take<T>(size_t(W) * W);
-    b.B = ar.take<T>(size_t(W) * W);
-    b.Rinv = ar.take<T>(size_t(W) * W);
-    b.Ut = ar.take<T>(size_t(m) * W * W);
+    using C = typename Cmp<T>::type;
+    b.parts = ar.take<C>(size_t(rb_grid) * W * W);
+    b.Cb = ar.take<C>(size_t(W) * W);
+    b.B = ar.take<C>(size_t(W) * W);
+    b.Rinv = ar.take<C>(size_t(W) * W);
+    b.Ut = ar.take<C>(size_t(m) * W * W);
     b.Gsum = ar.take<double>(size_t(W) * W);
     b.Hd = ar.take<double>(size_t(m) * M * M);
     b.Hs = ar.take<double>(size_t(m) * M * M);
     b.R1 = ar.take<double>(size_t(M) * M);
-    b.Cstk = ar.take<T>(size_t(m) * W * W);
+    b.Cstk = ar.take<C>(size_t(m) * W * W);
     b.V0 = ar.take<double>(size_t(m) * M * M);
     b.V1 = ar.take<double>(size_t(m) * M * M);
     b.V2 = ar.take<double>(size_t(m) * M * M);
     b.U = ar.take<double>(size_t(m) * M * M);
     b.ctrl = ar.take<Ctrl>(1);
+    b.gen = ar.take<uint8_t>(size_t(n));
+    b.tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
 }
 
 template <typename T>
 int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy) {
+    using C = typename Cmp<T>::type;
     const int64_t n = c.g->dev.n;
     const int W = width_for(M);
-    const bool f64 = sizeof(T) == 8;
+    const bool f64 = sizeof(C) == 8;
     const int rb_grid = rowblock_max_grid<T>(W);
     Arena dry;
     CblBufs<T> b{};
@@ -173,34 +182,50 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
         const double inv_thresh2 = (tau_inv * lam) * (tau_inv * lam) * M;
         const double piv2 = tau_piv * tau_piv;
         KB_TRY(launch_ctrl_init(b.ctrl, m, c.s));
-        KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W, c.s));
+        // with the frontier restriction only reached tiles are written, so every block
+        // starts from zeros; otherwise each block is written in full
+        KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W * (c.frontier ? m : 1), c.s));
         KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
+        const int32_t *tg = c.frontier ? b.tgen : nullptr;
+        if (c.frontier) {
+            KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
+            // the SpMM and the row-block kernels tile rows differently; rows of L Q_k that
+            // the SpMM skips must read as zero in the row-block kernels (the reached set
+            // only grows, so zeroing once suffices)
+            KB_CUDA_TRY(cudaMemsetAsync(b.wbuf, 0, sizeof(T) * size_t(n) * W, c.s));
+        }
         const int64_t bs = n * W;
         for (int k = 1; k <= m; ++k) {
             T *Qk = b.basis + (k - 1) * bs;
             T *Qp = k >= 2 ? b.basis + (k - 2) * bs : nullptr;
+            // Q_k is supported on rows within k-1 hops of W; L Q_k within k hops
+            if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
             // line 3 (first half): W = L Q_k
             LinEpi<T> e;
             e.s1 = 1.0;
             e.out = b.wbuf;
             e.ctrl = b.ctrl;
+            e.tgen = tg;
+            e.limit = k;
             KB_TRY(launch_spmm<T>(c.g->dev, W, Qk, e, c.s, nullptr, M, 0));
             ++c.spmm;
             // line 4: H_kk = Q_k^T L Q_k
             int grid = 0;
             RowArgs<T> pa;
             pa.n = n; pa.x = b.wbuf; pa.qa = Qk; pa.partials = b.parts; pa.ctrl = b.ctrl;
+            pa.tgen = tg; pa.limit = k;
             KB_TRY(launch_rowblock<T>(RB_PROJ, W, pa, c.s, &grid, M));
-            KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
-            KB_TRY(launch_hkk<T>(b.Gsum, M, W, b.Hd + size_t(k - 1) * M * M, b.Cb, b.ctrl, c.s));
+            KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+            KB_TRY(launch_hkk<C>(b.Gsum, M, W, b.Hd + size_t(k - 1) * M * M, b.Cb, b.ctrl, c.s));
             if (k == m) break;   // Q_{m+1} is never used (reading A9)
             // lines 3 and 5: X = L Q_k - Q_{k-1} H_{k-1,k} - Q_k H_kk, then Gram X^T X
             T *X = b.basis + k * bs;
             RowArgs<T> ua;
             ua.n = n; ua.x = b.wbuf; ua.qa = Qp; ua.ca = b.B; ua.qb = Qk; ua.cb = b.Cb;
             ua.out = X; ua.partials = b.parts; ua.ctrl = b.ctrl;
+            ua.tgen = tg; ua.limit = k;
             KB_TRY(launch_rowblock<T>(RB_UPD, W, ua, c.s, &grid, M));
-            KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+            KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
             if (c.p.reorth) {
                 // full reorthogonalisation (not in the paper, reading A10): classical
                 // Gram-Schmidt against all stored blocks, X -= Q_{1:k} (Q_{1:k}^T X), twice;
@@ -210,28 +235,32 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                         RowArgs<T> ra;
                         ra.n = n; ra.x = X; ra.qa = b.basis + j * bs; ra.partials = b.parts;
                         ra.ctrl = b.ctrl;
+                        ra.tgen = tg; ra.limit = k;
                         KB_TRY(launch_rowblock<T>(RB_PROJ, W, ra, c.s, &grid, M));
-                        KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl,
+                        KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl,
                                                 b.Cstk + size_t(j) * W * W));
                     }
                     RowArgs<T> sa;
                     sa.n = n; sa.x = X; sa.basis = b.basis; sa.block_stride = bs; sa.nblk = k;
                     sa.ca = b.Cstk; sa.out = X; sa.partials = b.parts; sa.ctrl = b.ctrl;
+                    sa.tgen = tg; sa.limit = k;
                     KB_TRY(launch_rowblock<T>(RB_ASMSUB, W, sa, c.s, &grid, M));
-                    KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+                    KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
                 }
             }
             // line 6: X = Q_{k+1} H_{k+1,k} by CholeskyQR2
-            KB_TRY(launch_chol<T>(b.Gsum, M, W, 1, k, inv_thresh2, piv2, b.R1, b.Rinv, nullptr,
+            KB_TRY(launch_chol<C>(b.Gsum, M, W, 1, k, inv_thresh2, piv2, b.R1, b.Rinv, nullptr,
                                   nullptr, b.ctrl, c.s));
             RowArgs<T> ma;
             ma.n = n; ma.x = X; ma.ca = b.Rinv; ma.out = X; ma.partials = b.parts; ma.ctrl = b.ctrl;
+            ma.tgen = tg; ma.limit = k;
             KB_TRY(launch_rowblock<T>(RB_MULGRAM, W, ma, c.s, &grid, M));
-            KB_TRY(launch_reduce<T>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
-            KB_TRY(launch_chol<T>(b.Gsum, M, W, 2, k, inv_thresh2, piv2, b.R1, b.Rinv,
+            KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+            KB_TRY(launch_chol<C>(b.Gsum, M, W, 2, k, inv_thresh2, piv2, b.R1, b.Rinv,
                                   b.Hs + size_t(k - 1) * M * M, b.B, b.ctrl, c.s));
             RowArgs<T> qa;
             qa.n = n; qa.x = X; qa.ca = b.Rinv; qa.out = X; qa.ctrl = b.ctrl;
+            qa.tgen = tg; qa.limit = k;
             KB_TRY(launch_rowblock<T>(RB_MUL, W, qa, c.s, &grid, M));
         }
         // line 8: U = phi(H_m) F_1 in FP64
@@ -242,11 +271,11 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, b.U,
                                     b.ctrl, c.s));
         }
-        KB_TRY(launch_u_convert<T>(b.U, M, W, m, b.Ut, b.ctrl, c.s));
+        KB_TRY(launch_u_convert<C>(b.U, M, W, m, b.Ut, b.ctrl, c.s));
         // line 9: Y = [Q_1 .. Q_m] U
         RowArgs<T> aa;
         aa.n = n; aa.basis = b.basis; aa.block_stride = bs; aa.nblk = m; aa.ca = b.Ut;
-        aa.y = Y; aa.ldy = ldy; aa.mo = M; aa.ctrl = b.ctrl;
+        aa.y = Y; aa.ldy = ldy; aa.mo = M; aa.ctrl = b.ctrl; aa.tgen = tg;
         int grid = 0;
         KB_TRY(launch_rowblock<T>(RB_ASM, W, aa, c.s, &grid, M));
         KB_TRY(launch_fill_nan(Y, n, ldy, M, b.ctrl, c.s));
@@ -269,6 +298,8 @@ struct LzBufs {
     int32_t *alive;
     double *c1, *c2, *aupd, *omega;
     Ctrl *ctrl;
+    uint8_t *gen;
+    int32_t *tgen;
 };
 
 template <typename T>
@@ -285,6 +316,8 @@ void plan_lz(Arena &ar, LzBufs<T> &b, int64_t n, int W, int m, int pgrid) {
     b.aupd = ar.take<double>(W);
     b.omega = ar.take<double>(size_t(m) * W);
     b.ctrl = ar.take<Ctrl>(1);
+    b.gen = ar.take<uint8_t>(size_t(n));
+    b.tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
 }
 
 template <typename T>
@@ -311,8 +344,10 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
     auto body = [&]() -> int {
         const double thresh = (f64 ? 1e-12 : 1e-6) * c.g->lambda;
         KB_TRY(launch_ctrl_init(b.ctrl, m, c.s));
-        KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W, c.s));
+        KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W * (c.frontier ? m + 1 : 1), c.s));
         KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
+        const int32_t *tg = c.frontier ? b.tgen : nullptr;
+        if (c.frontier) KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
         KB_CUDA_TRY(cudaMemsetAsync(b.beta, 0, sizeof(double) * size_t(m + 1) * W, c.s));
         KB_CUDA_TRY(cudaMemsetAsync(b.alpha, 0, sizeof(double) * size_t(m + 1) * W, c.s));
         KB_CUDA_TRY(cudaMemsetAsync(b.sigma, 0, sizeof(double) * size_t(m + 1) * W, c.s));
@@ -322,8 +357,11 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
             T *Pk = b.basis + (k - 1) * bs;
             T *Pp = k >= 2 ? b.basis + (k - 2) * bs : nullptr;
             T *X = b.basis + k * bs;
+            if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
             // X = L Q_k - h_{k,k-1} Q_{k-1}, with Q_k = sigma_k P_k; dots <P_k, X> per column
             LinEpi<T> e;
+            e.tgen = tg;
+            e.limit = k;
             e.a1 = b.c1;
             e.a2 = b.c2;
             e.s0 = 0.0;
@@ -338,13 +376,13 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
                                         b.aupd, b.ctrl, c.s));
             if (k == m) break;
             int grid2 = 0;
-            KB_TRY(launch_axpy_colnorm<T>(W, X, Pk, b.aupd, n, b.parts, &grid2, b.ctrl, c.s));
+            KB_TRY(launch_axpy_colnorm<T>(W, X, Pk, b.aupd, n, b.parts, &grid2, b.ctrl, tg, k, M, c.s));
             KB_TRY(launch_lanczos_beta(b.parts, grid2, W, M, gbl ? 1 : 0, k - 1, f64 ? 0 : 1, thresh, b.beta,
                                        b.sigma, b.alive, b.c1, b.c2, b.ctrl, c.s));
         }
         KB_TRY(launch_tridiag_phi(W, M, m, gbl ? 1 : 0, b.alpha, b.beta, b.sigma, int(c.phi),
                                   c.p.eps, c.s_int, c.g->lambda, cc, b.omega, b.work, b.ctrl, c.s));
-        KB_TRY(launch_assemble_diag<T>(W, b.basis, bs, m, b.omega, n, Y, ldy, M, M, c.s));
+        KB_TRY(launch_assemble_diag<T>(W, b.basis, bs, m, b.omega, n, Y, ldy, M, M, tg, c.s));
         return 0;
     };
     int rc = body();
@@ -360,7 +398,8 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
 template <typename T>
 int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int64_t n,
               const int32_t *marker, const int32_t *nodes, int Mc, const T *Zsrc, T *bufs[3],
-              T *out, float *yout, int64_t ldo, int mo, int64_t M_alg) {
+              T *out, float *yout, int64_t ldo, int mo, int64_t M_alg, uint8_t *gen,
+              int32_t *tgen, int hop0) {
     // weights of sum_k'' c_k T_k (reading A3)
     const int h = int(coef.size()) - 1;
     std::vector<double> w(coef);
@@ -380,7 +419,13 @@ int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int
         const bool last = k == 0;
         int dst_i = 0;
         while (dst_i == cur_i || dst_i == prev_i) ++dst_i;
+        // b_k is supported on rows within hop0 + (h - k) hops of W
+        const int hop = hop0 + (h - k);
+        if (tgen) KB_TRY(launch_frontier_expand(c.g->dev, gen, tgen, hop, c.s));
         LinEpi<T> e;
+        e.tgen = tgen;
+        e.limit = hop;
+        e.zero_inactive = last ? 1 : 0;
         e.s1 = (last ? -2.0 : -4.0) / lam;
         e.s0 = last ? 1.0 : 2.0;
         e.s2 = -1.0;
@@ -412,31 +457,43 @@ int run_cheb(Common &c, bool squared, const int32_t *nodes, int M, int m, float 
     const int Mmax = std::min(M, sizeof(T) == 8 ? 64 : 128);
     const int Wmax = width_for(Mmax);
     Arena dry;
-    auto plan = [&](Arena &ar, T **bufs, T **Z, int32_t **marker) {
+    auto plan = [&](Arena &ar, T **bufs, T **Z, int32_t **marker, uint8_t **gen, int32_t **tgen) {
         for (int i = 0; i < 3; ++i) bufs[i] = ar.take<T>(size_t(n) * Wmax);
         *Z = squared ? ar.take<T>(size_t(n) * Wmax) : nullptr;
         *marker = ar.take<int32_t>(size_t(n));
+        *gen = ar.take<uint8_t>(size_t(n));
+        *tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
     };
     T *bufs[3], *Z;
-    int32_t *marker;
-    plan(dry, bufs, &Z, &marker);
+    int32_t *marker, *tgen;
+    uint8_t *gen;
+    plan(dry, bufs, &Z, &marker, &gen, &tgen);
     Arena ar;
     KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
-    plan(ar, bufs, &Z, &marker);
+    plan(ar, bufs, &Z, &marker, &gen, &tgen);
     auto body = [&]() -> int {
         for (int col0 = 0; col0 < M; col0 += Mmax) {
             const int Mc = std::min(Mmax, M - col0);
             const int W = width_for(Mc);
             KB_CUDA_TRY(cudaMemsetAsync(marker, 0xFF, sizeof(int32_t) * size_t(n), c.s));
             KB_TRY(launch_marker(marker, nodes + col0, Mc, c.s));
+            int32_t *tg = nullptr;
+            if (c.frontier) {
+                // Clenshaw blocks are written on reached tiles only: start from zeros
+                for (int i = 0; i < 3; ++i)
+                    KB_CUDA_TRY(cudaMemsetAsync(bufs[i], 0, sizeof(T) * size_t(n) * W, c.s));
+                if (Z) KB_CUDA_TRY(cudaMemsetAsync(Z, 0, sizeof(T) * size_t(n) * W, c.s));
+                KB_TRY(launch_frontier_init(gen, tgen, n, nodes + col0, Mc, c.s));
+                tg = tgen;
+            }
             if (!squared) {
                 KB_TRY(cheb_pass<T>(c, coef, lam, W, n, marker, nodes + col0, Mc, nullptr, bufs,
-                                    nullptr, Y + col0, ldy, Mc, Mc));
+                                    nullptr, Y + col0, ldy, Mc, Mc, gen, tg, 0));
             } else {
                 KB_TRY(cheb_pass<T>(c, coef, lam, W, n, marker, nodes + col0, Mc, nullptr, bufs, Z,
-                                    nullptr, 0, 0, Mc));
+                                    nullptr, 0, 0, Mc, gen, tg, 0));
                 KB_TRY(cheb_pass<T>(c, coef, lam, W, n, marker, nodes + col0, Mc, Z, bufs,
-                                    nullptr, Y + col0, ldy, Mc, Mc));
+                                    nullptr, Y + col0, ldy, Mc, Mc, gen, tg, h));
             }
         }
         return 0;
@@ -465,8 +522,8 @@ int validate(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
     if (M < 1 || M > g->dev.n) return fail(KB_ERR_ARG, "M out of range");
     if (m < 1 || m > 100000) return fail(KB_ERR_ARG, "m out of range");
     if (method == KB_CHEB2 && m < 2) return fail(KB_ERR_ARG, "KB_CHEB2 needs m >= 2");
-    if (params->basis != KB_F32 && params->basis != KB_F64)
-        return fail(KB_ERR_UNSUPPORTED, "basis dtype not implemented");
+    if (params->basis != KB_F32 && params->basis != KB_F64 && params->basis != KB_BF16)
+        return fail(KB_ERR_ARG, "bad basis dtype");
     if (params->reorth && method != KB_CBL)
         return fail(KB_ERR_UNSUPPORTED, "reorthogonalisation is implemented for KB_CBL only");
     const int wmax = params->basis == KB_F64 ? 64 : 128;
@@ -501,8 +558,12 @@ int apply_device(kb_graph *g, kb_method method, kb_phi phi, const kb_params *par
     if (rc) return rc;
     KB_CUDA_TRY(cudaSetDevice(g->device));
     ensure_pool(g->device);
-    Common c{g, phi, *params, s_int, static_cast<cudaStream_t>(stream), 0, nullptr};
+    Common c{g, phi, *params, s_int, static_cast<cudaStream_t>(stream), 0, nullptr, true};
+    // exact restriction of the per-step kernels to rows reached from W (hop distances are
+    // kept in 8 bits)
+    c.frontier = !params->no_frontier && m <= FRONTIER_MAX_HOPS;
     const bool f64 = params->basis == KB_F64;
+    const bool bf16 = params->basis == KB_BF16;
     const int chunk = f64 ? 64 : 128;
     // one host control block per column group (sbl may run several groups)
     std::vector<Ctrl> hc;
@@ -511,25 +572,30 @@ int apply_device(kb_graph *g, kb_method method, kb_phi phi, const kb_params *par
     switch (method) {
         case KB_CBL:
             c.hctrl = info ? &hc[0] : nullptr;
-            rc = f64 ? run_cbl<double>(c, nodes, M, m, Y, M) : run_cbl<float>(c, nodes, M, m, Y, M);
+            rc = f64 ? run_cbl<double>(c, nodes, M, m, Y, M)
+                 : bf16 ? run_cbl<__nv_bfloat16>(c, nodes, M, m, Y, M)
+                        : run_cbl<float>(c, nodes, M, m, Y, M);
             break;
         case KB_GBL:
             c.hctrl = info ? &hc[0] : nullptr;
             rc = f64 ? run_lanczos_scalar<double>(c, true, nodes, M, m, Y, M)
-                     : run_lanczos_scalar<float>(c, true, nodes, M, m, Y, M);
+                 : bf16 ? run_lanczos_scalar<__nv_bfloat16>(c, true, nodes, M, m, Y, M)
+                        : run_lanczos_scalar<float>(c, true, nodes, M, m, Y, M);
             break;
         case KB_SBL:
             for (int col0 = 0, gi = 0; col0 < M && !rc; col0 += chunk, ++gi) {
                 const int Mc = std::min(chunk, M - col0);
                 c.hctrl = info ? &hc[gi] : nullptr;
                 rc = f64 ? run_lanczos_scalar<double>(c, false, nodes + col0, Mc, m, Y + col0, M)
-                         : run_lanczos_scalar<float>(c, false, nodes + col0, Mc, m, Y + col0, M);
+                     : bf16 ? run_lanczos_scalar<__nv_bfloat16>(c, false, nodes + col0, Mc, m, Y + col0, M)
+                            : run_lanczos_scalar<float>(c, false, nodes + col0, Mc, m, Y + col0, M);
             }
             break;
         case KB_CHEB:
         case KB_CHEB2:
             rc = f64 ? run_cheb<double>(c, method == KB_CHEB2, nodes, M, m, Y, M)
-                     : run_cheb<float>(c, method == KB_CHEB2, nodes, M, m, Y, M);
+                 : bf16 ? run_cheb<__nv_bfloat16>(c, method == KB_CHEB2, nodes, M, m, Y, M)
+                        : run_cheb<float>(c, method == KB_CHEB2, nodes, M, m, Y, M);
             break;
     }
     if (rc) return rc;

@@ -11,6 +11,8 @@
 // accumulated in two levels (per tile, then across tiles) to keep the rounding growth of
 // long sums small; each CTA writes its partial Gram, and the partials are summed in FP64
 // by k_reduce in a fixed order (deterministic).
+#include <type_traits>
+
 #include "kb_internal.cuh"
 
 #include <algorithm>
@@ -46,6 +48,28 @@ __device__ __forceinline__ void st4<double>(double *p, const double (&v)[4]) {
     reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
+// Global block access: load 4 stored elements widened to the compute type, store narrowed.
+template <typename T>
+__device__ __forceinline__ void ldg4(const T *p, typename Cmp<T>::type (&v)[4]) { ld4<T>(p, v); }
+template <>
+__device__ __forceinline__ void ldg4<__nv_bfloat16>(const __nv_bfloat16 *p, float (&v)[4]) {
+    const uint2 raw = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <typename T>
+__device__ __forceinline__ void stg4(T *p, const typename Cmp<T>::type (&v)[4]) { st4<T>(p, v); }
+template <>
+__device__ __forceinline__ void stg4<__nv_bfloat16>(__nv_bfloat16 *p, const float (&v)[4]) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 raw;
+    raw.x = *reinterpret_cast<const unsigned int *>(&a);
+    raw.y = *reinterpret_cast<const unsigned int *>(&b);
+    *reinterpret_cast<uint2 *>(p) = raw;
+}
+
 template <typename T, int W>
 struct Geo {
     static constexpr int TR = 4096 / W;     // rows per tile
@@ -53,9 +77,9 @@ struct Geo {
     static constexpr int GR = W / 16;       // Gram sub-block edge per thread
     static constexpr int LDA = TR + 4;      // transposed A chunk row stride
     static constexpr int LDO = W + 4;       // out tile row stride
-    static constexpr size_t smem_a = sizeof(T) * KC * LDA;
-    static constexpr size_t smem_c = sizeof(T) * KC * W;
-    static constexpr size_t smem_o = sizeof(T) * TR * LDO;
+    static constexpr size_t smem_a = sizeof(typename Cmp<T>::type) * KC * LDA;
+    static constexpr size_t smem_c = sizeof(typename Cmp<T>::type) * KC * W;
+    static constexpr size_t smem_o = sizeof(typename Cmp<T>::type) * TR * LDO;
     static constexpr size_t smem = smem_a + smem_c + 2 * smem_o;
 };
 
@@ -68,14 +92,15 @@ k_rowblock(RowArgs<T> a) {
     constexpr bool GRAM = MODE == RB_PROJ || MODE == RB_UPD || MODE == RB_MULGRAM || MODE == RB_ASMSUB;
     constexpr bool SUBX = MODE == RB_UPD || MODE == RB_ASMSUB;     // out = X - product
     constexpr bool MULTI = MODE == RB_ASM || MODE == RB_ASMSUB;    // product over basis blocks
-    constexpr bool TWO = sizeof(T) == 4;
+    using C = typename Cmp<T>::type;   // arithmetic / shared-memory type
+    constexpr bool TWO = sizeof(C) == 4;
     if (MODE != RB_ASM && a.ctrl && a.ctrl->stop) return;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sA = reinterpret_cast<T *>(smem_raw);                      // [KC][LDA]
-    T *sC = reinterpret_cast<T *>(smem_raw + G::smem_a);          // [KC][W]
-    T *sO = reinterpret_cast<T *>(smem_raw + G::smem_a + G::smem_c);            // [TR][LDO]
-    T *sQ = reinterpret_cast<T *>(smem_raw + G::smem_a + G::smem_c + G::smem_o);  // [TR][LDO]
+    C *sA = reinterpret_cast<C *>(smem_raw);                      // [KC][LDA]
+    C *sC = reinterpret_cast<C *>(smem_raw + G::smem_a);          // [KC][W]
+    C *sO = reinterpret_cast<C *>(smem_raw + G::smem_a + G::smem_c);            // [TR][LDO]
+    C *sQ = reinterpret_cast<C *>(smem_raw + G::smem_a + G::smem_c + G::smem_o);  // [TR][LDO]
 
     const int tid = threadIdx.x;
     // product mapping: consecutive threads share an output column group, so a warp covers
@@ -91,34 +116,49 @@ k_rowblock(RowArgs<T> a) {
     if (MODE == RB_ASM) nkb = a.ctrl ? min(a.ctrl->steps, a.nblk) : a.nblk;
     if (MODE == RB_ASMSUB) nkb = a.nblk;
 
-    T g1[GR][GR], g2[GR][GR];
+    C g1[GR][GR], g2[GR][GR];
 #pragma unroll
     for (int i = 0; i < GR; ++i)
 #pragma unroll
         for (int j = 0; j < GR; ++j) { g1[i][j] = 0; g2[i][j] = 0; }
 
     const int64_t ntiles = (a.n + TR - 1) / TR;
+    unsigned long long my_rows = 0, my_units = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t r0 = tile * TR;
+        const int rows_t = (a.n - r0 < TR) ? int(a.n - r0) : TR;
+        // frontier restriction: a tile beyond the limit is zero in every operand; in the
+        // assemblies basis blocks k below the tile's hop distance are zero there
+        int kb0 = 0;
+        if (a.tgen) {
+            const int tmin = tile_min_gen(a.tgen, r0, rows_t);
+            if (MODE == RB_ASM) {
+                kb0 = min(tmin, nkb);
+            } else {
+                if (tmin > a.limit) continue;
+                if (MODE == RB_ASMSUB) kb0 = min(tmin, nkb);
+            }
+        }
+        if (threadIdx.x == 0) { my_rows += rows_t; my_units += (unsigned long long)rows_t * (nkb - kb0); }
         if constexpr (PROD) {
             if (SUBX) {
                 // stage the X tile (coalesced); the first __syncthreads of the K loop orders it
                 for (int idx = tid; idx < TR * CG; idx += RB_THREADS) {
                     const int r = idx / CG;
                     const int c = (idx % CG) * 4;
-                    T xv[4] = {0, 0, 0, 0};
-                    if (r0 + r < a.n) ld4<T>(a.x + (r0 + r) * W + c, xv);
-                    st4<T>(sO + r * G::LDO + c, xv);
+                    C xv[4] = {0, 0, 0, 0};
+                    if (r0 + r < a.n) ldg4<T>(a.x + (r0 + r) * W + c, xv);
+                    st4<C>(sO + r * G::LDO + c, xv);
                 }
             }
-            T acc[4][4];
+            C acc[4][4];
 #pragma unroll
             for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[r][q] = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
+            for (int kb = kb0; kb < nkb; ++kb) {
                 const T *src;
-                const T *cmat;
+                const C *cmat;
                 if (MODE == RB_UPD) {
                     src = (a.qa && kb == 0) ? a.qa : a.qb;
                     cmat = (a.qa && kb == 0) ? a.ca : a.cb;
@@ -134,17 +174,17 @@ k_rowblock(RowArgs<T> a) {
                     for (int idx = tid; idx < TR * (KC / 4); idx += RB_THREADS) {
                         const int r = idx / (KC / 4);
                         const int kq = (idx % (KC / 4)) * 4;
-                        T v[4] = {0, 0, 0, 0};
-                        if (r0 + r < a.n) ld4<T>(src + (r0 + r) * W + k0 + kq, v);
+                        C v[4] = {0, 0, 0, 0};
+                        if (r0 + r < a.n) ldg4<T>(src + (r0 + r) * W + k0 + kq, v);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) sA[(kq + q) * G::LDA + r] = v[q];
                     }
                     for (int idx = tid; idx < KC * CG; idx += RB_THREADS) {
                         const int kr = idx / CG;
                         const int c = (idx % CG) * 4;
-                        T v[4];
-                        ld4<T>(cmat + (k0 + kr) * W + c, v);
-                        st4<T>(sC + kr * W + c, v);
+                        C v[4];
+                        ld4<C>(cmat + (k0 + kr) * W + c, v);
+                        st4<C>(sC + kr * W + c, v);
                     }
                     __syncthreads();
                     // R^{-1} (MUL, MULGRAM) is upper triangular: rows k > c contribute nothing
@@ -156,9 +196,9 @@ k_rowblock(RowArgs<T> a) {
                     if (!skip)
 #pragma unroll
                     for (int k = 0; k < KC; ++k) {
-                        T av[4], cv[4];
-                        ld4<T>(sA + k * G::LDA + row0, av);
-                        ld4<T>(sC + k * W + col4, cv);
+                        C av[4], cv[4];
+                        ld4<C>(sA + k * G::LDA + row0, av);
+                        ld4<C>(sC + k * W + col4, cv);
 #pragma unroll
                         for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -171,17 +211,22 @@ k_rowblock(RowArgs<T> a) {
             // the X tile staged there), then the whole tile is stored with coalesced rows
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                T o[4];
+                C o[4];
                 if (SUBX) {
-                    T xv[4];
-                    ld4<T>(sO + (row0 + r) * G::LDO + col4, xv);
+                    C xv[4];
+                    ld4<C>(sO + (row0 + r) * G::LDO + col4, xv);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) o[q] = xv[q] - acc[r][q];
                 } else {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) o[q] = acc[r][q];
                 }
-                st4<T>(sO + (row0 + r) * G::LDO + col4, o);
+                // narrow stored blocks now, so the Gram below is that of the stored values
+                if constexpr (!std::is_same<T, C>::value && MODE != RB_ASM) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) o[q] = C(T(o[q]));
+                }
+                st4<C>(sO + (row0 + r) * G::LDO + col4, o);
             }
             __syncthreads();
             for (int idx = tid; idx < TR * CG; idx += RB_THREADS) {
@@ -189,14 +234,14 @@ k_rowblock(RowArgs<T> a) {
                 const int c = (idx % CG) * 4;
                 const int64_t row = r0 + r;
                 if (row >= a.n) continue;
-                T o[4];
-                ld4<T>(sO + r * G::LDO + c, o);
+                C o[4];
+                ld4<C>(sO + r * G::LDO + c, o);
                 if (MODE == RB_ASM) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         if (c + q < a.mo) a.y[row * a.ldy + c + q] = float(o[q]);
                 } else {
-                    st4<T>(a.out + row * W + c, o);
+                    stg4<T>(a.out + row * W + c, o);
                 }
             }
         } else {
@@ -204,28 +249,28 @@ k_rowblock(RowArgs<T> a) {
             for (int idx = tid; idx < TR * CG; idx += RB_THREADS) {
                 const int r = idx / CG;
                 const int c = (idx % CG) * 4;
-                T xv[4] = {0, 0, 0, 0}, qv[4] = {0, 0, 0, 0};
+                C xv[4] = {0, 0, 0, 0}, qv[4] = {0, 0, 0, 0};
                 if (r0 + r < a.n) {
-                    ld4<T>(a.x + (r0 + r) * W + c, xv);
-                    ld4<T>(a.qa + (r0 + r) * W + c, qv);
+                    ldg4<T>(a.x + (r0 + r) * W + c, xv);
+                    ldg4<T>(a.qa + (r0 + r) * W + c, qv);
                 }
-                st4<T>(sO + r * G::LDO + c, xv);
-                st4<T>(sQ + r * G::LDO + c, qv);
+                st4<C>(sO + r * G::LDO + c, xv);
+                st4<C>(sQ + r * G::LDO + c, qv);
             }
         }
         if constexpr (GRAM) {
             __syncthreads();
-            const T *left = (MODE == RB_PROJ) ? sQ : sO;
+            const C *left = (MODE == RB_PROJ) ? sQ : sO;
             for (int r = 0; r < TR; ++r) {
-                T av[GR], bv[GR];
+                C av[GR], bv[GR];
                 if constexpr (GR >= 4) {
 #pragma unroll
                     for (int q = 0; q < GR; q += 4) {
-                        T t4[4];
-                        ld4<T>(left + r * G::LDO + gi0 + q, t4);
+                        C t4[4];
+                        ld4<C>(left + r * G::LDO + gi0 + q, t4);
 #pragma unroll
                         for (int u = 0; u < 4; ++u) av[q + u] = t4[u];
-                        ld4<T>(sO + r * G::LDO + gj0 + q, t4);
+                        ld4<C>(sO + r * G::LDO + gj0 + q, t4);
 #pragma unroll
                         for (int u = 0; u < 4; ++u) bv[q + u] = t4[u];
                     }
@@ -253,8 +298,12 @@ k_rowblock(RowArgs<T> a) {
             __syncthreads();
         }
     }
+    if (threadIdx.x == 0 && a.prof.rows) {
+        atomicAdd(a.prof.rows, my_rows);
+        atomicAdd(a.prof.nnz, my_units);
+    }
     if constexpr (GRAM) {
-        T *p = a.partials + int64_t(blockIdx.x) * W * W;
+        C *p = a.partials + int64_t(blockIdx.x) * W * W;
 #pragma unroll
         for (int i = 0; i < GR; ++i)
 #pragma unroll
@@ -336,16 +385,17 @@ __global__ void __launch_bounds__(256) k_reduce(const P *__restrict__ parts, int
 template <typename T>
 int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *grid_out,
                     int64_t M_alg) {
-    if (sizeof(T) == 8 && W > 64) return fail(KB_ERR_UNSUPPORTED, "FP64 blocks wider than 64");
+    if (sizeof(typename Cmp<T>::type) == 8 && W > 64) return fail(KB_ERR_UNSUPPORTED, "FP64 blocks wider than 64");
     const int cls = mode == RB_ASM ? KernelClass::ASSEMBLE : KernelClass::ROWBLOCK;
-    prof_begin(cls, s);
+    RowArgs<T> aa = a;
+    aa.prof = prof_begin(cls, s);
     int rc = 0;
     switch (W) {
-        case 16: rc = launch_w<T, 16>(mode, a, s, grid_out); break;
-        case 32: rc = launch_w<T, 32>(mode, a, s, grid_out); break;
-        case 64: rc = launch_w<T, 64>(mode, a, s, grid_out); break;
+        case 16: rc = launch_w<T, 16>(mode, aa, s, grid_out); break;
+        case 32: rc = launch_w<T, 32>(mode, aa, s, grid_out); break;
+        case 64: rc = launch_w<T, 64>(mode, aa, s, grid_out); break;
         case 128:
-            if constexpr (sizeof(T) == 4) { rc = launch_w<T, 128>(mode, a, s, grid_out); break; }
+            if constexpr (sizeof(typename Cmp<T>::type) == 4) { rc = launch_w<T, 128>(mode, aa, s, grid_out); break; }
             [[fallthrough]];
         default: return fail(KB_ERR_ARG, "unsupported block width");
     }
@@ -353,17 +403,26 @@ int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *g
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "k_rowblock launch");
     const double blk = double(a.n) * double(M_alg) * sizeof(T);
-    double bytes = 0, flops = 0;
-    const double mm = double(a.n) * double(M_alg) * double(M_alg) * 2.0;
+    const double row = double(M_alg) * sizeof(T);             // bytes of one block row
+    const double fr = 2.0 * double(M_alg) * double(M_alg);    // flops of one row times M x M
+    double bytes = 0, flops = 0, per_row = 0, per_unit = 0, frow = 0, fixed = 0;
+    const double mm = double(a.n) * fr;
     switch (mode) {
-        case RB_PROJ: bytes = 2 * blk; flops = mm; break;
-        case RB_UPD: bytes = (a.qa ? 4 : 3) * blk; flops = (a.qa ? 3 : 2) * mm; break;
-        case RB_MULGRAM: bytes = 2 * blk; flops = 2 * mm; break;
-        case RB_MUL: bytes = 2 * blk; flops = mm; break;
-        case RB_ASM: bytes = (a.nblk + 1) * blk; flops = a.nblk * mm; break;
-        case RB_ASMSUB: bytes = (a.nblk + 2) * blk; flops = a.nblk * mm + mm; break;
+        case RB_PROJ: bytes = 2 * blk; flops = mm; per_row = 2 * row; frow = fr; break;
+        case RB_UPD:
+            bytes = (a.qa ? 4 : 3) * blk; flops = (a.qa ? 3 : 2) * mm;
+            per_row = (a.qa ? 4 : 3) * row; frow = (a.qa ? 3 : 2) * fr; break;
+        case RB_MULGRAM: bytes = 2 * blk; flops = 2 * mm; per_row = 2 * row; frow = 2 * fr; break;
+        case RB_MUL: bytes = 2 * blk; flops = mm; per_row = 2 * row; frow = fr; break;
+        case RB_ASM:
+            // block rows read (counted per tile and block) + the FP32 output written in full
+            bytes = (a.nblk + 1) * blk; flops = a.nblk * mm;
+            per_unit = row; fixed = double(a.n) * double(M_alg) * 4.0; break;
+        case RB_ASMSUB:
+            bytes = (a.nblk + 2) * blk; flops = a.nblk * mm + mm;
+            per_row = 2 * row; per_unit = row; frow = fr; break;
     }
-    prof_end(cls, s, bytes, flops);
+    prof_end(cls, s, bytes, flops, 1, per_row, per_unit, frow, fixed);
     return 0;
 }
 
@@ -374,7 +433,7 @@ int rowblock_max_grid(int W) {
         case 32: return max_grid_w<T, 32>();
         case 64: return max_grid_w<T, 64>();
         default:
-            if constexpr (sizeof(T) == 4) return max_grid_w<T, 128>();
+            if constexpr (sizeof(typename Cmp<T>::type) == 4) return max_grid_w<T, 128>();
             return 0;
     }
 }
@@ -394,6 +453,8 @@ template int launch_rowblock<float>(int, int, const RowArgs<float> &, cudaStream
 template int launch_rowblock<double>(int, int, const RowArgs<double> &, cudaStream_t, int *, int64_t);
 template int rowblock_max_grid<float>(int);
 template int rowblock_max_grid<double>(int);
+template int launch_rowblock<__nv_bfloat16>(int, int, const RowArgs<__nv_bfloat16> &, cudaStream_t, int *, int64_t);
+template int rowblock_max_grid<__nv_bfloat16>(int);
 template int launch_reduce<float>(const float *, int, int, double *, cudaStream_t, const Ctrl *, float *);
 template int launch_reduce<double>(const double *, int, int, double *, cudaStream_t, const Ctrl *, double *);
 

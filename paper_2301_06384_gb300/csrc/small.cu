@@ -12,6 +12,8 @@
 //                   line 8; Section 3.3 with phi applied, reading A2).
 //  * element-wise   unit blocks E_W, node markers, column norms, scaled copies, the
 //                   diagonal assembly sum_k u_k Q_k, NaN fill on breakdown.
+#include <type_traits>
+
 #include "kb_internal.cuh"
 #include "kb_kernels.cuh"
 
@@ -33,6 +35,24 @@ __device__ __forceinline__ void stv4(float *p, const float (&v)[4]) {
 __device__ __forceinline__ void stv4(double *p, const double (&v)[4]) {
     reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
     reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void ldv4(const __nv_bfloat16 *p, float (&v)[4]) {
+    const uint2 raw = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void stv4(__nv_bfloat16 *p, const float (&v)[4]) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 raw;
+    raw.x = *reinterpret_cast<const unsigned int *>(&a);
+    raw.y = *reinterpret_cast<const unsigned int *>(&b);
+    *reinterpret_cast<uint2 *>(p) = raw;
+}
+template <typename T> __device__ __forceinline__ double to_double(T v) { return double(v); }
+template <> __device__ __forceinline__ double to_double<__nv_bfloat16>(__nv_bfloat16 v) {
+    return double(__bfloat162float(v));
 }
 
 // ---------------------------------------------------------------- control / init
@@ -58,7 +78,7 @@ template <typename T>
 __global__ void k_scale_copy(T *out, const T *in, int64_t count, double scale) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count;
          i += int64_t(gridDim.x) * blockDim.x)
-        out[i] = T(scale * double(in[i]));
+        out[i] = T(scale * to_double(in[i]));
 }
 
 __global__ void k_fill_nan(float *Y, int64_t n, int64_t ldy, int mo, const Ctrl *ctrl) {
@@ -86,115 +106,255 @@ __global__ void k_hkk(const double *G, int M, int W, double *Hd, T *C, const Ctr
 
 // In-place inverse of an upper triangular M x M matrix in shared memory (ld lda), column
 // by column: with the leading j x j block already inverted, column j of the inverse is
-// -(1/a_jj) X_{0:j,0:j} a_{0:j,j}.  Each row's dot product is split over TPR consecutive
-// lanes (TPR = 1, 2, 4 or 8) and combined with shuffles.  t: shared scratch of M doubles.
-__device__ void tri_inv_upper_inplace(double *A, int lda, int M, double *t) {
+// -(1/a_jj) X_{0:j,0:j} a_{0:j,j}.  The diagonal reciprocals do not depend on the other
+// columns and are formed first, all in parallel; the original entries of column j+1 are
+// copied into the second half of t while column j is formed, so each column costs one
+// barrier.  Each row's dot product is split over TPR consecutive lanes (TPR = 1, 2, 4 or 8)
+// and combined with shuffles.  t: shared scratch of 2 M values.
+template <typename S>
+__device__ void tri_inv_upper_inplace(S *A, int lda, int M, S *t) {
     int TPR = 1;
     while (TPR < 8 && TPR * 2 * M <= int(blockDim.x)) TPR *= 2;
     const int sub = threadIdx.x % TPR;
     const int row0 = threadIdx.x / TPR;
     const int rstride = blockDim.x / TPR;
-    for (int j = 0; j < M; ++j) {
-        for (int i = threadIdx.x; i < j; i += blockDim.x) t[i] = A[i * lda + j];
-        __syncthreads();
-        const double ajj = 1.0 / A[j * lda + j];
+    for (int j = threadIdx.x; j < M; j += blockDim.x) A[j * lda + j] = S(1) / A[j * lda + j];
+    if (M > 1 && threadIdx.x == 0) t[M] = A[1];   // column 1, row 0
+    __syncthreads();
+    for (int j = 1; j < M; ++j) {
+        const S *tc = (j & 1) ? t + M : t;   // original column j, rows < j
+        S *tn = (j & 1) ? t : t + M;         // original column j+1, rows <= j
+        if (j + 1 < M)
+            for (int i = threadIdx.x; i <= j; i += blockDim.x) tn[i] = A[i * lda + j + 1];
+        const S ajj = A[j * lda + j];        // already 1 / a_jj
         // rows i < j, all TPR lanes of a row iterate together (uniform loop bound per warp)
         for (int ib = 0; ib < j; ib += rstride) {
             const int i = ib + row0;
-            double acc = 0.0;
+            S acc = S(0);
             if (i < j)
-                for (int k = i + sub; k < j; k += TPR) acc = fma(A[i * lda + k], t[k], acc);
+                for (int k = i + sub; k < j; k += TPR) acc = fma(A[i * lda + k], tc[k], acc);
             for (int off = 1; off < TPR; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
             if (i < j && sub == 0) A[i * lda + j] = -ajj * acc;
         }
         __syncthreads();
-        if (threadIdx.x == 0) A[j * lda + j] = ajj;
-        __syncthreads();
     }
 }
 
-// Cholesky G = R^T R (upper R) of the leading M x M block in shared memory, then R^{-1}.
+// Cholesky G = R^T R of an M x M symmetric matrix in shared memory, upper R overwriting A
+// and the lower part zeroed.  Square-root-free form: step j needs the pivot d_j (the
+// diagonal of the current Schur complement) and one reciprocal; the Schur complement update
+// is A_ab -= u_ja u_jb / d_j with the unscaled pivot row u_j.  The square roots and the row
+// scaling R_j = u_j / sqrt(d_j) are applied at the end, for all rows at once, which keeps
+// the serial FP64 work per column to one division.  Returns false (all threads) on a pivot
+// <= piv_rel2 * max diag.  t: shared scratch of 2 M doubles.
+__device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, double maxdiag,
+                                   double *t, int *bad) {
+    double *srow = t;       // u_j / d_j
+    double *piv = t + M;    // d_j
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < M; ++j) {
+        if (threadIdx.x < 32) {
+            const double d = A[j * lda + j];
+            if (!(d > piv_rel2 * maxdiag)) {
+                if (lane == 0) *bad = 1;
+            } else {
+                const double dinv = 1.0 / d;
+                for (int c = j + 1 + lane; c < M; c += 32) srow[c] = A[j * lda + c] * dinv;
+                if (lane == 0) piv[j] = d;
+            }
+        }
+        __syncthreads();
+        if (*bad) return false;
+        const int L = M - j - 1;
+        const int npairs = L * (L + 1) / 2;
+        for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
+            // idx -> (a, b), b <= a, in the trailing upper triangle (FP32 root estimate,
+            // corrected exactly in integers)
+            int a = int((sqrtf(8.f * float(idx) + 1.f) - 1.f) * 0.5f);
+            while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+            while (a * (a + 1) / 2 > idx) --a;
+            const int b = idx - a * (a + 1) / 2;
+            const int ra = j + 1 + b, rb = j + 1 + a;   // ra <= rb
+            A[ra * lda + rb] -= A[j * lda + ra] * srow[rb];
+        }
+        __syncthreads();
+    }
+    // R_jj = sqrt(d_j), R_jc = u_jc / sqrt(d_j)
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        const double r = sqrt(piv[j]);
+        piv[j] = r;
+        srow[j] = 1.0 / r;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+        const int i = idx / M, j = idx % M;
+        if (j < i) A[i * lda + j] = 0.0;
+        else if (j == i) A[i * lda + j] = piv[i];
+        else A[i * lda + j] *= srow[i];
+    }
+    __syncthreads();
+    return true;
+}
+
+// Reduced QR of the new block by CholeskyQR (Algorithm 1, line 6), pass 1 or 2 of
+// CholeskyQR2.  Outputs: Rinv (W x W, basis precision) applied by the row-block kernels;
+// pass 1 records R1 = the FP64 inverse of the applied inverse; pass 2 records
+// H_{k+1,k} = R2 R1 (rounded to the basis precision) and B = H^T.
+//
+// Pass 1 (G = X^T X, any conditioning): FP64 Cholesky; in the FP32 path the inverse is
+// formed in FP32 from R1 and R1 is then recomputed as the FP64 inverse of that FP32
+// inverse, so that X = X1 R1 holds for the applied matrices.
+// Pass 2 of the FP32 path (G = I + E, ||E|| of the order of the FP32 rounding of pass 1):
+// to first order R2 = I + Phi(E) with Phi = strict upper part plus half the diagonal,
+// R2^{-1} = I - Phi(E) (the orthogonality of Q = X1 (I - Phi(E)) is then I + O(||E||^2));
+// the applied inverse I - F has the inverse I + F + F^2 + O(F^3), so H = R1 + F R1 + F (F R1),
+// the corrections formed in FP32.  When ||E|| is not small (max |E_ij| >= 1e-4), and always
+// in the FP64 mode, pass 2 uses the pass-1 algorithm.
+//
+// FP64 arithmetic is slow on this part: the kernel avoids serial FP64 loops (the statistics
+// of G are reduced in parallel, max |E_ij| through the order-preserving bit patterns of
+// non-negative doubles) and the Cholesky factorisation needs one FP64 division per column.
 template <typename T>
 __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int pass, int step,
                                               double inv_thresh2, double piv_rel2, double *R1,
                                               T *Rinv, double *Hs, T *Bout, Ctrl *ctrl) {
     if (ctrl->stop) return;
-    extern __shared__ double A[];   // [M][M+1], then t[M]
-    __shared__ int bad;
+    // [M][M+1] FP64, then [M][M+1] T, then 2 M + 2 doubles of scratch
+    extern __shared__ __align__(16) double A[];
+    __shared__ int bad, small;
     __shared__ double maxdiag;
+    __shared__ unsigned long long emax_bits;
     const int lda = M + 1;
-    double *t = A + M * lda;
-    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-        const int i = idx / M, j = idx % M;
-        A[i * lda + j] = G[i * W + j];
+    T *Sf = reinterpret_cast<T *>(A + M * lda);
+    double *t = reinterpret_cast<double *>(Sf + M * lda + (sizeof(T) == 4 ? (M * lda) % 2 : 0));
+    const bool try_small = pass == 2 && sizeof(T) == 4;
+    if (threadIdx.x == 0) {
+        emax_bits = 0ull;
+        bad = 0;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double tr = 0.0, mx = 0.0;
-        for (int i = 0; i < M; ++i) { tr += A[i * lda + i]; mx = fmax(mx, A[i * lda + i]); }
-        maxdiag = mx;
-        bad = 0;
-        if (pass == 1 && !(tr > inv_thresh2)) {
-            // X vanished: the block Krylov space is invariant; keep the blocks so far
-            ctrl->stop = 1;
-            ctrl->steps = step;
-            bad = 2;
+    unsigned long long my_e = 0ull;
+    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+        const int i = idx / M, j = idx % M;
+        const double g = G[i * W + j];
+        A[i * lda + j] = g;
+        if (try_small) {
+            double e = g;
+            if (i == j) e -= 1.0;
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(fabs(e)));
+            my_e = b > my_e ? b : my_e;
+        }
+    }
+    if (try_small) {
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_e, off);
+            my_e = o > my_e ? o : my_e;
+        }
+        if ((threadIdx.x & 31) == 0) atomicMax(&emax_bits, my_e);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // trace and largest diagonal entry (non-negative for a Gram matrix: bit order)
+        double tr = 0.0;
+        unsigned long long mx = 0ull;
+        for (int i = threadIdx.x; i < M; i += 32) {
+            const double d = A[i * lda + i];
+            tr += d;
+            const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(fabs(d)));
+            mx = b > mx ? b : mx;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            tr += __shfl_xor_sync(0xffffffffu, tr, off);
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+            mx = o > mx ? o : mx;
+        }
+        if (threadIdx.x == 0) {
+            maxdiag = __longlong_as_double(static_cast<long long>(mx));
+            small = (try_small && __longlong_as_double(static_cast<long long>(emax_bits)) < 1e-4) ? 1 : 0;
+            if (pass == 1 && !(tr > inv_thresh2)) {
+                // X vanished: the block Krylov space is invariant; keep the blocks so far
+                ctrl->stop = 1;
+                ctrl->steps = step;
+                bad = 2;
+            }
         }
     }
     __syncthreads();
     if (bad) return;
-    for (int j = 0; j < M; ++j) {
-        if (threadIdx.x == 0) {
-            const double d = A[j * lda + j];
-            if (!(d > piv_rel2 * maxdiag)) {
-                bad = 1;
-                ctrl->status = KB_ERR_BREAKDOWN;
-                ctrl->stop = 1;
-                ctrl->steps = step;
-                ctrl->breakdown_step = step;
-            } else {
-                const double r = sqrt(d);
-                A[j * lda + j] = r;
-                t[0] = 1.0 / r;
+    if (small) {
+        // ---- pass 2, first order (FP32 path): S = I - Phi(E) applied; F = I - S exactly
+        for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+            const int i = idx / W, j = idx % W;
+            T v = T(0);
+            if (i < M && j < M && j >= i) {
+                const double e = A[i * lda + j] - (i == j ? 1.0 : 0.0);
+                const double phi = (i == j) ? 0.5 * e : e;
+                v = T((i == j ? 1.0 : 0.0) - phi);
             }
+            Rinv[idx] = v;
+            if (i < M && j < M) Sf[i * lda + j] = (j >= i) ? T((i == j ? 1.0 : 0.0) - double(v)) : T(0);
         }
         __syncthreads();
-        if (bad) return;
-        const double rinv = t[0];
-        for (int c = j + 1 + threadIdx.x; c < M; c += blockDim.x) A[j * lda + c] *= rinv;
-        __syncthreads();
-        const int L = M - j - 1;
-        const int npairs = L * (L + 1) / 2;
-        for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
-            // idx -> (a, b), a <= b, in the trailing upper triangle (FP32 root estimate,
-            // corrected exactly in integers)
-            int a = int((sqrtf(8.f * float(idx) + 1.f) - 1.f) * 0.5f);
-            while ((a + 1) * (a + 2) / 2 <= idx) ++a;
-            while (a * (a + 1) / 2 > idx) --a;
-            const int b = idx - a * (a + 1) / 2;   // 0 <= b <= a
-            const int ra = j + 1 + b, rb = j + 1 + a;   // ra <= rb
-            A[ra * lda + rb] -= A[j * lda + ra] * A[j * lda + rb];
+        // A is free now: R1 rounded to T, and C = F R1 (both upper triangular)
+        T *R1t = reinterpret_cast<T *>(A);
+        T *Ct = R1t + M * lda;
+        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+            const int i = idx / M, j = idx % M;
+            R1t[i * lda + j] = (j >= i) ? T(__ldg(R1 + idx)) : T(0);
         }
         __syncthreads();
+        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+            const int i = idx / M, j = idx % M;
+            T corr = T(0);
+            for (int k = i; k <= j; ++k) corr = fma(Sf[i * lda + k], R1t[k * lda + j], corr);
+            Ct[i * lda + j] = corr;
+        }
+        __syncthreads();
+        // H = (I + F + F^2) R1 = R1 + (C + F C), the corrections of relative size ||E||
+        for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+            const int i = idx / W, j = idx % W;
+            double h = 0.0;
+            if (i < M && j < M && j >= i) {
+                T corr2 = T(0);
+                for (int k = i; k <= j; ++k) corr2 = fma(Sf[i * lda + k], Ct[k * lda + j], corr2);
+                h = __ldg(R1 + i * M + j) + double(Ct[i * lda + j] + corr2);
+            }
+            const T ht = T(h);
+            if (i < M && j < M) Hs[i * M + j] = double(ht);
+            Bout[j * W + i] = ht;
+        }
+        return;
+    }
+    // ---- general CholeskyQR pass
+    if (!chol_upper_inplace(A, lda, M, piv_rel2, maxdiag, t, &bad)) {
+        if (threadIdx.x == 0) {
+            ctrl->status = KB_ERR_BREAKDOWN;
+            ctrl->stop = 1;
+            ctrl->steps = step;
+            ctrl->breakdown_step = step;
+        }
+        return;
     }
     for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
         const int i = idx / M, j = idx % M;
-        if (j < i) A[i * lda + j] = 0.0;
+        Sf[i * lda + j] = T(A[i * lda + j]);
     }
     __syncthreads();
-    // R^{-1} (upper triangular), in place
-    tri_inv_upper_inplace(A, lda, M, t);
+    tri_inv_upper_inplace<T>(Sf, lda, M, reinterpret_cast<T *>(t));
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
         const int i = idx / W, j = idx % W;
-        const T v = (i < M && j < M && j >= i) ? T(A[i * lda + j]) : T(0);
-        Rinv[idx] = v;
-        if (i < M && j < M) A[i * lda + j] = double(v);
+        Rinv[idx] = (i < M && j < M && j >= i) ? Sf[i * lda + j] : T(0);
     }
-    __syncthreads();
-    // The row-block kernels apply the inverse rounded to the basis precision.  Record the
-    // factor actually applied, the FP64 inverse of the rounded inverse, so that
-    // X = Q_{k+1} H_{k+1,k} holds for the stored blocks up to the rounding of Q.
-    tri_inv_upper_inplace(A, lda, M, t);
+    if (sizeof(T) == 4) {
+        // R = FP64 inverse of the applied FP32 inverse
+        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+            const int i = idx / M, j = idx % M;
+            A[i * lda + j] = (j >= i) ? double(Sf[i * lda + j]) : 0.0;
+        }
+        __syncthreads();
+        tri_inv_upper_inplace<double>(A, lda, M, t);
+    }
+    // (FP64 basis: the inverse is applied in FP64, R needs no correction)
     if (pass == 1) {
         for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
             const int i = idx / M, j = idx % M;
@@ -334,122 +494,159 @@ __global__ void k_lanczos_beta(const double *parts, int nparts, int W, int M, in
 // u = phi(T) e_1 for each column's tridiagonal T (diag alpha_k, off-diagonal beta_{k+1}),
 // then assembly weights omega_k[c] = scale * u_k * sigma_k[c].
 //   exp:    Chebyshev series of e^{-t lambda} on [0, Lambda] in T_j(I - 2T/Lambda)
-//   spline: s_int solves with the SPD tridiagonal eps I + T (Thomas algorithm)
-__global__ void k_tridiag_phi(int W, int M, int m, int gbl, const double *alpha,
-                              const double *beta, const double *sigma, int phi_kind,
-                              double eps, int s_int, double lam, ChebCoef cc, double *omega,
-                              double *work, const Ctrl *ctrl) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+//   spline: s_int solves with the SPD tridiagonal eps I + T (Thomas algorithm; the
+//           factorisation is formed once and reused by the s_int solves)
+// One CTA per tridiagonal (column c; a single one for the global method), its threads
+// parallel over the rows of the three-term recurrence.  The vectors live in shared memory
+// when 6 m doubles fit (m <= TRI_SMEM_M), else in the global scratch work (4 m per column).
+constexpr int TRI_SMEM_M = 1024;
+constexpr int TRI_THREADS = 128;
+__global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m, int gbl,
+                                                             const double *alpha,
+                                                             const double *beta,
+                                                             const double *sigma, int phi_kind,
+                                                             double eps, int s_int, double lam,
+                                                             ChebCoef cc, double *omega,
+                                                             double *work, const Ctrl *ctrl) {
+    const int c = blockIdx.x;
     const int ncol = gbl ? 1 : M;
-    if (c >= W) return;
-    const int steps = gbl ? ctrl->steps : m;
     if (c >= ncol) {
-        if (!gbl)
-            for (int k = 0; k < m; ++k) omega[int64_t(k) * W + c] = 0.0;
+        for (int k = threadIdx.x; k < m; k += blockDim.x) omega[int64_t(k) * W + c] = 0.0;
         return;
     }
-    // per-thread work vectors in global scratch: 4 vectors of length m
-    double *v0 = work + int64_t(c) * 4 * m;
-    double *v1 = v0 + m, *v2 = v1 + m, *u = v2 + m;
-    auto a_of = [&](int k) { return alpha[int64_t(k) * W + c]; };
-    auto b_of = [&](int k) { return beta[int64_t(k) * W + c]; };   // couples k-1 and k
-    const int s = steps;
-    for (int k = 0; k < s; ++k) { v0[k] = 0.0; v1[k] = 0.0; v2[k] = 0.0; u[k] = 0.0; }
+    const int s = gbl ? ctrl->steps : m;
+    extern __shared__ __align__(16) double tsm[];
+    const bool in_smem = m <= TRI_SMEM_M;
+    double *v0, *v1, *v2, *u;
+    const double *av, *bv;
+    int64_t st;   // stride of av / bv
+    if (in_smem) {
+        v0 = tsm; v1 = v0 + m; v2 = v1 + m; u = v2 + m;
+        double *a_s = u + m, *b_s = a_s + m;
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            a_s[k] = alpha[int64_t(k) * W + c];
+            b_s[k] = beta[int64_t(k) * W + c];
+        }
+        av = a_s; bv = b_s; st = 1;
+    } else {
+        v0 = work + int64_t(c) * 4 * m; v1 = v0 + m; v2 = v1 + m; u = v2 + m;
+        av = alpha + c; bv = beta + c; st = W;
+    }
+    // b_of(k) couples rows k-1 and k
+    auto a_of = [&](int k) { return av[int64_t(k) * st]; };
+    auto b_of = [&](int k) { return bv[int64_t(k) * st]; };
+    for (int k = threadIdx.x; k < m; k += blockDim.x) { v0[k] = 0.0; v1[k] = 0.0; v2[k] = 0.0; u[k] = 0.0; }
+    __syncthreads();
     if (phi_kind == KB_PHI_EXP) {
         // v0 = e_1, v1 = A e_1, v_{j+1} = 2 A v_j - v_{j-1}, A = I - (2/lam) T
         const double g = 2.0 / lam;
-        v0[0] = 1.0;
-        u[0] = cc.d[0];
+        if (threadIdx.x == 0) { v0[0] = 1.0; u[0] = cc.d[0]; }
+        __syncthreads();
         double *pp = v0, *pc = v1, *pn = v2;
-        // pc = A pp
-        for (int k = 0; k < s; ++k) {
+        for (int k = threadIdx.x; k < s; k += blockDim.x) {
             double tv = a_of(k) * pp[k];
             if (k > 0) tv += b_of(k) * pp[k - 1];
             if (k + 1 < s) tv += b_of(k + 1) * pp[k + 1];
             pc[k] = pp[k] - g * tv;
             u[k] += cc.d[1] * pc[k];
         }
+        __syncthreads();
         for (int j = 2; j < cc.n; ++j) {
-            for (int k = 0; k < s; ++k) {
+            for (int k = threadIdx.x; k < s; k += blockDim.x) {
                 double tv = a_of(k) * pc[k];
                 if (k > 0) tv += b_of(k) * pc[k - 1];
                 if (k + 1 < s) tv += b_of(k + 1) * pc[k + 1];
                 pn[k] = 2.0 * (pc[k] - g * tv) - pp[k];
                 u[k] += cc.d[j] * pn[k];
             }
+            __syncthreads();
             double *t = pp; pp = pc; pc = pn; pn = t;
         }
-    } else {
-        // Thomas algorithm for (eps I + T) x = rhs, repeated s_int times from rhs = e_1
+    } else if (threadIdx.x == 0) {
+        // (eps I + T) = L U: v0 = modified super-diagonal, v2 = reciprocal pivots (once);
+        // then s_int forward / backward sweeps from rhs = e_1
+        double den = eps + a_of(0);
+        v2[0] = 1.0 / den;
+        v0[0] = (s > 1) ? b_of(1) * v2[0] : 0.0;
+        for (int k = 1; k < s; ++k) {
+            den = eps + a_of(k) - b_of(k) * v0[k - 1];
+            v2[k] = 1.0 / den;
+            v0[k] = (k + 1 < s) ? b_of(k + 1) * v2[k] : 0.0;
+        }
         u[0] = 1.0;
         for (int rep = 0; rep < s_int; ++rep) {
-            // forward elimination: v0 = modified super-diagonal, v1 = modified rhs
-            double den = eps + a_of(0);
-            v0[0] = (s > 1) ? b_of(1) / den : 0.0;
-            v1[0] = u[0] / den;
-            for (int k = 1; k < s; ++k) {
-                den = eps + a_of(k) - b_of(k) * v0[k - 1];
-                v0[k] = (k + 1 < s) ? b_of(k + 1) / den : 0.0;
-                v1[k] = (u[k] - b_of(k) * v1[k - 1]) / den;
-            }
+            v1[0] = u[0] * v2[0];
+            for (int k = 1; k < s; ++k) v1[k] = (u[k] - b_of(k) * v1[k - 1]) * v2[k];
             u[s - 1] = v1[s - 1];
             for (int k = s - 2; k >= 0; --k) u[k] = v1[k] - v0[k] * u[k + 1];
         }
     }
+    __syncthreads();
     // E_W = P_1 and Q_1 = sigma_1 P_1, so Y = (1/sigma_1) [Q_1..Q_m] phi(T) e_1
     // (sqrt(N) of Algorithm 2, line 8, for the global method)
     const double scale = 1.0 / sigma[c];
-    for (int k = 0; k < m; ++k) {
-        double om = 0.0;
-        if (k < s) om = scale * u[k] * sigma[int64_t(k) * W + c];
-        if (gbl) {
-            for (int cc2 = 0; cc2 < W; ++cc2)
-                omega[int64_t(k) * W + cc2] = cc2 < M ? om : 0.0;
-        } else {
-            omega[int64_t(k) * W + c] = om;
+    if (gbl) {
+        for (int idx = threadIdx.x; idx < m * W; idx += blockDim.x) {
+            const int k = idx / W, c2 = idx % W;
+            omega[idx] = (c2 < M && k < s) ? scale * u[k] * sigma[int64_t(k) * W] : 0.0;
         }
+    } else {
+        for (int k = threadIdx.x; k < m; k += blockDim.x)
+            omega[int64_t(k) * W + c] = k < s ? scale * u[k] * sigma[int64_t(k) * W + c] : 0.0;
     }
 }
 
-// X[:, c] -= a[c] * P[:, c]; partial column sums of X^2 per CTA
+// X[:, c] -= a[c] * P[:, c]; partial column sums of X^2 per CTA.  Rows of tiles beyond
+// the frontier limit are zero in X and P and are skipped.
 template <typename T, int W>
 __global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const double *a, int64_t n,
-                                                       double *parts, const Ctrl *ctrl) {
+                                                       double *parts, const Ctrl *ctrl,
+                                                       const int32_t *tgen, int limit, ProfCount pc) {
     if (ctrl->stop) return;
+    using C = typename Cmp<T>::type;
     constexpr int CG = W / 4;
     constexpr int RPP = 256 / CG;   // rows per pass
     __shared__ double s[RPP][W];
     const int cg = threadIdx.x % CG, rr = threadIdx.x / CG;
     const int c4 = cg * 4;
-    T ah[4], al[4];
+    C ah[4], al[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        ah[q] = T(a[c4 + q]);
-        al[q] = T(a[c4 + q] - double(ah[q]));
+        ah[q] = C(a[c4 + q]);
+        al[q] = C(a[c4 + q] - double(ah[q]));
     }
-    T acc[4] = {0, 0, 0, 0};
+    C acc[4] = {0, 0, 0, 0};
+    unsigned long long my_rows = 0;
     // two rows per iteration, 16-byte vector accesses: four loads in flight per thread
     const int64_t stride = int64_t(gridDim.x) * RPP;
     for (int64_t row = int64_t(blockIdx.x) * RPP + rr; row < n; row += 2 * stride) {
         const int64_t row2 = row + stride;
-        T xv[2][4], pv[2][4];
-        ldv4(X + row * W + c4, xv[0]);
-        ldv4(P + row * W + c4, pv[0]);
-        if (row2 < n) {
+        const bool act0 = !tgen || __ldg(tgen + row / ACT_ROWS) <= limit;
+        const bool act1 = row2 < n && (!tgen || __ldg(tgen + row2 / ACT_ROWS) <= limit);
+        C xv[2][4], pv[2][4];
+        if (act0) {
+            ldv4(X + row * W + c4, xv[0]);
+            ldv4(P + row * W + c4, pv[0]);
+        }
+        if (act1) {
             ldv4(X + row2 * W + c4, xv[1]);
             ldv4(P + row2 * W + c4, pv[1]);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            if (h == 1 && row2 >= n) break;
+            if (!(h ? act1 : act0)) continue;
+            if (cg == 0) ++my_rows;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 xv[h][q] = xv[h][q] - fma(ah[q], pv[h][q], al[q] * pv[h][q]);
+                // the norm is that of the stored (narrowed) value
+                if constexpr (!std::is_same<T, C>::value) xv[h][q] = C(T(xv[h][q]));
                 acc[q] = fma(xv[h][q], xv[h][q], acc[q]);
             }
             stv4(X + (h ? row2 : row) * W + c4, xv[h]);
         }
     }
+    if (pc.rows && cg == 0 && my_rows) atomicAdd(pc.rows, my_rows);
 #pragma unroll
     for (int q = 0; q < 4; ++q) s[rr][c4 + q] = acc[q];
     __syncthreads();
@@ -460,29 +657,63 @@ __global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const do
     }
 }
 
-// Y[i, c] = sum_k omega_k[c] P_k[i, c]  (global / sequential Lanczos assembly)
+// Y[i, c] = sum_k omega_k[c] P_k[i, c]  (global / sequential Lanczos assembly); with a
+// frontier, block k is zero in rows whose tile is more than k hops from W.
 template <typename T, int W>
 __global__ void __launch_bounds__(256) k_assemble_diag(const T *basis, int64_t stride, int nblk,
                                                         const double *omega, int64_t n, float *Y,
-                                                        int64_t ldy, int mo) {
+                                                        int64_t ldy, int mo, const int32_t *tgen,
+                                                        ProfCount pc) {
     constexpr int CG = W / 4;
     constexpr int RPP = 256 / CG;
+    using C = typename Cmp<T>::type;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T *som = reinterpret_cast<T *>(sm_raw);     // [nblk][W]
-    for (int i = threadIdx.x; i < nblk * W; i += blockDim.x) som[i] = T(omega[i]);
+    C *som = reinterpret_cast<C *>(sm_raw);     // [nblk][W]
+    for (int i = threadIdx.x; i < nblk * W; i += blockDim.x) som[i] = C(omega[i]);
     __syncthreads();
     const int cg = threadIdx.x % CG, rr = threadIdx.x / CG;
     const int c4 = cg * 4;
+    unsigned long long my_units = 0;
     for (int64_t row = int64_t(blockIdx.x) * RPP + rr; row < n; row += int64_t(gridDim.x) * RPP) {
-        T acc[4] = {0, 0, 0, 0};
-        for (int k = 0; k < nblk; ++k) {
-            const T *p = basis + int64_t(k) * stride + row * W + c4;
+        C acc[4] = {0, 0, 0, 0};
+        const int k0 = tgen ? min(__ldg(tgen + row / ACT_ROWS), nblk) : 0;
+        if (cg == 0) my_units += nblk - k0;
+        for (int k = k0; k < nblk; ++k) {
+            C pv[4];
+            ldv4(basis + int64_t(k) * stride + row * W + c4, pv);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fma(som[k * W + c4 + q], p[q], acc[q]);
+            for (int q = 0; q < 4; ++q) acc[q] = fma(som[k * W + c4 + q], pv[q], acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if (c4 + q < mo) Y[row * ldy + c4 + q] = acc[q];
+    }
+    if (pc.nnz && cg == 0 && my_units) atomicAdd(pc.nnz, my_units);
+}
+
+// ---------------------------------------------------------------- frontier
+__global__ void k_frontier_seed(uint8_t *gen, int32_t *tgen, NodeChunk ch) {
+    const int j = threadIdx.x + blockIdx.x * blockDim.x;
+    if (j < ch.cnt) {
+        gen[ch.idx[j]] = 0;
+        tgen[ch.idx[j] / ACT_ROWS] = 0;
+    }
+}
+
+// One hop: rows at distance k-1 mark their unreached neighbours with distance k.
+__global__ void __launch_bounds__(256) k_frontier_expand(GraphDev g, uint8_t *gen, int32_t *tgen, int k) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < g.n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        if (__ldg(tgen + i / ACT_ROWS) > k - 1) continue;
+        if (gen[i] != uint8_t(k - 1)) continue;
+        const int beg = __ldg(g.rowptr + i), end = __ldg(g.rowptr + i + 1);
+        for (int p = beg; p < end; ++p) {
+            const int j = __ldg(g.col + p);
+            if (gen[j] == 255) {
+                gen[j] = uint8_t(k);
+                atomicMin(tgen + j / ACT_ROWS, k);
+            }
+        }
     }
 }
 
@@ -543,6 +774,31 @@ int launch_scale_copy(T *out, const T *in, int64_t count, double scale, cudaStre
     return 0;
 }
 
+int launch_frontier_init(uint8_t *gen, int32_t *tgen, int64_t n, const int32_t *nodes, int M,
+                         cudaStream_t s) {
+    KB_CUDA_TRY(cudaMemsetAsync(gen, 0xFF, size_t(n), s));
+    KB_CUDA_TRY(cudaMemsetAsync(tgen, 0x7F, sizeof(int32_t) * size_t((n + ACT_ROWS - 1) / ACT_ROWS), s));
+    for (int j0 = 0; j0 < M; j0 += NodeChunk::CAP) {
+        NodeChunk ch;
+        ch.cnt = std::min(NodeChunk::CAP, M - j0);
+        ch.col0 = j0;
+        for (int j = 0; j < ch.cnt; ++j) ch.idx[j] = nodes[j0 + j];
+        k_frontier_seed<<<1, NodeChunk::CAP, 0, s>>>(gen, tgen, ch);
+        count_launches(1);
+    }
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int launch_frontier_expand(const GraphDev &g, uint8_t *gen, int32_t *tgen, int k, cudaStream_t s) {
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, int64_t(num_sms()) * 8)));
+    prof_begin(KernelClass::OTHER, s);
+    k_frontier_expand<<<grid, 256, 0, s>>>(g, gen, tgen, k);
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::OTHER, s, double(g.n) / ACT_ROWS * 4, 0);
+    return 0;
+}
+
 int launch_fill_nan(float *Y, int64_t n, int64_t ldy, int mo, const Ctrl *ctrl, cudaStream_t s) {
     const int grid = int(std::min<int64_t>((n * mo + 255) / 256, int64_t(num_sms()) * 8));
     k_fill_nan<<<std::max(grid, 1), 256, 0, s>>>(Y, n, ldy, mo, ctrl);
@@ -564,11 +820,16 @@ template <typename T>
 int launch_chol(const double *G, int M, int W, int pass, int step, double inv_thresh2,
                 double piv_rel2, double *R1, T *Rinv, double *Hs, T *Bout, Ctrl *ctrl,
                 cudaStream_t s) {
-    const size_t smem = sizeof(double) * (size_t(M) * (M + 1) + M);
+    auto bytes_for = [](int m) {
+        return sizeof(double) * size_t(m) * (m + 1) + sizeof(T) * (size_t(m) * (m + 1) + 2) +
+               sizeof(double) * size_t(2 * m + 2);
+    };
+    const size_t smem = bytes_for(M);
     static bool attr = false;
     if (!attr) {
+        // FP64 blocks are at most 64 wide
         cudaFuncSetAttribute(k_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(sizeof(double) * (128 * 129 + 128)));
+                             int(bytes_for(sizeof(T) == 8 ? 64 : 128)));
         attr = true;
     }
     prof_begin(KernelClass::SMALL, s);
@@ -613,8 +874,16 @@ int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const 
                        const ChebCoef &cc, double *omega, double *work, const Ctrl *ctrl,
                        cudaStream_t s) {
     prof_begin(KernelClass::PROJECTED, s);
-    k_tridiag_phi<<<(W + 63) / 64, 64, 0, s>>>(W, M, m, gbl, alpha, beta, sigma, phi_kind, eps,
-                                                s_int, lam, cc, omega, work, ctrl);
+    const size_t smem = m <= TRI_SMEM_M ? sizeof(double) * 6 * size_t(m) : 0;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_tridiag_phi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(double) * 6 * TRI_SMEM_M));
+        attr = true;
+    }
+    k_tridiag_phi<<<gbl ? 1 : W, TRI_THREADS, smem, s>>>(W, M, m, gbl, alpha, beta, sigma,
+                                                         phi_kind, eps, s_int, lam, cc, omega,
+                                                         work, ctrl);
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::PROJECTED, s, 0, 0);
     return 0;
@@ -622,20 +891,23 @@ int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const 
 
 template <typename T>
 int launch_axpy_colnorm(int W, T *X, const T *P, const double *a, int64_t n, double *parts,
-                        int *grid_out, const Ctrl *ctrl, cudaStream_t s) {
+                        int *grid_out, const Ctrl *ctrl, const int32_t *tgen, int limit,
+                        int64_t M_alg, cudaStream_t s) {
     const int rpp = 256 / (W / 4);
     const int grid = int(std::min<int64_t>((n + rpp - 1) / rpp, int64_t(num_sms()) * 4));
     *grid_out = std::max(grid, 1);
-    prof_begin(KernelClass::ROWBLOCK, s);
+    const ProfCount pc = prof_begin(KernelClass::ROWBLOCK, s);
     switch (W) {
-        case 16: k_axpy_colnorm<T, 16><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl); break;
-        case 32: k_axpy_colnorm<T, 32><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl); break;
-        case 64: k_axpy_colnorm<T, 64><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl); break;
-        case 128: k_axpy_colnorm<T, 128><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl); break;
+        case 16: k_axpy_colnorm<T, 16><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, pc); break;
+        case 32: k_axpy_colnorm<T, 32><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, pc); break;
+        case 64: k_axpy_colnorm<T, 64><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, pc); break;
+        case 128: k_axpy_colnorm<T, 128><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, pc); break;
         default: return fail(KB_ERR_ARG, "bad width");
     }
     KB_CUDA_TRY(cudaGetLastError());
-    prof_end(KernelClass::ROWBLOCK, s, 3.0 * double(n) * W * sizeof(T), 3.0 * double(n) * W);
+    const double row = double(M_alg) * sizeof(T);
+    prof_end(KernelClass::ROWBLOCK, s, 3.0 * double(n) * row, 3.0 * double(n) * M_alg, 1, 3.0 * row,
+             0.0, 3.0 * M_alg, 0.0);
     return 0;
 }
 
@@ -645,17 +917,19 @@ int axpy_max_grid() { return num_sms() * 4; }
     do {                                                                                      \
         cudaFuncSetAttribute(k_assemble_diag<T, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              int(smem));                                                      \
-        k_assemble_diag<T, WW><<<grid, 256, smem, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo); \
+        k_assemble_diag<T, WW><<<grid, 256, smem, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo,  \
+                                                       tgen, pc);                             \
     } while (0)
 
 template <typename T>
 int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const double *omega,
-                         int64_t n, float *Y, int64_t ldy, int mo, int64_t M_alg, cudaStream_t s) {
+                         int64_t n, float *Y, int64_t ldy, int mo, int64_t M_alg,
+                         const int32_t *tgen, cudaStream_t s) {
     const int rpp = 256 / (W / 4);
     const int grid = std::max(1, int(std::min<int64_t>((n + rpp - 1) / rpp, int64_t(num_sms()) * 8)));
-    const size_t smem = sizeof(T) * size_t(nblk) * W;
+    const size_t smem = sizeof(typename Cmp<T>::type) * size_t(nblk) * W;
     if (smem > 200 * 1024) return fail(KB_ERR_UNSUPPORTED, "too many blocks for the diagonal assembly");
-    prof_begin(KernelClass::ASSEMBLE, s);
+    const ProfCount pc = prof_begin(KernelClass::ASSEMBLE, s);
     switch (W) {
         case 16: KB_ASM_DIAG(16); break;
         case 32: KB_ASM_DIAG(32); break;
@@ -665,7 +939,8 @@ int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const 
     }
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::ASSEMBLE, s, double(nblk) * n * M_alg * sizeof(T) + double(n) * M_alg * 4,
-             2.0 * nblk * double(n) * M_alg);
+             2.0 * nblk * double(n) * M_alg, 1, 0.0, double(M_alg) * sizeof(T), 0.0,
+             double(n) * M_alg * 4);
     return 0;
 }
 
@@ -685,13 +960,27 @@ int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ct
     template int launch_hkk<T>(const double *, int, int, double *, T *, const Ctrl *, cudaStream_t); \
     template int launch_chol<T>(const double *, int, int, int, int, double, double, double *,   \
                                 T *, double *, T *, Ctrl *, cudaStream_t);                      \
-    template int launch_axpy_colnorm<T>(int, T *, const T *, const double *, int64_t, double *, \
-                                        int *, const Ctrl *, cudaStream_t);                     \
+    template int launch_axpy_colnorm<T>(int, T *, const T *, const double *, int64_t, double *,  \
+                                        int *, const Ctrl *, const int32_t *, int, int64_t,     \
+                                        cudaStream_t);                                          \
     template int launch_assemble_diag<T>(int, const T *, int64_t, int, const double *, int64_t, \
-                                         float *, int64_t, int, int64_t, cudaStream_t);         \
+                                         float *, int64_t, int, int64_t, const int32_t *,       \
+                                         cudaStream_t);                                         \
     template int launch_u_convert<T>(const double *, int, int, int, T *, const Ctrl *, cudaStream_t);
 KB_INST(float)
 KB_INST(double)
 #undef KB_INST
+// BF16 blocks: element-wise kernels on the stored type (small matrices stay FP32)
+template int launch_scatter<__nv_bfloat16>(__nv_bfloat16 *, int64_t, const int32_t *, int, int,
+                                           __nv_bfloat16, cudaStream_t);
+template int launch_scale_copy<__nv_bfloat16>(__nv_bfloat16 *, const __nv_bfloat16 *, int64_t,
+                                              double, cudaStream_t);
+template int launch_axpy_colnorm<__nv_bfloat16>(int, __nv_bfloat16 *, const __nv_bfloat16 *,
+                                                const double *, int64_t, double *, int *,
+                                                const Ctrl *, const int32_t *, int, int64_t,
+                                                cudaStream_t);
+template int launch_assemble_diag<__nv_bfloat16>(int, const __nv_bfloat16 *, int64_t, int,
+                                                 const double *, int64_t, float *, int64_t, int,
+                                                 int64_t, const int32_t *, cudaStream_t);
 
 }  // namespace kb

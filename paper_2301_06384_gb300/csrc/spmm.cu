@@ -17,6 +17,8 @@
 // which gives L 1 = 0 exactly for D - A and drops the diagonal load for standard
 // Laplacians.  Epilogue coefficients arrive in FP64; in the FP32 path each is split into
 // a float pair (hi + lo) so that c * (L x) carries only the rounding of the final sum.
+#include <type_traits>
+
 #include "kb_internal.cuh"
 
 namespace kb {
@@ -31,6 +33,24 @@ template <> struct V4<float> {
     }
     __device__ __forceinline__ void store(float *p) const {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct V4<__nv_bfloat16> {
+    // four BF16 values (8 bytes) widened to FP32
+    float v[4];
+    __device__ __forceinline__ static V4 load(const __nv_bfloat16 *p) {
+        const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(p));
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
+        return V4{{a.x, a.y, b.x, b.y}};
+    }
+    __device__ __forceinline__ void store(__nv_bfloat16 *p) const {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 raw;
+        raw.x = *reinterpret_cast<const unsigned int *>(&a);
+        raw.y = *reinterpret_cast<const unsigned int *>(&b);
+        *reinterpret_cast<uint2 *>(p) = raw;
     }
 };
 template <> struct V4<double> {
@@ -65,51 +85,66 @@ struct SpmmGeo {
 // dot products fits 5 (40 warps), the others fewer.
 template <typename T, bool DOT>
 struct SpmmOcc {
-    static constexpr int value = sizeof(T) == 8 ? 3 : (DOT ? 4 : 5);
+    static constexpr int value = sizeof(typename Cmp<T>::type) == 8 ? 3 : (DOT ? 4 : 5);
 };
 
 template <typename T, int W, bool DOT>
 __global__ void __launch_bounds__(SPMM_THREADS, (SpmmOcc<T, DOT>::value))
 k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
     using G = SpmmGeo<W>;
+    using C = typename Cmp<T>::type;   // arithmetic type
     constexpr int LPR = G::LPR, RPW = G::RPW, NG = G::NG, TR = G::TR, RPG = G::RPG;
     if (e.ctrl && e.ctrl->stop) return;
     __shared__ int s_rp[TR + 1];
     __shared__ int s_col[CAP];
     __shared__ float s_w[CAP];
-    __shared__ __align__(16) T s_coef[5][W];       // c1 hi, c1 lo, c0, c2 hi, c2 lo
+    __shared__ __align__(16) C s_coef[5][W];       // c1 hi, c1 lo, c0, c2 hi, c2 lo
     __shared__ double s_dot[WARPS][W];
     for (int c = threadIdx.x; c < W; c += blockDim.x) {
         const double d1 = e.a1 ? e.a1[c] : e.s1;
         const double d2 = e.a2 ? e.a2[c] : e.s2;
-        const T h1 = T(d1), h2 = T(d2);
+        const C h1 = C(d1), h2 = C(d2);
         s_coef[0][c] = h1;
-        s_coef[1][c] = T(d1 - double(h1));
-        s_coef[2][c] = T(e.a0 ? e.a0[c] : e.s0);
+        s_coef[1][c] = C(d1 - double(h1));
+        s_coef[2][c] = C(e.a0 ? e.a0[c] : e.s0);
         s_coef[3][c] = h2;
-        s_coef[4][c] = T(d2 - double(h2));
+        s_coef[4][c] = C(d2 - double(h2));
     }
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int grp = lane / LPR;
     const int cb = (lane % LPR) * (4 * VPL);   // first column of this lane
     const int gid = warp * RPW + grp;
-    T dot[VPL][4];
+    C dot[VPL][4];
 #pragma unroll
     for (int v = 0; v < VPL; ++v)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dot[v][q] = T(0);
+        for (int q = 0; q < 4; ++q) dot[v][q] = C(0);
     const int64_t ntiles = (g.n + TR - 1) / TR;
+    unsigned long long my_rows = 0, my_nnz = 0;
 
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t r0 = tile * TR;
         const int rows = (g.n - r0 < TR) ? int(g.n - r0) : TR;
+        if (e.tgen && tile_min_gen(e.tgen, r0, rows) > e.limit) {
+            // every row of the tile is beyond the frontier: its output is exactly zero
+            if (e.zero_inactive) {
+                if (e.yout) {
+                    for (int i = threadIdx.x; i < rows * mo; i += blockDim.x)
+                        e.yout[(r0 + i / mo) * ldo + (i % mo)] = 0.f;
+                } else {
+                    for (int i = threadIdx.x; i < rows * W; i += blockDim.x) e.out[r0 * W + i] = T(0.f);
+                }
+            }
+            continue;
+        }
         __syncthreads();   // previous tile done with the shared arrays
         for (int i = threadIdx.x; i <= rows; i += blockDim.x) s_rp[i] = __ldg(g.rowptr + r0 + i);
         __syncthreads();
         const int base = s_rp[0];
         const int cnt = s_rp[rows] - base;
         const bool staged = cnt <= CAP;
+        if (threadIdx.x == 0) { my_rows += rows; my_nnz += cnt; }
         if (staged) {
             for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
                 s_col[i] = __ldg(g.col + base + i);
@@ -125,21 +160,21 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
             const int beg = s_rp[lrow] - base;
             const int end = s_rp[lrow + 1] - base;
             V4<T> xi[VPL];
-            T acc[VPL][4];
+            C acc[VPL][4];
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
                 xi[v] = V4<T>::load(x + row * W + cb + 4 * v);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[v][q] = T(0);
+                for (int q = 0; q < 4; ++q) acc[v][q] = C(0);
             }
             for (int p = beg; p < end; p += U) {
                 V4<T> xj[U][VPL];
-                T wv[U];
+                C wv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     if (p + u < end) {
                         const int j = staged ? s_col[p + u] : __ldg(g.col + base + p + u);
-                        wv[u] = g.w ? T(staged ? s_w[p + u] : __ldg(g.w + base + p + u)) : T(1);
+                        wv[u] = g.w ? C(staged ? s_w[p + u] : __ldg(g.w + base + p + u)) : C(1);
 #pragma unroll
                         for (int v = 0; v < VPL; ++v) xj[u][v] = V4<T>::load(x + int64_t(j) * W + cb + 4 * v);
                     }
@@ -153,15 +188,15 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                             for (int q = 0; q < 4; ++q)
                                 acc[v][q] = fma(wv[u], xi[v].v[q] - xj[u][v].v[q], acc[v][q]);
             }
-            const T r = g.rdiag ? T(__ldg(g.rdiag + row)) : T(0);
+            const C r = g.rdiag ? C(__ldg(g.rdiag + row)) : C(0);
             const int mk = e.marker ? __ldg(e.marker + row) : -1;
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
                 const int c = cb + 4 * v;
-                T o[4];
+                C o[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const T a = fma(r, xi[v].v[q], acc[v][q]);
+                    const C a = fma(r, xi[v].v[q], acc[v][q]);
                     o[q] = fma(s_coef[0][c + q], a, fma(s_coef[1][c + q], a, s_coef[2][c + q] * xi[v].v[q]));
                 }
                 if (e.y) {
@@ -173,10 +208,15 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                 if (e.z) {
                     const V4<T> zi = V4<T>::load(e.z + row * W + c);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) o[q] = fma(T(e.s3), zi.v[q], o[q]);
+                    for (int q = 0; q < 4; ++q) o[q] = fma(C(e.s3), zi.v[q], o[q]);
                 }
-                if (mk >= c && mk < c + 4) o[mk - c] += T(e.wE);
+                if (mk >= c && mk < c + 4) o[mk - c] += C(e.wE);
                 if (!e.yout) {
+                    // narrowed blocks: the dot below is that of the stored values
+                    if constexpr (!std::is_same<T, C>::value) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) o[q] = C(T(o[q]));
+                    }
                     V4<T> ov;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) ov.v[q] = o[q];
@@ -192,6 +232,10 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                 }
             }
         }
+    }
+    if (threadIdx.x == 0 && e.prof.rows) {
+        atomicAdd(e.prof.rows, my_rows);
+        atomicAdd(e.prof.nnz, my_nnz);
     }
     if (DOT) {
 #pragma unroll
@@ -247,12 +291,13 @@ template <typename T>
 int launch_spmm(const GraphDev &g, int W, const T *x, const LinEpi<T> &e, cudaStream_t s,
                 int *grid_out, int64_t M_alg, int n_dense_in, int64_t ldo, int mo) {
     if (ldo <= 0) { ldo = W; mo = W; }
-    prof_begin(KernelClass::SPMM, s);
+    LinEpi<T> ee = e;
+    ee.prof = prof_begin(KernelClass::SPMM, s);
     switch (W) {
-        case 16: launch_w<T, 16>(g, x, e, ldo, mo, s, grid_out); break;
-        case 32: launch_w<T, 32>(g, x, e, ldo, mo, s, grid_out); break;
-        case 64: launch_w<T, 64>(g, x, e, ldo, mo, s, grid_out); break;
-        case 128: launch_w<T, 128>(g, x, e, ldo, mo, s, grid_out); break;
+        case 16: launch_w<T, 16>(g, x, ee, ldo, mo, s, grid_out); break;
+        case 32: launch_w<T, 32>(g, x, ee, ldo, mo, s, grid_out); break;
+        case 64: launch_w<T, 64>(g, x, ee, ldo, mo, s, grid_out); break;
+        case 128: launch_w<T, 128>(g, x, ee, ldo, mo, s, grid_out); break;
         default: return fail(KB_ERR_ARG, "unsupported block width");
     }
     cudaError_t err = cudaGetLastError();
@@ -262,8 +307,14 @@ int launch_spmm(const GraphDev &g, int W, const T *x, const LinEpi<T> &e, cudaSt
     double csr = 4.0 * double(g.n + 1) + 4.0 * double(g.nnz) + (g.w ? 4.0 * double(g.nnz) : 0.0) +
                  (g.rdiag ? 4.0 * double(g.n) : 0.0);
     double blk = double(g.n) * double(M_alg) * double(sizeof(T));
-    prof_end(KernelClass::SPMM, s, csr + blk * (2 + n_dense_in),
-             3.0 * double(g.nnz) * double(M_alg));
+    // per processed row: its row pointer (+ diagonal excess), the gathered block counted
+    // once, the other dense inputs and the output; per stored nonzero: index (+ weight)
+    const double per_row = 4.0 + (g.rdiag ? 4.0 : 0.0) +
+                           double(M_alg) * double(sizeof(T)) * (2 + n_dense_in);
+    const double per_nnz = 4.0 + (g.w ? 4.0 : 0.0);
+    const double flops_per_row = 3.0 * double(M_alg) * double(g.nnz) / double(g.n);
+    prof_end(KernelClass::SPMM, s, csr + blk * (2 + n_dense_in), 3.0 * double(g.nnz) * double(M_alg),
+             1, per_row, per_nnz, flops_per_row, 4.0);
     return 0;
 }
 
@@ -282,7 +333,11 @@ template int launch_spmm<float>(const GraphDev &, int, const float *, const LinE
                                 cudaStream_t, int *, int64_t, int, int64_t, int);
 template int launch_spmm<double>(const GraphDev &, int, const double *, const LinEpi<double> &,
                                  cudaStream_t, int *, int64_t, int, int64_t, int);
+template int launch_spmm<__nv_bfloat16>(const GraphDev &, int, const __nv_bfloat16 *,
+                                        const LinEpi<__nv_bfloat16> &, cudaStream_t, int *, int64_t,
+                                        int, int64_t, int);
 template int spmm_max_grid<float>(int);
 template int spmm_max_grid<double>(int);
+template int spmm_max_grid<__nv_bfloat16>(int);
 
 }  // namespace kb
