@@ -55,8 +55,14 @@ def parse():
     ap.add_argument("--ref-sample-cols", type=int, default=4)
     ap.add_argument("--no-frontier", action="store_true",
                     help="touch all n rows at every step (disables the exact frontier restriction)")
-    ap.add_argument("--streams", type=int, default=1,
+    ap.add_argument("--streams", type=int, default=5,
                     help="CUDA streams the independent solves of a step are spread over")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving-latency sample (kb_server_*)")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-max-n", type=int, default=200_000,
+                    help="largest of the 8 serving graphs (the others are log-spaced from 1e4)")
+    ap.add_argument("--serve-streams", type=int, default=4)
     return ap.parse_args()
 
 
@@ -70,6 +76,104 @@ def workload_config(a):
             "l2": "256 MiB flush write between steps; per-solve working set > L2",
             "streams": a.streams,
             "frontier": not a.no_frontier}
+
+
+# ----------------------------------------------------------------------------- serving
+def serving_sample(a, kb, torch):
+    """Latency of kernel-column requests through the serving front end (kb_server_*).
+
+    8 graphs with n_k = 1e4 * (max_n / 1e4)^(k/7), random geometric for even k and
+    Barabasi-Albert (5 edges per node) for odd k.  Requests: method cbl, m = 30, M uniform
+    in 1..128, half e^{-tL} with t ~ U[0.1, 5], half (eps I + L)^{-s} with eps log-uniform
+    in [1e-3, 1e-1] and s in {1, 2}, graph uniform.  First the saturated throughput is
+    measured (all requests submitted at once), then the same requests arrive as a Poisson
+    process at 0.8 of that rate; latency = submit to end of the solve.  One reference
+    request (the middle graph, M = 64, t = 1) is also timed alone on an idle server.
+    """
+    import synth
+    rng = np.random.default_rng(77)
+    K = 8
+    ns = [int(round(1e4 * (a.serve_max_n / 1e4) ** (k / 7))) for k in range(K)]
+    hg = [synth.random_geometric_graph(n, 10, seed=100 + k) if k % 2 == 0
+          else synth.barabasi_albert_graph(n, 5, seed=100 + k) for k, n in enumerate(ns)]
+    Gs = [kb.Graph.from_csr(g) for g in hg]
+    R = a.serve_requests
+    reqs = []
+    for i in range(R):
+        k = int(rng.integers(0, K))
+        M = int(rng.integers(1, 129))
+        if rng.random() < 0.5:
+            p = kb.make_params(t=float(rng.uniform(0.1, 5.0)))
+            phi = "exp"
+        else:
+            p = kb.make_params(eps=float(10 ** rng.uniform(-3, -1)), s=float(rng.integers(1, 3)))
+            phi = "spline"
+        nodes = synth.sample_nodes(ns[k], M, seed=1000 + i)
+        reqs.append((k, phi, p, nodes))
+    window = 64
+    slots = [torch.empty(max(ns) * 128, dtype=torch.float32, device="cuda") for _ in range(window)]
+
+    failed = [0]
+
+    def finish(sv, tk, lat):
+        # a request whose Lanczos process meets a rank-deficient block (a node set spanning
+        # a small connected component) fails with KB_ERR_BREAKDOWN; it is counted, not timed
+        try:
+            lat.append(sv.poll(tk, wait_ms=-1)[1])
+        except kb.KbError:
+            failed[0] += 1
+
+    def run(arrival_times):
+        lat = []
+        with kb.Server(streams=a.serve_streams, queue_capacity=R + 1) as sv:
+            outstanding = []   # (ticket, slot)
+            free = list(range(window))
+            t0 = time.perf_counter()
+            for i, (k, phi, p, nodes) in enumerate(reqs):
+                if arrival_times is not None:
+                    dt = t0 + arrival_times[i] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                while not free:
+                    tk, sl = outstanding.pop(0)
+                    finish(sv, tk, lat)
+                    free.append(sl)
+                sl = free.pop()
+                Y = slots[sl][: ns[k] * nodes.size].view(ns[k], nodes.size)
+                outstanding.append((sv.submit(Gs[k], "cbl", phi, p, nodes, 30, Y), sl))
+            for tk, sl in outstanding:
+                finish(sv, tk, lat)
+            wall = time.perf_counter() - t0
+        return lat, wall
+
+    run(None)                                  # warm-up (pool growth, lazy module loads)
+    failed[0] = 0
+    _, wall = run(None)
+    failed_sat = failed[0]
+    failed[0] = 0
+    sat = R / wall
+    rate = 0.8 * sat
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=R))
+    lat, _ = run(arrivals)
+    kmid = K // 2
+    ref_nodes = synth.sample_nodes(ns[kmid], 64, seed=5)
+    Yref = torch.empty((ns[kmid], 64), dtype=torch.float32, device="cuda")
+    alone = []
+    with kb.Server(streams=a.serve_streams, queue_capacity=4) as sv:
+        for _ in range(5):
+            tk = sv.submit(Gs[kmid], "cbl", "exp", kb.make_params(t=1.0), ref_nodes, 30, Yref)
+            alone.append(sv.poll(tk, wait_ms=-1)[1])
+    for G in Gs:
+        G.destroy()
+    q = np.percentile(np.array(lat), [50, 99])
+    return {"requests": R, "graph_n": ns, "streams": a.serve_streams, "method": "cbl", "m": 30,
+            "mix": "M~U{1..128}; exp t~U[0.1,5] | spline eps~logU[1e-3,1e-1], s in {1,2}",
+            "saturated_rps": round(sat, 2), "rate_rps": round(rate, 2),
+            "p50_ms": round(float(q[0]), 3), "p99_ms": round(float(q[1]), 3),
+            "mean_ms": round(float(np.mean(lat)), 3),
+            "failed_breakdown": failed[0], "failed_breakdown_saturated_run": failed_sat,
+            "reference_alone_ms": round(float(np.median(alone)), 3),
+            "reference": f"n={ns[kmid]} M=64 exp t=1 cbl m=30 on an idle server"}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -209,6 +313,29 @@ def cpu_baseline(a, budget_s=25.0):
                       f"{len(nodes)} of {a.M} nodes, m={a.m}, full graph, {dt:.1f} s"}
 
 
+# ----------------------------------------------------------------------------- replicas
+def replica_node_seed(node_seed: int, rank: int) -> int:
+    """Each rank is an independent replica of the workload with its own node set."""
+    return node_seed + rank
+
+
+def job_time_ms(ms_local: float, world: int, device) -> float:
+    """Time of the whole job: the slowest rank (max over ranks; no data-path collective)."""
+    if world == 1:
+        return ms_local
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(tt.item())
+
+
+def job_value(cols_per_step: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the columns all ranks produced per second of job time."""
+    return world * cols_per_step / (ms / 1e3)
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     a = parse()
@@ -231,7 +358,7 @@ def main():
     ts = [float(x) for x in a.ts.split(",")]
     methods = a.methods.split(",")
     g = synth.random_geometric_graph(a.n, 10, seed=a.graph_seed)
-    nodes = synth.sample_nodes(a.n, a.M, seed=a.node_seed + rank)
+    nodes = synth.sample_nodes(a.n, a.M, seed=replica_node_seed(a.node_seed, rank))
     stream = torch.cuda.current_stream()
     G = kb.Graph.from_csr(g, stream=stream)
     streams = [stream] + [torch.cuda.Stream() for _ in range(max(1, a.streams) - 1)]
@@ -274,14 +401,9 @@ def main():
     clocks = sampler.stop()
     launches = (kb.kb_launch_counter() - l0) // max(a.steps, 1)
     stats = kb.kb_profile_read()
-    ms = e0.elapsed_time(e1) / a.steps
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-        dist.barrier()
+    ms = job_time_ms(e0.elapsed_time(e1) / a.steps, world, "cuda")
     cols_per_step = len(solves) * a.M
-    value = world * cols_per_step / (ms / 1e3)
+    value = job_value(cols_per_step, world, ms)
 
     # roofline of the dominant kernel class and of the SpMM
     peak, peak_kind = measured_peaks()
@@ -303,13 +425,49 @@ def main():
     dom = max(stats.items(), key=lambda kv: kv[1]["total_ms"])[0] if stats else None
     shares = {k: round(v["total_ms"] / a.steps / ms, 4) for k, v in stats.items() if v["launches"]}
 
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    # time of each solve alone (one stream, after the timed region; not part of value), with
+    # the kernel-class profile of that pass: launch durations free of other streams' kernels
+    solve_ms = {}
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(solves) + 1)]
+    flush.zero_()
+    kb.kb_profile_enable(True)
+    evs[0].record(stream)
+    for i, ((mth, t), Y) in enumerate(zip(solves, Ys)):
+        kb.kb_krylov_apply(G, mth, "exp", params[t], nodes, a.M, a.m, Y, stream=stream)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    kb.kb_profile_enable(False)
+    stats1 = kb.kb_profile_read()
+    for i, (mth, t) in enumerate(solves):
+        solve_ms[f"{mth} t={t:g}"] = round(evs[i].elapsed_time(evs[i + 1]), 3)
+    ms1 = evs[0].elapsed_time(evs[-1])
+    spmm1 = stats1.get("spmm")
+    spmm_one_stream = None
+    if spmm1 and spmm1["total_ms"] > 0:
+        gbs1 = spmm1["alg_bytes"] / (spmm1["total_ms"] / 1e3) / 1e9
+        spmm_one_stream = {"bound": "hbm", "achieved": round(gbs1, 1), "peak": peak, "unit": "GB/s",
+                           "frac": round(gbs1 / peak, 4), "kernel": "spmm",
+                           "avg_launch_ms": spmm1["total_ms"] / max(spmm1["launches"], 1),
+                           "share_of_step": round(spmm1["total_ms"] / ms1, 4),
+                           "peak_kind": f"{peak_kind} hbm_gbs (launch duration alone on the GPU)"}
+    shares_one_stream = {k: round(v["total_ms"] / ms1, 4) for k, v in stats1.items() if v["launches"]}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed
+    # region; one host thread per stream, each running its share of the solves
     e2e = None
     if not a.no_e2e:
+        from concurrent.futures import ThreadPoolExecutor
         Yh = [torch.empty((a.n, a.M), dtype=torch.float32).pin_memory() for _ in solves]
+        pool = ThreadPoolExecutor(max_workers=len(streams))
+
+        def run_share(j):
+            for i in range(j, len(solves), len(streams)):
+                mth, t = solves[i]
+                kb.kb_krylov_apply_host(G, mth, "exp", params[t], nodes, a.M, a.m, Yh[i],
+                                        stream=streams[j])
+
         def step_host():
-            for (mth, t), Y in zip(solves, Yh):
-                kb.kb_krylov_apply_host(G, mth, "exp", params[t], nodes, a.M, a.m, Y, stream=stream)
+            list(pool.map(run_share, range(len(streams))))
         step_host()
         torch.cuda.synchronize()
         ksteps = max(1, min(a.steps, 2))
@@ -318,7 +476,8 @@ def main():
             step_host()
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / ksteps
-        e2e = {"value": world * cols_per_step / dt, "unit": "kernel_columns/s",
+        e2e = {"value": job_value(cols_per_step, world, job_time_ms(dt * 1e3, world, "cuda")),
+               "unit": "kernel_columns/s",
                "h2d_bytes_per_step": len(solves) * a.M * 4,
                "d2h_bytes_per_step": len(solves) * a.n * a.M * 4}
 
@@ -342,6 +501,13 @@ def main():
         except kb.KbError as exc:
             fp64 = {"unavailable": str(exc)}
 
+    serving = None
+    if not a.no_serving and world == 1:
+        try:
+            serving = serving_sample(a, kb, torch)
+        except kb.KbError as exc:
+            serving = {"unavailable": str(exc)}
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": round(value, 2), "unit": "kernel_columns/s",
@@ -353,7 +519,9 @@ def main():
             "roofline": roof(dom) if dom else None,
             "spmm_roofline": roof("spmm"),
             "kernel_shares": shares,
-            "e2e": e2e, "fp64_plain": fp64,
+            "e2e": e2e, "fp64_plain": fp64, "solve_ms_one_stream": solve_ms,
+            "spmm_roofline_one_stream": spmm_one_stream, "kernel_shares_one_stream": shares_one_stream,
+            "serving": serving,
         }
         if world == 1 and not a.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(a)

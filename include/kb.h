@@ -44,7 +44,9 @@ enum {
     KB_ERR_CUDA = -4,         /* a CUDA runtime call failed (message in kb_last_error)          */
     KB_ERR_NOMEM = -5,        /* device memory exhausted                                         */
     KB_ERR_BREAKDOWN = -6,    /* a Lanczos block became rank deficient (reading A6)              */
-    KB_ERR_UNSUPPORTED = -7   /* combination not implemented (see kb_krylov_apply)               */
+    KB_ERR_UNSUPPORTED = -7,  /* combination not implemented (see kb_krylov_apply)               */
+    KB_ERR_BUSY = -8,         /* serving queue full (kb_server_submit)                           */
+    KB_PENDING = 1            /* not an error: the request has not finished (kb_server_poll)     */
 };
 
 /* ------------------------------------------------------------------ enums and params */
@@ -94,7 +96,13 @@ typedef struct kb_graph kb_graph;   /* opaque; owned by the library */
  *           w_ij = -L_ij), and the matrix must be symmetric (bitwise L_ij == L_ji).  The
  *           diagonal entry may be absent (taken as 0).  NULL means the unit-weight standard
  *           Laplacian D - A of the pattern (diagonal entries of the pattern are ignored).
- *   flags   0, or KB_GRAPH_SKIP_SYMMETRY_CHECK to skip the O(nnz log deg) symmetry check.
+ *   flags   0, or a sum of KB_GRAPH_SKIP_SYMMETRY_CHECK (skip the O(nnz log deg) symmetry
+ *           check) and KB_GRAPH_NORMALIZED (store the normalized Laplacian
+ *           I - D^{-1/2} A D^{-1/2} of the graph instead: A = the off-diagonal weights w_ij,
+ *           D = diag of the weighted degrees; the given diagonal is ignored; nodes without
+ *           edges get a zero row; Lambda = min(Gershgorin, 2) since the spectrum lies in
+ *           [0, 2].  The paper uses this Laplacian in Section 8 without defining it;
+ *           reading A7).
  *   stream  stream for the upload and the Lambda reduction; the call synchronises it.
  *   out     receives the handle.
  *
@@ -105,6 +113,7 @@ typedef struct kb_graph kb_graph;   /* opaque; owned by the library */
  * call), KB_ERR_NOMEM, KB_ERR_CUDA.  On error *out is set to NULL.
  */
 #define KB_GRAPH_SKIP_SYMMETRY_CHECK 1
+#define KB_GRAPH_NORMALIZED 2
 int kb_graph_create(int64_t n, const int32_t *rowptr, const int32_t *col, const float *val,
                     int32_t flags, void *stream, kb_graph **out);
 
@@ -235,6 +244,66 @@ int kb_profile_read(kb_kernel_stats *out, int32_t cap, int32_t *count);
 const char *kb_kernel_class_name(int32_t cls);
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t kb_launch_counter(void);
+
+/* ------------------------------------------------------------------ RLS predictor
+ * Regularised least-squares kernel predictor from approximated kernel columns (Section 5,
+ * Eq. (computationcoefficientskrylov); Algorithm 3 for KB_CBL, whose collocation matrix
+ * E_W^T Y equals F_1^T phi(H_m) F_1 by the proof of Theorem 3.1):
+ *     Y = p_{phi,m-1}^{(kr)}(L) E_W            (as kb_krylov_apply, into library scratch)
+ *     (E_W^T Y + gamma M I) c = labels         (FP64 LU with partial pivoting on the device)
+ *     y_pred = Y c                             (device, n float32, caller-owned)
+ * labels: host, M doubles (label of node nodes[i]); gamma >= 0 (gamma = 0: interpolation);
+ * c_host: NULL or host, M doubles receiving c.  M <= 128.  The call synchronises `stream`.
+ * Errors: as kb_krylov_apply; KB_ERR_BREAKDOWN when E_W^T Y + gamma M I is numerically
+ * singular (possible for gbl, sbl and cheb at small m, Section 8.3; never for cbl). */
+int kb_rls_predict(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
+                   const int32_t *nodes, int32_t M, int32_t m, const double *labels,
+                   double gamma, float *y_pred, double *c_host, void *stream, kb_info *info);
+
+/* ------------------------------------------------------------------ scratch size */
+/* Bytes of device scratch one kb_krylov_apply call with these arguments takes from the
+ * stream-ordered pool (the result Y excluded).  Host-only; validates the arguments as
+ * kb_krylov_apply does, except the node list. */
+int kb_workspace_bytes(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
+                       int32_t M, int32_t m, uint64_t *bytes);
+
+/* ------------------------------------------------------------------ serving
+ * A request queue over kb_krylov_apply for many independent kernel-column requests (the
+ * serving use of Section 3's methods; the paper has no serving layer).
+ *
+ * kb_server_create starts `streams` host worker threads on `device`, each owning one CUDA
+ * stream.  Requests start in submission order; a worker starts the oldest pending request
+ * once its scratch (kb_workspace_bytes) fits in `memory_budget` next to the requests in
+ * flight (memory_budget <= 0: three quarters of the free device memory at creation), runs
+ * it on its stream and waits for it, so at most `streams` solves run concurrently and
+ * requests may complete out of order.
+ *
+ * kb_server_submit copies the node list and the parameters; the caller keeps `g` alive
+ * and must not touch the device array Y (n x M float32, as for kb_krylov_apply) until the
+ * request has been polled as finished.  It returns a ticket, or KB_ERR_BUSY when
+ * queue_capacity requests are pending or unpolled, or KB_ERR_NOMEM when the request alone
+ * exceeds the memory budget.  Argument errors of the solve itself are reported by poll.
+ *
+ * kb_server_poll waits up to wait_ms milliseconds (0: do not wait, < 0: wait until done).
+ * It returns KB_PENDING while the request runs or waits, otherwise the solve's status; a
+ * finished request is reported once (its ticket is then forgotten).  info (nullable)
+ * receives the solve's kb_info, latency_ms (nullable) the host time from submit to the end
+ * of the solve.  kb_server_destroy runs every submitted request to completion, then stops
+ * the workers and destroys the streams.  All four functions may be called from any host
+ * thread. */
+typedef struct kb_server kb_server;
+typedef struct {
+    int32_t streams;         /* concurrent solves, 1..64                                          */
+    int32_t queue_capacity;  /* maximum requests submitted and not yet polled as finished         */
+    int64_t memory_budget;   /* bytes of scratch the running requests may hold together          */
+} kb_server_config;
+int kb_server_create(int32_t device, const kb_server_config *cfg, kb_server **out);
+int kb_server_submit(kb_server *sv, kb_graph *g, kb_method method, kb_phi phi,
+                     const kb_params *params, const int32_t *nodes, int32_t M, int32_t m,
+                     float *Y, int64_t *ticket);
+int kb_server_poll(kb_server *sv, int64_t ticket, int32_t wait_ms, kb_info *info,
+                   double *latency_ms);
+int kb_server_destroy(kb_server *sv);
 
 #ifdef __cplusplus
 }

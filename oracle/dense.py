@@ -50,6 +50,16 @@ def laplacian_dense(n: int, rowptr, col, val) -> np.ndarray:
     return L
 
 
+def normalized_laplacian_dense(L: np.ndarray) -> np.ndarray:
+    """I - D^{-1/2} A D^{-1/2} from a dense Laplacian (A = minus its off-diagonal part,
+    D = weighted degrees; rows without edges stay zero).  The paper uses this Laplacian in
+    Section 8 without a definition (reading A7); its spectrum lies in [0, 2]."""
+    A = -(L - np.diag(np.diag(L)))
+    d = A.sum(axis=1)
+    s = np.where(d > 0, 1.0 / np.sqrt(np.where(d > 0, d, 1.0)), 0.0)
+    return np.diag((d > 0).astype(np.float64)) - (s[:, None] * A * s[None, :])
+
+
 def unit_block(n: int, nodes) -> np.ndarray:
     """E_W = [e_{w_1}, ..., e_{w_N}] (Section 3)."""
     nodes = np.asarray(nodes, dtype=np.int64)

@@ -201,6 +201,18 @@ extern "C" int kb_graph_create(int64_t n, const int32_t *rowptr, const int32_t *
                 }
             }
         }
+        // normalized Laplacian I - D^{-1/2} A D^{-1/2} (reading A7): weighted degrees first
+        const bool normalized = (flags & KB_GRAPH_NORMALIZED) != 0;
+        std::vector<double> deg(normalized ? n : 0, 0.0);
+        if (normalized) {
+            unit = false;
+            for (int64_t i = 0; i < n; ++i)
+                for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                    if (col[p] == i) continue;
+                    const float v = val ? val[p] : -1.f;
+                    deg[i] += double(-v);
+                }
+        }
         // build the stored form
         std::vector<int32_t> h_rowptr(n + 1);
         std::vector<int32_t> h_col(noff);
@@ -221,13 +233,16 @@ extern "C" int kb_graph_create(int64_t n, const int32_t *rowptr, const int32_t *
                 const float v = val ? val[p] : -1.f;
                 if (v == 0.f) continue;
                 h_col[q] = j;
-                if (!unit) h_w[q] = -v;
-                wsum += double(-v);
+                const double w = normalized ? double(-v) / std::sqrt(deg[i] * deg[j]) : double(-v);
+                if (!unit) h_w[q] = float(w);
+                wsum += normalized ? double(float(w)) : w;
                 ++q;
             }
             h_rowptr[i + 1] = int32_t(q);
-            // val == NULL: standard Laplacian, diagonal = degree (zero excess)
-            const double excess = (val ? (has_diag ? diag : 0.0) : wsum) - wsum;
+            // val == NULL: standard Laplacian, diagonal = degree (zero excess); normalized:
+            // diagonal 1 on every node with an edge
+            double excess = (val ? (has_diag ? diag : 0.0) : wsum) - wsum;
+            if (normalized) excess = (deg[i] > 0.0 ? 1.0 : 0.0) - wsum;
             h_rdiag[i] = float(excess);
             if (h_rdiag[i] != 0.f) zero_excess = false;
         }
@@ -267,6 +282,8 @@ extern "C" int kb_graph_create(int64_t n, const int32_t *rowptr, const int32_t *
             cleanup();
             return rc;
         }
+        // the spectrum of the normalized Laplacian lies in [0, 2] (tighter than Gershgorin)
+        if (normalized) g->lambda = std::min(g->lambda, 2.0);
         *out = g;
         return KB_OK;
     } catch (const std::bad_alloc &) {
@@ -306,6 +323,8 @@ extern "C" const char *kb_status_string(int status) {
         case KB_ERR_NOMEM: return "out of device memory";
         case KB_ERR_BREAKDOWN: return "Lanczos breakdown (rank-deficient block)";
         case KB_ERR_UNSUPPORTED: return "unsupported combination";
+        case KB_ERR_BUSY: return "serving queue full";
+        case KB_PENDING: return "pending";
         default: return "unknown status";
     }
 }

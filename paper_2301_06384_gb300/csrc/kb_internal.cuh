@@ -110,6 +110,35 @@ __device__ __forceinline__ int tile_min_gen(const int32_t *tgen, int64_t r0, int
 template <typename T> struct Cmp { using type = T; };
 template <> struct Cmp<__nv_bfloat16> { using type = float; };
 
+// ------------------------------------------------------------------ double-float sums
+// FP64 arithmetic is slow on this part, so reductions of FP32 data accumulate in an
+// unevaluated pair hi + lo of floats (about 48 significant bits) on the FP32 pipe.
+// two_sum is the error-free transformation of Knuth (s + e == a + b exactly); merging two
+// pairs renormalises with Dekker's fast two-sum.  The pairs are stored as 8-byte DF values
+// where the FP64 path stores doubles.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void df_add(DF &a, float b) {
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    a.hi = s;
+    a.lo += e;
+}
+__device__ __forceinline__ void df_merge(DF &a, const DF &b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    const float lo = a.lo + b.lo + e;
+    a.hi = s + lo;
+    a.lo = lo - (a.hi - s);
+}
+__device__ __forceinline__ double df_value(const DF &a) { return double(a.hi) + double(a.lo); }
+
 // ------------------------------------------------------------------ launch helpers
 int num_sms();
 inline int width_for(int M) { return M <= 16 ? 16 : M <= 32 ? 32 : M <= 64 ? 64 : 128; }
@@ -127,7 +156,8 @@ struct LinEpi {
     double wE = 0.0;
     T *out = nullptr;                 // internal n x W output (used when yout is null)
     float *yout = nullptr;            // final FP32 output with leading dimension ldo, mo columns
-    double *dot_partials = nullptr;   // [grid][W]: sum_i x_i[c] * out_i[c]
+    double *dot_partials = nullptr;   // [grid][W]: sum_i x_i[c] * out_i[c] (DF pairs when
+                                      // the arithmetic is FP32, doubles for FP64)
     const Ctrl *ctrl = nullptr;
     const int32_t *tgen = nullptr;    // frontier tiles (nullptr: all rows)
     int limit = 0;                    // process tiles with tgen <= limit

@@ -39,7 +39,7 @@ int launch_chol(const double *G, int M, int W, int pass, int step, double inv_th
 
 int launch_lanczos_init(int W, int M, int gbl, int round32, double *sigma, int32_t *alive,
                         double *c1, double *c2, cudaStream_t s);
-int launch_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k,
+int launch_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k, int df,
                          const double *sigma, double *alpha, double *a_upd, const Ctrl *ctrl,
                          cudaStream_t s);
 int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, int k, int round32,

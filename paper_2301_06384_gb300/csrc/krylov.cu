@@ -372,7 +372,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
             int grid = 0;
             KB_TRY(launch_spmm<T>(c.g->dev, W, Pk, e, c.s, &grid, M, Pp ? 1 : 0));
             ++c.spmm;
-            KB_TRY(launch_lanczos_alpha(b.parts, grid, W, M, gbl ? 1 : 0, k - 1, b.sigma, b.alpha,
+            KB_TRY(launch_lanczos_alpha(b.parts, grid, W, M, gbl ? 1 : 0, k - 1, f64 ? 0 : 1, b.sigma, b.alpha,
                                         b.aupd, b.ctrl, c.s));
             if (k == m) break;
             int grid2 = 0;
@@ -449,28 +449,31 @@ int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int
 }
 
 template <typename T>
+void plan_cheb(Arena &ar, int64_t n, int Mmax, bool squared, T **bufs, T **Z, int32_t **marker,
+               uint8_t **gen, int32_t **tgen) {
+    const int Wmax = width_for(Mmax);
+    for (int i = 0; i < 3; ++i) bufs[i] = ar.take<T>(size_t(n) * Wmax);
+    *Z = squared ? ar.take<T>(size_t(n) * Wmax) : nullptr;
+    *marker = ar.take<int32_t>(size_t(n));
+    *gen = ar.take<uint8_t>(size_t(n));
+    *tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
+}
+
+template <typename T>
 int run_cheb(Common &c, bool squared, const int32_t *nodes, int M, int m, float *Y, int64_t ldy) {
     const int64_t n = c.g->dev.n;
     const double lam = c.p.lambda_max > 0 ? c.p.lambda_max : c.g->lambda;
     const int h = squared ? m / 2 : m;
     const std::vector<double> coef = lobatto_coeffs(c.phi, c.p, h, lam, squared);
     const int Mmax = std::min(M, sizeof(T) == 8 ? 64 : 128);
-    const int Wmax = width_for(Mmax);
     Arena dry;
-    auto plan = [&](Arena &ar, T **bufs, T **Z, int32_t **marker, uint8_t **gen, int32_t **tgen) {
-        for (int i = 0; i < 3; ++i) bufs[i] = ar.take<T>(size_t(n) * Wmax);
-        *Z = squared ? ar.take<T>(size_t(n) * Wmax) : nullptr;
-        *marker = ar.take<int32_t>(size_t(n));
-        *gen = ar.take<uint8_t>(size_t(n));
-        *tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
-    };
     T *bufs[3], *Z;
     int32_t *marker, *tgen;
     uint8_t *gen;
-    plan(dry, bufs, &Z, &marker, &gen, &tgen);
+    plan_cheb<T>(dry, n, Mmax, squared, bufs, &Z, &marker, &gen, &tgen);
     Arena ar;
     KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
-    plan(ar, bufs, &Z, &marker, &gen, &tgen);
+    plan_cheb<T>(ar, n, Mmax, squared, bufs, &Z, &marker, &gen, &tgen);
     auto body = [&]() -> int {
         for (int col0 = 0; col0 < M; col0 += Mmax) {
             const int Mc = std::min(Mmax, M - col0);
@@ -501,6 +504,39 @@ int run_cheb(Common &c, bool squared, const int32_t *nodes, int M, int m, float 
     const int rc = body();
     cudaFreeAsync(ar.base, c.s);
     return rc;
+}
+
+// Scratch bytes of one solve (the same plans the runs allocate).
+template <typename T>
+size_t workspace_bytes_t(int64_t n, kb_method method, int M, int m) {
+    Arena dry;
+    const int W = width_for(M);
+    switch (method) {
+        case KB_CBL: {
+            CblBufs<T> b{};
+            plan_cbl<T>(dry, b, n, M, W, m, rowblock_max_grid<T>(W));
+            break;
+        }
+        case KB_GBL:
+        case KB_SBL: {
+            // sbl runs column groups one after the other; each group allocates its own scratch
+            const int Mg = method == KB_SBL ? std::min(M, sizeof(T) == 8 ? 64 : 128) : M;
+            const int Wg = width_for(Mg);
+            LzBufs<T> b{};
+            plan_lz<T>(dry, b, n, Wg, m, std::max(spmm_max_grid<T>(Wg), axpy_max_grid()));
+            break;
+        }
+        case KB_CHEB:
+        case KB_CHEB2: {
+            T *bufs[3], *Z;
+            int32_t *marker, *tgen;
+            uint8_t *gen;
+            plan_cheb<T>(dry, n, std::min(M, sizeof(T) == 8 ? 64 : 128), method == KB_CHEB2, bufs, &Z,
+                         &marker, &gen, &tgen);
+            break;
+        }
+    }
+    return dry.off;
 }
 
 }  // namespace
@@ -652,6 +688,31 @@ extern "C" int kb_krylov_apply_host(kb_graph *g, kb_method method, kb_phi phi,
         cudaFreeAsync(dY, s);
         cudaStreamSynchronize(s);
         return rc;
+    } catch (...) {
+        return fail(KB_ERR_CUDA, "unexpected exception");
+    }
+}
+
+extern "C" int kb_workspace_bytes(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
+                                  int32_t M, int32_t m, uint64_t *bytes) {
+    try {
+        if (!bytes) return fail(KB_ERR_ARG, "bytes is NULL");
+        if (!g) return fail(KB_ERR_ARG, "graph is NULL");
+        if (M < 1 || M > g->dev.n) return fail(KB_ERR_ARG, "M out of range");
+        // validate everything but the node list (a dummy non-null list of distinct nodes)
+        std::vector<int32_t> dummy(static_cast<size_t>(M));
+        for (int i = 0; i < M; ++i) dummy[i] = i;
+        int s_int = 0;
+        const float probe = 0.f;
+        int rc = validate(g, method, phi, params, dummy.data(), M, m, &probe, &s_int);
+        if (rc) return rc;
+        const int64_t n = g->dev.n;
+        switch (params->basis) {
+            case KB_F64: *bytes = workspace_bytes_t<double>(n, method, M, m); break;
+            case KB_BF16: *bytes = workspace_bytes_t<__nv_bfloat16>(n, method, M, m); break;
+            default: *bytes = workspace_bytes_t<float>(n, method, M, m); break;
+        }
+        return KB_OK;
     } catch (...) {
         return fail(KB_ERR_CUDA, "unexpected exception");
     }

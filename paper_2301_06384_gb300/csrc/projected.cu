@@ -18,7 +18,7 @@
 namespace kb {
 namespace {
 
-constexpr int TC = 16;   // output columns per CTA
+constexpr int TC = 4;    // output columns per CTA (many small CTAs: the FP64 work spreads over all SMs)
 
 __global__ void k_cheb_bt_seed(double *V0, double *U, int M, double d0) {
     const int i = threadIdx.x + blockIdx.x * blockDim.x;

@@ -359,24 +359,49 @@ int max_grid_w() {
 
 // ---------------------------------------------------------------- deterministic reduction
 template <typename P>
-__global__ void __launch_bounds__(256) k_reduce(const P *__restrict__ parts, int nparts, int len,
-                                                 double *__restrict__ out, const Ctrl *ctrl,
-                                                 P *__restrict__ out_p) {
+__global__ void __launch_bounds__(1024) k_reduce(const P *__restrict__ parts, int nparts, int len,
+                                                  double *__restrict__ out, const Ctrl *ctrl,
+                                                  P *__restrict__ out_p) {
+    // 32 columns per CTA, 32 warps over the partials (two loads in flight per lane), then a
+    // fixed-order combination of the warps' sums by warp 0
     if (ctrl && ctrl->stop) return;
-    __shared__ double s[8][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ double s[32][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int e = blockIdx.x * 32 + lane;
-    double acc = 0.0;
-    if (e < len)
-        for (int p = warp; p < nparts; p += 8) acc += double(parts[int64_t(p) * len + e]);
-    s[warp][lane] = acc;
-    __syncthreads();
-    if (warp == 0 && e < len) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) t += s[w][lane];
-        out[e] = t;
-        if (out_p) out_p[e] = P(t);
+    if constexpr (std::is_same<P, float>::value) {
+        // double-float accumulation on the FP32 pipe
+        DF a0{0.f, 0.f}, a1{0.f, 0.f};
+        if (e < len) {
+            int p = warp;
+            for (; p + nw < nparts; p += 2 * nw) {
+                const float v0 = parts[int64_t(p) * len + e], v1 = parts[int64_t(p + nw) * len + e];
+                df_add(a0, v0);
+                df_add(a1, v1);
+            }
+            if (p < nparts) df_add(a0, parts[int64_t(p) * len + e]);
+        }
+        df_merge(a0, a1);
+        reinterpret_cast<DF *>(&s[warp][0])[lane] = a0;
+        __syncthreads();
+        if (warp == 0 && e < len) {
+            DF t = reinterpret_cast<const DF *>(&s[0][0])[lane];
+            for (int w = 1; w < nw; ++w) df_merge(t, reinterpret_cast<const DF *>(&s[w][0])[lane]);
+            const double v = df_value(t);
+            out[e] = v;
+            if (out_p) out_p[e] = P(v);
+        }
+    } else {
+        double acc = 0.0;
+        if (e < len)
+            for (int p = warp; p < nparts; p += nw) acc += double(parts[int64_t(p) * len + e]);
+        s[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && e < len) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += s[w][lane];
+            out[e] = t;
+            if (out_p) out_p[e] = P(t);
+        }
     }
 }
 
@@ -442,7 +467,7 @@ template <typename P>
 int launch_reduce(const P *parts, int nparts, int len, double *out, cudaStream_t s,
                   const Ctrl *ctrl, P *out_p) {
     prof_begin(KernelClass::REDUCE, s);
-    k_reduce<P><<<(len + 31) / 32, 256, 0, s>>>(parts, nparts, len, out, ctrl, out_p);
+    k_reduce<P><<<(len + 31) / 32, 1024, 0, s>>>(parts, nparts, len, out, ctrl, out_p);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "k_reduce launch");
     prof_end(KernelClass::REDUCE, s, double(nparts) * len * sizeof(P), 0);

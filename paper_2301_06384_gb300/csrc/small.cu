@@ -214,6 +214,7 @@ __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, d
 // FP64 arithmetic is slow on this part: the kernel avoids serial FP64 loops (the statistics
 // of G are reduced in parallel, max |E_ij| through the order-preserving bit patterns of
 // non-negative doubles) and the Cholesky factorisation needs one FP64 division per column.
+constexpr int CHOL_NEWTON_MAX = 64;   // widest block with the corrected-inverse scratch
 template <typename T>
 __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int pass, int step,
                                               double inv_thresh2, double piv_rel2, double *R1,
@@ -335,9 +336,14 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
         }
         return;
     }
+    const bool newton = sizeof(T) == 4 && M <= CHOL_NEWTON_MAX;
+    double *Sd = t + 2 * M + 2;                               // [M][M+1] (newton only)
+    float *Rf = reinterpret_cast<float *>(Sd + M * lda);      // [M][M+1]
+    float *C1 = Rf + M * lda;                                 // [M][M+1]
     for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
         const int i = idx / M, j = idx % M;
         Sf[i * lda + j] = T(A[i * lda + j]);
+        if (newton) Rf[i * lda + j] = float(Sf[i * lda + j]);
     }
     __syncthreads();
     tri_inv_upper_inplace<T>(Sf, lda, M, reinterpret_cast<T *>(t));
@@ -346,13 +352,69 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
         Rinv[idx] = (i < M && j < M && j >= i) ? Sf[i * lda + j] : T(0);
     }
     if (sizeof(T) == 4) {
-        // R = FP64 inverse of the applied FP32 inverse
-        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-            const int i = idx / M, j = idx % M;
-            A[i * lda + j] = (j >= i) ? double(Sf[i * lda + j]) : 0.0;
+        // R := the FP64 inverse of the applied FP32 inverse S.
+        bool exact = !newton;
+        if (newton) {
+            // With S R = I - E (E upper triangular, of the order of the FP32 rounding),
+            // S^{-1} = R (I - E)^{-1} = R + R E + R E^2 + O(E^3): E is formed in FP64 from S
+            // and R (a fully parallel triangular product), the corrections in FP32.  When
+            // max |E_ij| >= 1e-3 the exact FP64 inverse below is used instead.
+            __shared__ unsigned int emax_e;
+            if (threadIdx.x == 0) emax_e = 0u;
+            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+                const int i = idx / M, j = idx % M;
+                Sd[i * lda + j] = (j >= i) ? double(Sf[i * lda + j]) : 0.0;
+            }
+            __syncthreads();
+            unsigned int my = 0u;
+            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+                const int i = idx / M, j = idx % M;
+                float ef = 0.f;
+                if (j >= i) {
+                    double e = (i == j) ? 1.0 : 0.0;
+                    for (int k = i; k <= j; ++k) e = fma(-Sd[i * lda + k], A[k * lda + j], e);
+                    ef = float(e);
+                }
+                Sf[i * lda + j] = T(ef);
+                const unsigned int b = __float_as_uint(fabsf(ef));
+                my = b > my ? b : my;
+            }
+            atomicMax(&emax_e, my);
+            __syncthreads();
+            if (__uint_as_float(emax_e) < 1e-3f) {
+                for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+                    const int i = idx / M, j = idx % M;
+                    float c = 0.f;
+                    if (j >= i)
+                        for (int k = i; k <= j; ++k) c = fmaf(Rf[i * lda + k], float(Sf[k * lda + j]), c);
+                    C1[i * lda + j] = c;
+                }
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+                    const int i = idx / M, j = idx % M;
+                    if (j >= i) {
+                        float c2 = 0.f;
+                        for (int k = i; k <= j; ++k) c2 = fmaf(C1[i * lda + k], float(Sf[k * lda + j]), c2);
+                        A[i * lda + j] += double(C1[i * lda + j] + c2);
+                    }
+                }
+                __syncthreads();
+            } else {
+                exact = true;
+                for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+                    const int i = idx / M, j = idx % M;
+                    A[i * lda + j] = Sd[i * lda + j];
+                }
+                __syncthreads();
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+                const int i = idx / M, j = idx % M;
+                A[i * lda + j] = (j >= i) ? double(Sf[i * lda + j]) : 0.0;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        tri_inv_upper_inplace<double>(A, lda, M, t);
+        if (exact) tri_inv_upper_inplace<double>(A, lda, M, t);
     }
     // (FP64 basis: the inverse is applied in FP64, R needs no correction)
     if (pass == 1) {
@@ -377,22 +439,50 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
 }
 
 // ---------------------------------------------------------------- gbl / sbl scalars
-// Reduce [nparts][W] partials per column (fixed order) into s[W].
-__device__ void reduce_cols(const double *parts, int nparts, int W, double *s) {
-    __shared__ double tmp[8][128];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Reduce [nparts][W] partials per column (fixed order) into s[W].  df: the partials are
+// double-float pairs (FP32 arithmetic), combined on the FP32 pipe; else doubles.
+__device__ void reduce_cols(const double *parts, int nparts, int W, double *s, int df) {
+    // one warp per strided subset of the partials (up to 32 warps), two loads in flight
+    // per lane, then a fixed-order combination of the warps' sums
+    __shared__ double tmp[32][128];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int c0 = 0; c0 < W; c0 += 32) {
         const int c = c0 + lane;
-        double acc = 0.0;
-        if (c < W)
-            for (int p = warp; p < nparts; p += 8) acc += parts[int64_t(p) * W + c];
-        if (c < W) tmp[warp][c] = acc;
+        if (c >= W) continue;
+        if (df) {
+            const DF *pp = reinterpret_cast<const DF *>(parts);
+            DF a0{0.f, 0.f}, a1{0.f, 0.f};
+            int p = warp;
+            for (; p + nw < nparts; p += 2 * nw) {
+                const DF v0 = pp[int64_t(p) * W + c], v1 = pp[int64_t(p + nw) * W + c];
+                df_merge(a0, v0);
+                df_merge(a1, v1);
+            }
+            if (p < nparts) df_merge(a0, pp[int64_t(p) * W + c]);
+            df_merge(a0, a1);
+            reinterpret_cast<DF *>(&tmp[warp][0])[c] = a0;
+        } else {
+            double a0 = 0.0, a1 = 0.0;
+            int p = warp;
+            for (; p + nw < nparts; p += 2 * nw) {
+                a0 += parts[int64_t(p) * W + c];
+                a1 += parts[int64_t(p + nw) * W + c];
+            }
+            if (p < nparts) a0 += parts[int64_t(p) * W + c];
+            tmp[warp][c] = a0 + a1;
+        }
     }
     __syncthreads();
     for (int c = threadIdx.x; c < W; c += blockDim.x) {
-        double t = 0.0;
-        for (int w = 0; w < 8; ++w) t += tmp[w][c];
-        s[c] = t;
+        if (df) {
+            DF t = reinterpret_cast<const DF *>(&tmp[0][0])[c];
+            for (int w = 1; w < nw; ++w) df_merge(t, reinterpret_cast<const DF *>(&tmp[w][0])[c]);
+            s[c] = df_value(t);
+        } else {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += tmp[w][c];
+            s[c] = t;
+        }
     }
     __syncthreads();
 }
@@ -415,19 +505,27 @@ __global__ void k_lanczos_init(int W, int M, int gbl, int round32, double *sigma
     }
 }
 
+// Sum of s[0..M) by warp 0 (fixed order); the result is returned to lane 0.
+__device__ __forceinline__ double warp0_sum(const double *s, int M) {
+    double t = 0.0;
+    for (int c = threadIdx.x; c < M; c += 32) t += s[c];
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    return t;
+}
+
 // alpha_k = <Q_k, X> (gbl: Frobenius, sbl: per column) from SpMM dot partials of P_k . X
 __global__ void k_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k,
-                                const double *sigma, double *alpha, double *a_upd, const Ctrl *ctrl) {
+                                int df, const double *sigma, double *alpha, double *a_upd,
+                                const Ctrl *ctrl) {
     if (ctrl->stop) return;
     __shared__ double s[128];
-    reduce_cols(parts, nparts, W, s);
+    reduce_cols(parts, nparts, W, s, df);
     const double *sg = sigma + int64_t(k) * W;
     if (gbl) {
         __shared__ double tot;
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int c = 0; c < M; ++c) t += s[c];
-            tot = sg[0] * t;
+        if (threadIdx.x < 32) {
+            const double t = warp0_sum(s, M);
+            if (threadIdx.x == 0) tot = sg[0] * t;
         }
         __syncthreads();
         for (int c = threadIdx.x; c < W; c += blockDim.x) {
@@ -452,19 +550,20 @@ __global__ void k_lanczos_beta(const double *parts, int nparts, int W, int M, in
                                int32_t *alive, double *c1, double *c2, Ctrl *ctrl) {
     if (ctrl->stop) return;
     __shared__ double s[128];
-    reduce_cols(parts, nparts, W, s);
+    reduce_cols(parts, nparts, W, s, round32);
     const double *sk = sigma + int64_t(k) * W;
     double *sn = sigma + int64_t(k + 1) * W;
     double *bn = beta + int64_t(k + 1) * W;
     if (gbl) {
         __shared__ double b;
         __shared__ int stop;
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int c = 0; c < M; ++c) t += s[c];
-            b = sqrt(t);
-            stop = !(b > thresh);
-            if (stop) { ctrl->stop = 1; ctrl->steps = k + 1; }
+        if (threadIdx.x < 32) {
+            const double t = warp0_sum(s, M);
+            if (threadIdx.x == 0) {
+                b = sqrt(t);
+                stop = !(b > thresh);
+                if (stop) { ctrl->stop = 1; ctrl->steps = k + 1; }
+            }
         }
         __syncthreads();
         const double sg = round_to(1.0 / b, round32);
@@ -647,13 +746,27 @@ __global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const do
         }
     }
     if (pc.rows && cg == 0 && my_rows) atomicAdd(pc.rows, my_rows);
+    if constexpr (std::is_same<C, float>::value) {
+        // double-float column sums on the FP32 pipe; partials written as DF pairs
+        DF *sd = reinterpret_cast<DF *>(&s[0][0]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) s[rr][c4 + q] = acc[q];
-    __syncthreads();
-    for (int c = threadIdx.x; c < W; c += 256) {
-        double t = 0.0;
-        for (int r = 0; r < RPP; ++r) t += s[r][c];
-        parts[int64_t(blockIdx.x) * W + c] = t;
+        for (int q = 0; q < 4; ++q) sd[rr * W + c4 + q] = DF{acc[q], 0.f};
+        __syncthreads();
+        DF *out = reinterpret_cast<DF *>(parts);
+        for (int c = threadIdx.x; c < W; c += 256) {
+            DF t = sd[c];
+            for (int r = 1; r < RPP; ++r) df_merge(t, sd[r * W + c]);
+            out[int64_t(blockIdx.x) * W + c] = t;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s[rr][c4 + q] = acc[q];
+        __syncthreads();
+        for (int c = threadIdx.x; c < W; c += 256) {
+            double t = 0.0;
+            for (int r = 0; r < RPP; ++r) t += s[r][c];
+            parts[int64_t(blockIdx.x) * W + c] = t;
+        }
     }
 }
 
@@ -821,8 +934,10 @@ int launch_chol(const double *G, int M, int W, int pass, int step, double inv_th
                 double piv_rel2, double *R1, T *Rinv, double *Hs, T *Bout, Ctrl *ctrl,
                 cudaStream_t s) {
     auto bytes_for = [](int m) {
+        const bool newton = sizeof(T) == 4 && m <= CHOL_NEWTON_MAX;
         return sizeof(double) * size_t(m) * (m + 1) + sizeof(T) * (size_t(m) * (m + 1) + 2) +
-               sizeof(double) * size_t(2 * m + 2);
+               sizeof(double) * size_t(2 * m + 2) +
+               (newton ? (sizeof(double) + 2 * sizeof(float)) * size_t(m) * (m + 1) : 0);
     };
     const size_t smem = bytes_for(M);
     static bool attr = false;
@@ -848,11 +963,11 @@ int launch_lanczos_init(int W, int M, int gbl, int round32, double *sigma, int32
     return 0;
 }
 
-int launch_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k,
+int launch_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl, int k, int df,
                          const double *sigma, double *alpha, double *a_upd, const Ctrl *ctrl,
                          cudaStream_t s) {
     prof_begin(KernelClass::SMALL, s);
-    k_lanczos_alpha<<<1, 256, 0, s>>>(parts, nparts, W, M, gbl, k, sigma, alpha, a_upd, ctrl);
+    k_lanczos_alpha<<<1, 1024, 0, s>>>(parts, nparts, W, M, gbl, k, df, sigma, alpha, a_upd, ctrl);
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::SMALL, s, double(nparts) * W * 8, 0);
     return 0;
@@ -862,7 +977,7 @@ int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, 
                         double thresh, double *beta, double *sigma, int32_t *alive, double *c1,
                         double *c2, Ctrl *ctrl, cudaStream_t s) {
     prof_begin(KernelClass::SMALL, s);
-    k_lanczos_beta<<<1, 256, 0, s>>>(parts, nparts, W, M, gbl, k, round32, thresh, beta, sigma,
+    k_lanczos_beta<<<1, 1024, 0, s>>>(parts, nparts, W, M, gbl, k, round32, thresh, beta, sigma,
                                      alive, c1, c2, ctrl);
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::SMALL, s, double(nparts) * W * 8, 0);

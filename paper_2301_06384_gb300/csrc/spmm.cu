@@ -83,6 +83,12 @@ struct SpmmGeo {
 
 // Resident CTAs per SM the register budget is sized for: the FP32 kernel without column
 // dot products fits 5 (40 warps), the others fewer.
+// Prefetch the 128-byte line holding p into L2 (no register result, no fault on the
+// addresses used here: every caller passes an address inside an allocated array).
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <typename T, bool DOT>
 struct SpmmOcc {
     static constexpr int value = sizeof(typename Cmp<T>::type) == 8 ? 3 : (DOT ? 4 : 5);
@@ -99,7 +105,12 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
     __shared__ int s_col[CAP];
     __shared__ float s_w[CAP];
     __shared__ __align__(16) C s_coef[5][W];       // c1 hi, c1 lo, c0, c2 hi, c2 lo
+    __shared__ C s_sc[2];                          // s3, wE in the arithmetic type
     __shared__ double s_dot[WARPS][W];
+    if (threadIdx.x == 0) {
+        s_sc[0] = C(e.s3);
+        s_sc[1] = C(e.wE);
+    }
     for (int c = threadIdx.x; c < W; c += blockDim.x) {
         const double d1 = e.a1 ? e.a1[c] : e.s1;
         const double d2 = e.a2 ? e.a2[c] : e.s2;
@@ -137,6 +148,21 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                 }
             }
             continue;
+        }
+        // ask L2 for the tile's own dense rows now (x_i at the row start, y / z in the
+        // epilogue) and for the next tile's row pointers, so that those loads, issued later,
+        // do not wait on DRAM
+        {
+            const char *xb = reinterpret_cast<const char *>(x + r0 * W);
+            const int64_t tile_bytes = int64_t(rows) * W * int64_t(sizeof(T));
+            for (int64_t off = int64_t(threadIdx.x) * 128; off < tile_bytes; off += int64_t(blockDim.x) * 128) {
+                prefetch_l2(xb + off);
+                if (e.y) prefetch_l2(reinterpret_cast<const char *>(e.y + r0 * W) + off);
+                if (e.z) prefetch_l2(reinterpret_cast<const char *>(e.z + r0 * W) + off);
+            }
+            const int64_t nr0 = r0 + int64_t(gridDim.x) * TR;
+            if (threadIdx.x < (TR + 1 + 31) / 32 && nr0 + threadIdx.x * 32 <= g.n)
+                prefetch_l2(g.rowptr + nr0 + threadIdx.x * 32);
         }
         __syncthreads();   // previous tile done with the shared arrays
         for (int i = threadIdx.x; i <= rows; i += blockDim.x) s_rp[i] = __ldg(g.rowptr + r0 + i);
@@ -208,9 +234,9 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                 if (e.z) {
                     const V4<T> zi = V4<T>::load(e.z + row * W + c);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) o[q] = fma(C(e.s3), zi.v[q], o[q]);
+                    for (int q = 0; q < 4; ++q) o[q] = fma(s_sc[0], zi.v[q], o[q]);
                 }
-                if (mk >= c && mk < c + 4) o[mk - c] += C(e.wE);
+                if (mk >= c && mk < c + 4) o[mk - c] += s_sc[1];
                 if (!e.yout) {
                     // narrowed blocks: the dot below is that of the stored values
                     if constexpr (!std::is_same<T, C>::value) {
@@ -237,7 +263,29 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
         atomicAdd(e.prof.rows, my_rows);
         atomicAdd(e.prof.nnz, my_nnz);
     }
-    if (DOT) {
+    if constexpr (DOT && std::is_same<C, float>::value) {
+        // double-float combination on the FP32 pipe; partials written as DF pairs
+        DF *sd = reinterpret_cast<DF *>(&s_dot[0][0]);
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                DF d{dot[v][q], 0.f};
+#pragma unroll
+                for (int off = LPR; off < 32; off <<= 1) {
+                    const DF o{__shfl_xor_sync(0xffffffffu, d.hi, off), __shfl_xor_sync(0xffffffffu, d.lo, off)};
+                    df_merge(d, o);
+                }
+                if (grp == 0) sd[warp * W + cb + 4 * v + q] = d;
+            }
+        __syncthreads();
+        DF *out = reinterpret_cast<DF *>(e.dot_partials);
+        for (int c = threadIdx.x; c < W; c += blockDim.x) {
+            DF s = sd[c];
+            for (int w2 = 1; w2 < WARPS; ++w2) df_merge(s, sd[w2 * W + c]);
+            out[int64_t(blockIdx.x) * W + c] = s;
+        }
+    } else if constexpr (DOT) {
 #pragma unroll
         for (int v = 0; v < VPL; ++v)
 #pragma unroll

@@ -20,8 +20,11 @@ METHODS = {"cbl": 0, "gbl": 1, "sbl": 2, "cheb": 3, "cheb2": 4}
 PHIS = {"exp": 0, "spline": 1}
 DTYPES = {"f32": 0, "bf16": 1, "f64": 2}
 KB_GRAPH_SKIP_SYMMETRY_CHECK = 1
+KB_GRAPH_NORMALIZED = 2
 STATUS = {0: "KB_OK", -1: "KB_ERR_ARG", -2: "KB_ERR_CSR", -3: "KB_ERR_NODES", -4: "KB_ERR_CUDA",
-          -5: "KB_ERR_NOMEM", -6: "KB_ERR_BREAKDOWN", -7: "KB_ERR_UNSUPPORTED"}
+          -5: "KB_ERR_NOMEM", -6: "KB_ERR_BREAKDOWN", -7: "KB_ERR_UNSUPPORTED", -8: "KB_ERR_BUSY",
+          1: "KB_PENDING"}
+KB_PENDING = 1
 
 
 class KbError(RuntimeError):
@@ -40,6 +43,11 @@ class kb_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("steps_done", ctypes.c_int32),
                 ("breakdown_step", ctypes.c_int32), ("spmm_launches", ctypes.c_int32),
                 ("lambda_used", ctypes.c_double)]
+
+
+class kb_server_config(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64)]
 
 
 class kb_kernel_stats(ctypes.Structure):
@@ -89,6 +97,21 @@ def lib() -> ctypes.CDLL:
     L.kb_launch_counter.restype = ctypes.c_int64
     L.kb_kernel_class_name.argtypes = [i32]
     L.kb_kernel_class_name.restype = ctypes.c_char_p
+    L.kb_workspace_bytes.argtypes = [vp, ctypes.c_int, ctypes.c_int, P(kb_params), i32, i32,
+                                     P(ctypes.c_uint64)]
+    L.kb_workspace_bytes.restype = ctypes.c_int
+    L.kb_rls_predict.argtypes = [vp, ctypes.c_int, ctypes.c_int, P(kb_params), vp, i32, i32, vp,
+                                 dbl, vp, vp, vp, P(kb_info)]
+    L.kb_rls_predict.restype = ctypes.c_int
+    L.kb_server_create.argtypes = [i32, P(kb_server_config), P(vp)]
+    L.kb_server_create.restype = ctypes.c_int
+    L.kb_server_submit.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, P(kb_params), vp, i32, i32,
+                                   vp, P(i64)]
+    L.kb_server_submit.restype = ctypes.c_int
+    L.kb_server_poll.argtypes = [vp, i64, i32, P(kb_info), P(dbl)]
+    L.kb_server_poll.restype = ctypes.c_int
+    L.kb_server_destroy.argtypes = [vp]
+    L.kb_server_destroy.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -277,3 +300,71 @@ def kb_cheb_apply_fixed_scratch(graph: Graph, phi: str, params: kb_params, nodes
     _check(L.kb_cheb_apply_fixed_scratch(graph.handle, PHIS[phi], ctypes.byref(params),
                                          nodes.ctypes.data, int(M), int(m),
                                          ctypes.c_void_p(_ptr(Y)), _stream_ptr(stream)))
+
+
+def kb_workspace_bytes(graph: Graph, method: str, phi: str, params: kb_params, M: int, m: int) -> int:
+    """Device scratch bytes one kb_krylov_apply call takes (kb_workspace_bytes)."""
+    b = ctypes.c_uint64()
+    _check(lib().kb_workspace_bytes(graph.handle, METHODS[method], PHIS[phi], ctypes.byref(params),
+                                    int(M), int(m), ctypes.byref(b)))
+    return int(b.value)
+
+
+class Server:
+    """Request queue over kb_krylov_apply (kb_server_create / submit / poll / destroy)."""
+
+    def __init__(self, streams: int = 4, queue_capacity: int = 4096, memory_budget: int = 0,
+                 device: int = 0):
+        cfg = kb_server_config(int(streams), int(queue_capacity), int(memory_budget))
+        h = ctypes.c_void_p()
+        _check(lib().kb_server_create(int(device), ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}   # ticket -> (graph, Y) kept alive until the request is polled
+
+    def submit(self, graph: Graph, method: str, phi: str, params: kb_params, nodes, m: int, Y) -> int:
+        nodes = np.ascontiguousarray(nodes, dtype=np.int32)
+        t = ctypes.c_int64()
+        _check(lib().kb_server_submit(self.handle, graph.handle, METHODS[method], PHIS[phi],
+                                      ctypes.byref(params), nodes.ctypes.data, int(nodes.size), int(m),
+                                      ctypes.c_void_p(_ptr(Y)), ctypes.byref(t)))
+        self._keep[t.value] = (graph, Y)
+        return t.value
+
+    def poll(self, ticket: int, wait_ms: int = 0):
+        """None while pending; else (info dict, latency in ms).  Raises KbError on failure."""
+        inf = kb_info()
+        lat = ctypes.c_double()
+        rc = lib().kb_server_poll(self.handle, int(ticket), int(wait_ms), ctypes.byref(inf),
+                                  ctypes.byref(lat))
+        if rc == KB_PENDING:
+            return None
+        self._keep.pop(ticket, None)
+        _check(rc)
+        return ({"status": inf.status, "steps_done": inf.steps_done,
+                 "breakdown_step": inf.breakdown_step, "spmm_launches": inf.spmm_launches,
+                 "lambda_used": inf.lambda_used}, lat.value)
+
+    def close(self):
+        if self.handle:
+            _check(lib().kb_server_destroy(self.handle))
+            self.handle = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def kb_rls_predict(graph: Graph, method: str, phi: str, params: kb_params, nodes, m: int, labels,
+                   gamma: float, y_pred, stream=None):
+    """RLS predictor (kb_rls_predict): fills device y_pred (n float32), returns c (numpy)."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.int32)
+    lab = np.ascontiguousarray(labels, dtype=np.float64)
+    c = np.zeros(nodes.size, dtype=np.float64)
+    _check(lib().kb_rls_predict(graph.handle, METHODS[method], PHIS[phi], ctypes.byref(params),
+                                nodes.ctypes.data, int(nodes.size), int(m), lab.ctypes.data,
+                                float(gamma), ctypes.c_void_p(_ptr(y_pred)), c.ctypes.data,
+                                _stream_ptr(stream), None))
+    return c

@@ -317,3 +317,98 @@ def test_planted_transposed_eigvectors_is_caught(monkeypatch):
     bad = dense.kernel_columns(_Ld(g), [0, 3], f)
     ref = dense.path_function(9, f)[:, [0, 3]]
     assert np.max(np.abs(good - ref)) < 1e-12 and np.max(np.abs(bad - ref)) > 1e-6
+
+
+# ----------------------------------------------------------------------------- RLS (Section 5)
+from oracle import rls  # noqa: E402
+
+
+def _rls_case(n=40, N=6, seed=20):
+    # a connected graph (2-D grid with about n nodes), so that no Lanczos block breaks down
+    side = int(round(np.sqrt(n)))
+    g = synth.grid_graph((side, max(2, n // side)))
+    L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
+    nodes = synth.sample_nodes(g.n, N, seed=seed + 1)
+    y = np.random.default_rng(seed).choice([-1.0, 1.0], size=N)
+    return L, nodes, y
+
+
+@pytest.mark.parametrize("phi,kw", [("exp", dict(t=2.0)), ("spline", dict(eps=0.1, s=2.0))])
+def test_rls_gamma_zero_interpolates(phi, kw):
+    # Section 2.3: with gamma = 0 the predictor interpolates the labels at W
+    L, nodes, y = _rls_case()
+    pred, c = rls.exact(L, nodes, y, 0.0, phi, **kw)
+    assert np.allclose(pred[nodes], y, atol=1e-9)
+
+
+def test_rls_residual_is_gamma_n_c():
+    # (K + gamma N I) c = y  <=>  y - pred(W) = gamma N c; pins the gamma N scaling
+    L, nodes, y = _rls_case()
+    gamma = 0.3
+    pred, c = rls.exact(L, nodes, y, gamma, "exp", t=1.0)
+    assert np.allclose(y - pred[nodes], gamma * len(nodes) * c, atol=1e-12)
+    # a planted mistake (gamma without the factor N) breaks the identity
+    K = dense.kernel_columns(L.toarray(), nodes, dense.phi_function("exp", t=1.0))[nodes, :]
+    c_bad = np.linalg.solve(K + gamma * np.eye(len(nodes)), y)
+    assert not np.allclose(y - K @ c_bad, gamma * len(nodes) * c_bad, atol=1e-6)
+
+
+def test_rls_krylov_exact_at_full_dimension():
+    # m N >= n: the cbl columns are exact, so the Krylov predictor is the exact one
+    L, nodes, y = _rls_case(n=30, N=6)
+    pe, ce = rls.exact(L, nodes, y, 0.05, "spline", eps=0.1, s=1.0)
+    pk, ck = rls.krylov_predictor("cbl", L, nodes, 6, y, 0.05, "spline", eps=0.1, s=1.0)
+    assert np.allclose(pk, pe, rtol=1e-8, atol=1e-10)
+
+
+def test_rls_algorithm3_equals_collocation_form():
+    # Algorithm 3 (F_1^T phi(H_m) F_1, basis times phi(H_m) F_1 c) equals the general form
+    # with E_W^T Y (identity from the proof of Theorem 3.1)
+    L, nodes, y = _rls_case(n=60, N=5)
+    p1, c1 = rls.cbl_alg3(L, nodes, 4, y, 0.01, "exp", t=1.5)
+    p2, c2 = rls.krylov_predictor("cbl", L, nodes, 4, y, 0.01, "exp", t=1.5)
+    assert np.allclose(c1, c2, rtol=1e-9, atol=1e-12)
+    assert np.allclose(p1, p2, rtol=1e-9, atol=1e-12)
+
+
+def test_rls_error_bound_of_section5():
+    # the bound of Theorem 5.1 (first order): ||y - y_kr|| <= ||y|| / (phi_min + gamma N)
+    # (1 + phi_max / (phi_min + gamma N)) ||phi(L) E_W - p(L) E_W||_2, checked with slack 2
+    L, nodes, y = _rls_case(n=80, N=5, seed=23)
+    gamma, t = 0.05, 1.0
+    f = dense.phi_function("exp", t=t)
+    lam = np.linalg.eigvalsh(L.toarray())
+    pe, _ = rls.exact(L, nodes, y, gamma, "exp", t=t)
+    Ye = dense.kernel_columns(L.toarray(), nodes, f)
+    N = len(nodes)
+    fmin, fmax = f(lam).min(), f(lam).max()
+    for m in (3, 5, 8):
+        pk, _ = rls.krylov_predictor("cbl", L, nodes, m, y, gamma, "exp", t=t)
+        Yk = krylov.apply("cbl", L, nodes, m, "exp", t=t).Y
+        bound = (np.linalg.norm(y) / (fmin + gamma * N) * (1 + fmax / (fmin + gamma * N))
+                 * np.linalg.norm(Ye - Yk, 2))
+        assert np.linalg.norm(pe - pk) <= 2 * bound + 1e-14
+
+
+# ----------------------------------------------------------------------------- normalized L
+@pytest.mark.parametrize("n", [5, 201])
+def test_normalized_path_spectrum_closed_form(n):
+    # the normalized Laplacian of the path P_n has eigenvalues 1 - cos(pi k / (n - 1))
+    g = synth.path_graph(n)
+    Ln = dense.normalized_laplacian_dense(_Ld(g))
+    lam = np.sort(np.linalg.eigvalsh(Ln))
+    ref = np.sort(1.0 - np.cos(np.pi * np.arange(n) / (n - 1)))
+    assert np.allclose(lam, ref, atol=1e-12)
+
+
+def test_normalized_laplacian_properties():
+    # D^{1/2} 1 spans the kernel; spectrum in [0, 2]; isolated nodes give zero rows
+    g = synth.random_geometric_graph(60, 5, seed=9)
+    L = _Ld(g)
+    Ln = dense.normalized_laplacian_dense(L)
+    d = np.diag(L)
+    assert np.allclose(Ln @ np.sqrt(d), 0.0, atol=1e-12)
+    lam = np.linalg.eigvalsh(Ln)
+    assert lam.min() > -1e-12 and lam.max() < 2 + 1e-12
+    iso = np.where(d == 0)[0]
+    assert np.all(Ln[iso, :] == 0.0)
