@@ -46,6 +46,9 @@ enum {
     KB_ERR_BREAKDOWN = -6,    /* a Lanczos block became rank deficient (reading A6)              */
     KB_ERR_UNSUPPORTED = -7,  /* combination not implemented (see kb_krylov_apply)               */
     KB_ERR_BUSY = -8,         /* serving queue full (kb_server_submit)                           */
+    KB_ERR_ORTHOGONALITY = -9,/* the projected matrix left [0, Lambda]: the Lanczos basis lost
+                                 orthogonality (FP32 on graphs whose top eigenvalues converge
+                                 fast, e.g. hubs); rerun with params.reorth = 2 or 1            */
     KB_PENDING = 1            /* not an error: the request has not finished (kb_server_poll)     */
 };
 
@@ -60,9 +63,11 @@ typedef struct {
     double s;           /* spline exponent s > 0 (KB_PHI_SPLINE)                                   */
     double lambda_max;  /* spectral bound Lambda used by KB_CHEB/KB_CHEB2; <= 0 selects the
                            graph's Gershgorin bound max_i sum_j |L_ij| (reading A5)               */
-    int32_t reorth;     /* KB_CBL only: 1 = full reorthogonalisation of each new block against
-                           all earlier blocks, classical Gram-Schmidt applied twice (not in the
-                           paper; needed in finite precision for long runs); 0 = none           */
+    int32_t reorth;     /* KB_CBL only (not in the paper; reading A10): 0 = none (Algorithm 1
+                           as printed); 1 = full: each new block is orthogonalised against all
+                           earlier blocks, classical Gram-Schmidt applied twice; 2 = local: a
+                           second Gram-Schmidt pass against the two previous blocks, which keeps
+                           the FP32 process on the FP64 one where Ritz values converge fast     */
     int32_t basis;      /* kb_dtype of the stored Krylov blocks: KB_F32 (FP32 arithmetic),
                            KB_BF16 (blocks stored in bfloat16, arithmetic in FP32, small
                            matrices as for KB_F32; relative error of order 1e-3 to 1e-2, set
@@ -145,8 +150,10 @@ int kb_graph_info(const kb_graph *g, int64_t *n, int64_t *nnz_offdiag, double *l
  *           device's stream-ordered memory pool on this stream.
  *   info    NULL, or receives facts about the run.  When non-NULL the call synchronises
  *           `stream` and returns KB_ERR_BREAKDOWN if the Lanczos process met a
- *           rank-deficient block (then Y is filled with NaN).  With info == NULL the call
- *           does not synchronise, and a breakdown shows only as NaN in Y.
+ *           rank-deficient block, or KB_ERR_ORTHOGONALITY if phi(H_m) F_1 exceeds the bound
+ *           max phi on [0, Lambda] (the projected matrix left the spectral interval); Y is
+ *           then filled with NaN.  With info == NULL the call does not synchronise, and
+ *           these failures show only as NaN in Y.
  *
  * Not implemented (KB_ERR_UNSUPPORTED): the Lanczos methods with KB_PHI_SPLINE and
  * non-integer s (or s > 64); reorth with methods other than KB_CBL; KB_CBL / KB_GBL with

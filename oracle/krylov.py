@@ -86,8 +86,9 @@ def cbl(L: sp.csr_matrix, nodes, m: int, f, reorth: bool = False,
     X -= Q_k H_kk; (k < m) X = Q_{k+1} H_{k+1,k}.  Then U = phi(H_m) F_1 and
     Y = [Q_1..Q_m] U.  The QR at k = m is skipped because Q_{m+1} is unused (A9).
 
-    ``reorth`` (not in the paper; reading A10) subtracts Q_{1:k}(Q_{1:k}^T X) twice after
-    line 5.  Breakdown (A6): if X vanishes (||X||_F <= tol * Lambda * sqrt(N)) the block
+    ``reorth`` (not in the paper; reading A10): True or "full" subtracts Q_{1:k}(Q_{1:k}^T X)
+    twice after line 5; "local" subtracts Q_k(Q_k^T X) + Q_{k-1}(Q_{k-1}^T X) once more
+    (a second Gram-Schmidt pass against the two blocks of the three-term recurrence).  Breakdown (A6): if X vanishes (||X||_F <= tol * Lambda * sqrt(N)) the block
     Krylov space is invariant, the process stops and H of the reached size is used (the
     result is then exact); a rank-deficient but non-zero X raises Breakdown.
     """
@@ -105,7 +106,9 @@ def cbl(L: sp.csr_matrix, nodes, m: int, f, reorth: bool = False,
         X = _three_term(L, Qk, Qprev, Hoff.T)
         Hkk = _project(Qk, X)
         X = _subtract(X, Qk, Hkk)
-        if reorth:
+        if reorth == "local":
+            X = X - Qk @ (Qk.T @ X) - Qprev @ (Qprev.T @ X)
+        elif reorth:
             B = np.hstack(Q)
             for _ in range(2):
                 X = X - B @ (B.T @ X)

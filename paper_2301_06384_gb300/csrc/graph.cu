@@ -324,6 +324,7 @@ extern "C" const char *kb_status_string(int status) {
         case KB_ERR_BREAKDOWN: return "Lanczos breakdown (rank-deficient block)";
         case KB_ERR_UNSUPPORTED: return "unsupported combination";
         case KB_ERR_BUSY: return "serving queue full";
+        case KB_ERR_ORTHOGONALITY: return "projected matrix outside [0, Lambda] (basis lost orthogonality)";
         case KB_PENDING: return "pending";
         default: return "unknown status";
     }

@@ -47,8 +47,8 @@ int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, 
                         double *c2, Ctrl *ctrl, cudaStream_t s);
 int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const double *beta,
                        const double *sigma, int phi_kind, double eps, int s_int, double lam,
-                       const ChebCoef &cc, double *omega, double *work, const Ctrl *ctrl,
-                       cudaStream_t s);
+                       const ChebCoef &cc, double *omega, double *work, Ctrl *ctrl,
+                       double bound, cudaStream_t s);
 template <typename T>
 int launch_axpy_colnorm(int W, T *X, const T *P, const double *a, int64_t n, double *parts,
                         int *grid_out, const Ctrl *ctrl, const int32_t *tgen, int limit,
@@ -77,5 +77,8 @@ int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double ep
 
 // Graph utilities.
 int launch_gershgorin(const GraphDev &g, double *out, cudaStream_t s);
+
+// Marks the solve KB_ERR_ORTHOGONALITY when |U| exceeds bound or is NaN.
+int launch_check_projected(const double *U, int64_t count, double bound, Ctrl *ctrl, cudaStream_t s);
 
 }  // namespace kb

@@ -126,6 +126,21 @@ struct Common {
         if (_rc) return _rc;     \
     } while (0)
 
+// Largest |entry| of phi(H) F_1 when the spectrum of H lies in [0, Lambda] (F_1 = I on the
+// first block): max phi on [0, Lambda]; infinity where no useful bound exists.
+double projected_bound(const Common &c) {
+    const double lam = c.g->lambda;
+    if (c.phi == KB_PHI_EXP) {
+        // slack 25 %: rounding of a slightly perturbed spectrum stays inside, a basis that
+        // lost orthogonality (values growing like cosh(j acosh|x|), |x| > 1) does not
+        if (c.p.t >= 0) return 1.25;
+        const double e = -c.p.t * lam;
+        return e < 700 ? std::exp(e) * 1.25 : std::numeric_limits<double>::infinity();
+    }
+    const double b = std::pow(c.p.eps, -c.p.s);
+    return std::isfinite(b) ? b * 1.25 : std::numeric_limits<double>::infinity();
+}
+
 // ---------------------------------------------------------------- cbl
 template <typename T>
 struct CblBufs {
@@ -226,7 +241,29 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             ua.tgen = tg; ua.limit = k;
             KB_TRY(launch_rowblock<T>(RB_UPD, W, ua, c.s, &grid, M));
             KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
-            if (c.p.reorth) {
+            if (c.p.reorth == 2) {
+                // local reorthogonalisation (not in the paper, reading A10): a second
+                // classical Gram-Schmidt pass against Q_k and Q_{k-1},
+                // X -= Q_k (Q_k^T X) + Q_{k-1} (Q_{k-1}^T X); it keeps the three-term
+                // orthogonality that FP32 rounding erodes when Ritz values converge
+                const T *loc[2] = {Qk, Qp};
+                for (int j = 0; j < 2; ++j) {
+                    if (!loc[j]) continue;
+                    RowArgs<T> ra;
+                    ra.n = n; ra.x = X; ra.qa = loc[j]; ra.partials = b.parts; ra.ctrl = b.ctrl;
+                    ra.tgen = tg; ra.limit = k;
+                    KB_TRY(launch_rowblock<T>(RB_PROJ, W, ra, c.s, &grid, M));
+                    KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl,
+                                            b.Cstk + size_t(j) * W * W));
+                }
+                RowArgs<T> la;
+                la.n = n; la.x = X; la.qa = Qp; la.ca = b.Cstk + size_t(W) * W; la.qb = Qk;
+                la.cb = b.Cstk; la.out = X; la.partials = b.parts; la.ctrl = b.ctrl;
+                la.tgen = tg; la.limit = k;
+                KB_TRY(launch_rowblock<T>(RB_UPD, W, la, c.s, &grid, M));
+                KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+            }
+            if (c.p.reorth == 1) {
                 // full reorthogonalisation (not in the paper, reading A10): classical
                 // Gram-Schmidt against all stored blocks, X -= Q_{1:k} (Q_{1:k}^T X), twice;
                 // the second subtraction also forms the Gram X^T X for the QR
@@ -271,6 +308,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, b.U,
                                     b.ctrl, c.s));
         }
+        KB_TRY(launch_check_projected(b.U, int64_t(m) * M * M, projected_bound(c), b.ctrl, c.s));
         KB_TRY(launch_u_convert<C>(b.U, M, W, m, b.Ut, b.ctrl, c.s));
         // line 9: Y = [Q_1 .. Q_m] U
         RowArgs<T> aa;
@@ -381,8 +419,10 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
                                        b.sigma, b.alive, b.c1, b.c2, b.ctrl, c.s));
         }
         KB_TRY(launch_tridiag_phi(W, M, m, gbl ? 1 : 0, b.alpha, b.beta, b.sigma, int(c.phi),
-                                  c.p.eps, c.s_int, c.g->lambda, cc, b.omega, b.work, b.ctrl, c.s));
+                                  c.p.eps, c.s_int, c.g->lambda, cc, b.omega, b.work, b.ctrl,
+                                  projected_bound(c), c.s));
         KB_TRY(launch_assemble_diag<T>(W, b.basis, bs, m, b.omega, n, Y, ldy, M, M, tg, c.s));
+        KB_TRY(launch_fill_nan(Y, n, ldy, M, b.ctrl, c.s));
         return 0;
     };
     int rc = body();
@@ -560,6 +600,7 @@ int validate(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
     if (method == KB_CHEB2 && m < 2) return fail(KB_ERR_ARG, "KB_CHEB2 needs m >= 2");
     if (params->basis != KB_F32 && params->basis != KB_F64 && params->basis != KB_BF16)
         return fail(KB_ERR_ARG, "bad basis dtype");
+    if (params->reorth < 0 || params->reorth > 2) return fail(KB_ERR_ARG, "reorth must be 0, 1 or 2");
     if (params->reorth && method != KB_CBL)
         return fail(KB_ERR_UNSUPPORTED, "reorthogonalisation is implemented for KB_CBL only");
     const int wmax = params->basis == KB_F64 ? 64 : 128;
@@ -650,6 +691,9 @@ int apply_device(kb_graph *g, kb_method method, kb_phi phi, const kb_params *par
     info->lambda_used = (method == KB_CHEB || method == KB_CHEB2)
                             ? (params->lambda_max > 0 ? params->lambda_max : g->lambda)
                             : 0.0;
+    if (info->status == KB_ERR_ORTHOGONALITY)
+        return fail(info->status, "the projected matrix left the spectral interval [0, Lambda] "
+                                  "(loss of orthogonality of the Lanczos basis); use reorth");
     if (info->status != KB_OK) return fail(info->status, "Lanczos breakdown: rank-deficient block");
     return KB_OK;
 }

@@ -208,7 +208,11 @@ k_rowblock(RowArgs<T> a) {
                 }
             }
             // finish the tile: the register tile goes to shared memory (UPD subtracts it from
-            // the X tile staged there), then the whole tile is stored with coalesced rows
+            // the X tile staged there), then the whole tile is stored with coalesced rows.
+            // The barrier matters when the K loop was empty (an assembly tile below every
+            // block's reach): without it this tile's writes to sO would race with the slower
+            // threads still storing the previous tile from sO.
+            __syncthreads();
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 C o[4];

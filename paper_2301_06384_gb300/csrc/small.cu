@@ -606,7 +606,8 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m
                                                              const double *sigma, int phi_kind,
                                                              double eps, int s_int, double lam,
                                                              ChebCoef cc, double *omega,
-                                                             double *work, const Ctrl *ctrl) {
+                                                             double *work, Ctrl *ctrl,
+                                                             double bound) {
     const int c = blockIdx.x;
     const int ncol = gbl ? 1 : M;
     if (c >= ncol) {
@@ -681,6 +682,14 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m
         }
     }
     __syncthreads();
+    // phi(T) e_1 within max phi on [0, Lambda] unless T left the interval (lost orthogonality)
+    {
+        bool bad = false;
+        for (int k = threadIdx.x; k < s; k += blockDim.x)
+            if (!(fabs(u[k]) <= bound)) bad = true;
+        if (__syncthreads_or(bad) && threadIdx.x == 0)
+            atomicCAS(reinterpret_cast<int *>(&ctrl->status), KB_OK, KB_ERR_ORTHOGONALITY);
+    }
     // E_W = P_1 and Q_1 = sigma_1 P_1, so Y = (1/sigma_1) [Q_1..Q_m] phi(T) e_1
     // (sqrt(N) of Algorithm 2, line 8, for the global method)
     const double scale = 1.0 / sigma[c];
@@ -844,7 +853,28 @@ __global__ void k_u_convert(const double *U, int M, int W, int m, T *Ut, const C
     }
 }
 
+// phi(H) F_1 (or phi(T) e_1) must stay within the bound that holds when the projected
+// matrix has its spectrum in [0, Lambda]; a NaN or a larger entry means the Lanczos basis
+// lost orthogonality, and the solve is marked KB_ERR_ORTHOGONALITY (Y is then NaN-filled).
+__global__ void k_check_projected(const double *U, int64_t count, double bound, Ctrl *ctrl) {
+    if (ctrl->status != KB_OK) return;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * blockDim.x)
+        if (!(fabs(U[i]) <= bound)) bad = true;
+    if (__syncthreads_or(bad) && threadIdx.x == 0)
+        atomicCAS(reinterpret_cast<int *>(&ctrl->status), KB_OK, KB_ERR_ORTHOGONALITY);
+}
+
 // ---------------------------------------------------------------- launchers
+int launch_check_projected(const double *U, int64_t count, double bound, Ctrl *ctrl, cudaStream_t s) {
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, int64_t(num_sms()) * 2)));
+    k_check_projected<<<grid, 256, 0, s>>>(U, count, bound, ctrl);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
 int launch_ctrl_init(Ctrl *c, int steps, cudaStream_t s) {
     k_ctrl_init<<<1, 1, 0, s>>>(c, steps);
     count_launches(1);
@@ -986,8 +1016,8 @@ int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, 
 
 int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const double *beta,
                        const double *sigma, int phi_kind, double eps, int s_int, double lam,
-                       const ChebCoef &cc, double *omega, double *work, const Ctrl *ctrl,
-                       cudaStream_t s) {
+                       const ChebCoef &cc, double *omega, double *work, Ctrl *ctrl,
+                       double bound, cudaStream_t s) {
     prof_begin(KernelClass::PROJECTED, s);
     const size_t smem = m <= TRI_SMEM_M ? sizeof(double) * 6 * size_t(m) : 0;
     static bool attr = false;
@@ -998,7 +1028,7 @@ int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const 
     }
     k_tridiag_phi<<<gbl ? 1 : W, TRI_THREADS, smem, s>>>(W, M, m, gbl, alpha, beta, sigma,
                                                          phi_kind, eps, s_int, lam, cc, omega,
-                                                         work, ctrl);
+                                                         work, ctrl, bound);
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::PROJECTED, s, 0, 0);
     return 0;

@@ -55,6 +55,8 @@ def _rel(a, b):
 
 def _oracle(g, method, nodes, m, phi, **kw):
     L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
+    if kw.get("reorth") == 2:
+        kw = dict(kw, reorth="local")
     return krylov.apply(method, L, nodes, m, phi, **kw).Y
 
 
@@ -408,3 +410,43 @@ def test_stream_ordering_and_no_sync_without_info(kb, rgg):
             kb.kb_krylov_apply(G, "cbl", "exp", kb.make_params(t=1.0), nodes, 16, 12, Y, stream=s)
         s.synchronize()
         assert np.array_equal(Y.cpu().numpy().astype(np.float64), ref)
+
+
+# ---------------------------------------------------------------- loss of orthogonality
+@pytest.fixture(scope="module")
+def ba():
+    return synth.barabasi_albert_graph(50_000, 5, seed=3, weighted=True)
+
+
+def test_lost_orthogonality_is_reported_not_returned(kb, ba):
+    # weighted BA graph: the hub eigenvalues converge within a few steps and the FP32 block
+    # Lanczos basis (reorth = 0) loses orthogonality (the FP64 process keeps the projected
+    # spectrum in [0, Lambda], the FP32 one may not).  The call either reports
+    # KB_ERR_ORTHOGONALITY (Y = NaN) or returns values within the bound max phi on
+    # [0, Lambda]; accuracy on such graphs needs reorth = 2 (next test).
+    nodes = synth.sample_nodes(ba.n, 64, seed=4)
+    with kb.Graph.from_csr(ba) as G:
+        for phi, kw, bound in (("exp", dict(t=0.5), 1.25), ("spline", dict(eps=1.0, s=2.0), 1.25)):
+            try:
+                Y, info = _gpu(kb, G, "cbl", phi, nodes, 30, info=True, **kw)
+            except kb.KbError as e:
+                assert e.code == -9
+                continue
+            assert np.isfinite(Y).all() and np.abs(Y).max() <= bound
+            ref = _oracle(ba, "cbl", nodes, 30, phi, **kw)
+            print(f"BA 5e4 cbl {phi} reorth=0: rel err {_rel(Y, ref):.2e} (no error reported)")
+
+
+@pytest.mark.parametrize("phi,kw", [("exp", dict(t=0.5)), ("spline", dict(eps=1.0, s=2.0))])
+def test_local_reorth_keeps_fp32_on_the_oracle(kb, ba, phi, kw):
+    # reorth = 2 (second Gram-Schmidt pass against Q_k, Q_{k-1}) keeps the FP32 process on
+    # the FP64 one on the same BA graph
+    nodes = synth.sample_nodes(ba.n, 64, seed=4)
+    with kb.Graph.from_csr(ba) as G:
+        Y, info = _gpu(kb, G, "cbl", phi, nodes, 30, info=True, reorth=2, **kw)
+        lam = G.lambda_max
+    ref = _oracle(ba, "cbl", nodes, 30, phi, reorth=2, **kw)
+    err = _rel(Y, ref)
+    print(f"BA 5e4 cbl {phi} reorth=2: rel err {err:.2e}")
+    assert info["status"] == 0
+    assert err < tol32(phi, lam, **kw)

@@ -412,3 +412,14 @@ def test_normalized_laplacian_properties():
     assert lam.min() > -1e-12 and lam.max() < 2 + 1e-12
     iso = np.where(d == 0)[0]
     assert np.all(Ln[iso, :] == 0.0)
+
+
+def test_local_reorth_is_a_no_op_in_exact_arithmetic():
+    # Q_k^T X = 0 and Q_{k-1}^T X = 0 in exact arithmetic, so the second local pass changes
+    # the FP64 result only at rounding level while orthogonality holds
+    g = synth.grid_graph((20, 20))
+    L = _L(g)
+    nodes = synth.sample_nodes(g.n, 5, seed=30)
+    a = krylov.apply("cbl", L, nodes, 8, "exp", t=1.0).Y
+    b = krylov.apply("cbl", L, nodes, 8, "exp", t=1.0, reorth="local").Y
+    assert _rel(b, a) < 1e-12
