@@ -238,7 +238,8 @@ def measured_peaks():
 
 
 def ncu_traffic():
-    """Per-launch DRAM bytes from the committed ncu summary (kernel -> bytes), if any."""
+    """DRAM traffic per algorithmic byte (kernel class -> ratio) from the committed ncu
+    summaries, if any."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     out = {}
     if os.path.exists(p):
@@ -416,7 +417,10 @@ def main():
         if not s or s["total_ms"] <= 0:
             return None
         gbs = s["alg_bytes"] / (s["total_ms"] / 1e3) / 1e9
-        tr = traffic.get(name)
+        ratio = traffic.get(name)
+        # DRAM bytes per launch: the captured traffic/algorithmic ratio times this run's
+        # algorithmic bytes per launch
+        tr = round(ratio * s["alg_bytes"] / max(s["launches"], 1)) if ratio else None
         return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(gbs / peak, 4), "traffic": tr,
                 "kernel": name, "launches_per_step": s["launches"] / a.steps,

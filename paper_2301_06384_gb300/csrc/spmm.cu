@@ -124,7 +124,11 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int grp = lane / LPR;
-    const int cb = (lane % LPR) * (4 * VPL);   // first column of this lane
+    // columns of this lane: 4 consecutive columns in each of VPL slices of 4 * LPR columns,
+    // so that one 16-byte load instruction of a lane group reads one contiguous 4 * LPR
+    // column span (whole 32-byte sectors) of the gathered row
+    const int sub = lane % LPR;
+#define KB_COL(v) (((v) * LPR + sub) * 4)
     const int gid = warp * RPW + grp;
     C dot[VPL][4];
 #pragma unroll
@@ -189,7 +193,7 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
             C acc[VPL][4];
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
-                xi[v] = V4<T>::load(x + row * W + cb + 4 * v);
+                xi[v] = V4<T>::load(x + row * W + KB_COL(v));
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[v][q] = C(0);
             }
@@ -202,7 +206,7 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                         const int j = staged ? s_col[p + u] : __ldg(g.col + base + p + u);
                         wv[u] = g.w ? C(staged ? s_w[p + u] : __ldg(g.w + base + p + u)) : C(1);
 #pragma unroll
-                        for (int v = 0; v < VPL; ++v) xj[u][v] = V4<T>::load(x + int64_t(j) * W + cb + 4 * v);
+                        for (int v = 0; v < VPL; ++v) xj[u][v] = V4<T>::load(x + int64_t(j) * W + KB_COL(v));
                     }
                 }
 #pragma unroll
@@ -218,7 +222,7 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
             const int mk = e.marker ? __ldg(e.marker + row) : -1;
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
-                const int c = cb + 4 * v;
+                const int c = KB_COL(v);
                 C o[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -276,7 +280,7 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                     const DF o{__shfl_xor_sync(0xffffffffu, d.hi, off), __shfl_xor_sync(0xffffffffu, d.lo, off)};
                     df_merge(d, o);
                 }
-                if (grp == 0) sd[warp * W + cb + 4 * v + q] = d;
+                if (grp == 0) sd[warp * W + KB_COL(v) + q] = d;
             }
         __syncthreads();
         DF *out = reinterpret_cast<DF *>(e.dot_partials);
@@ -293,7 +297,7 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                 double dd = double(dot[v][q]);
 #pragma unroll
                 for (int off = LPR; off < 32; off <<= 1) dd += __shfl_xor_sync(0xffffffffu, dd, off);
-                if (grp == 0) s_dot[warp][cb + 4 * v + q] = dd;
+                if (grp == 0) s_dot[warp][KB_COL(v) + q] = dd;
             }
         __syncthreads();
         for (int c = threadIdx.x; c < W; c += blockDim.x) {
@@ -303,6 +307,8 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
         }
     }
 }
+
+#undef KB_COL
 
 template <typename T, int W, bool DOT>
 int occupancy_spmm() {
