@@ -78,6 +78,36 @@ def workload_config(a):
             "frontier": not a.no_frontier}
 
 
+# ----------------------------------------------------------------------------- small config
+def small_config(kb, torch):
+    """CPU-baseline leg for the 32 x 32 grid (n = 1024), 16 nodes, e^{-L}, cbl m = 20: the
+    dense FP64 eigendecomposition on the host beside the GPU kernel columns/s (one stream,
+    50 solves), and the relative error of the GPU result against the dense evaluation."""
+    import synth
+    from oracle import dense
+    g = synth.grid_graph((32, 32))
+    nodes = synth.sample_nodes(g.n, 16, seed=1)
+    with kb.Graph.from_csr(g) as G:
+        Y = kb.kernel_columns(G, "cbl", "exp", nodes, 20, t=1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(50):
+            Y = kb.kernel_columns(G, "cbl", "exp", nodes, 20, t=1.0)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 50
+        y = Y.cpu().numpy().astype(np.float64)
+    t0 = time.perf_counter()
+    Lh = dense.laplacian_dense(g.n, g.rowptr, g.col, g.val)
+    ex = dense.kernel_columns(Lh, nodes, dense.phi_function("exp", t=1.0))
+    cpu_s = time.perf_counter() - t0
+    return {"workload": "grid 32x32, M=16, exp t=1, cbl m=20", "gpu_ms_per_solve": round(ms, 3),
+            "gpu_kernel_columns_per_s": round(16 / (ms / 1e3), 1),
+            "cpu_dense_eig_kernel_columns_per_s": round(16 / cpu_s, 1),
+            "rel_err_vs_dense_eig": float(np.linalg.norm(y - ex) / np.linalg.norm(ex))}
+
+
 # ----------------------------------------------------------------------------- serving
 def serving_sample(a, kb, torch):
     """Latency of kernel-column requests through the serving front end (kb_server_*).
@@ -363,7 +393,10 @@ def main():
     g = synth.random_geometric_graph(a.n, 10, seed=a.graph_seed)
     nodes = synth.sample_nodes(a.n, a.M, seed=replica_node_seed(a.node_seed, rank))
     stream = torch.cuda.current_stream()
-    G = kb.Graph.from_csr(g, stream=stream)
+    torch.cuda.synchronize()
+    tg0 = time.perf_counter()
+    G = kb.Graph.from_csr(g, stream=stream)   # host validation + upload + Gershgorin bound
+    graph_create_ms = (time.perf_counter() - tg0) * 1e3
     streams = [stream] + [torch.cuda.Stream() for _ in range(max(1, a.streams) - 1)]
     solves = [(mth, t) for mth in methods for t in ts]
     Ys = [torch.empty((a.n, a.M), dtype=torch.float32, device="cuda") for _ in solves]
@@ -426,7 +459,8 @@ def main():
                 "kernel": name, "launches_per_step": s["launches"] / a.steps,
                 "avg_launch_ms": s["total_ms"] / max(s["launches"], 1),
                 "share_of_step": round(s["total_ms"] / a.steps / ms, 4),
-                "peak_kind": f"{peak_kind} hbm_gbs"}
+                "peak_kind": f"{peak_kind} hbm_gbs",
+                "frac_of_nominal_7900_gbs": round(gbs / 7900.0, 4)}
 
     dom = max(stats.items(), key=lambda kv: kv[1]["total_ms"])[0] if stats else None
     shares = {k: round(v["total_ms"] / a.steps / ms, 4) for k, v in stats.items() if v["launches"]}
@@ -527,10 +561,12 @@ def main():
             "kernel_shares": shares,
             "e2e": e2e, "fp64_plain": fp64, "solve_ms_one_stream": solve_ms,
             "spmm_roofline_one_stream": spmm_one_stream, "kernel_shares_one_stream": shares_one_stream,
-            "serving": serving,
+            "serving": serving, "graph_create_ms": round(graph_create_ms, 1),
         }
         if world == 1 and not a.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(a)
+            # the small grid case with its dense-eigendecomposition baseline
+            out["cpu_baseline_small_config"] = small_config(kb, torch)
         print(json.dumps(out))
     G.destroy()
     if world > 1:

@@ -76,6 +76,12 @@ typedef struct {
     int32_t no_frontier;/* 0 (default): the products and block updates of step k touch only
                            rows within k hops of W (the Krylov blocks are exactly zero
                            elsewhere); 1: every step touches all n rows                           */
+    int32_t two_pass;   /* 0 (default): the Krylov basis is stored (m blocks of n x W); 1: the
+                           Lanczos methods keep three blocks and run the recurrence twice,
+                           the second time with the recorded coefficients, adding each block
+                           to Y as it is recomputed (twice the products with L, O(n W) memory
+                           instead of the m n W of Table 2).  Not with reorth = 1; no effect
+                           for KB_CHEB / KB_CHEB2, which never store a basis                    */
 } kb_params;
 
 typedef struct {
@@ -142,7 +148,7 @@ int kb_graph_info(const kb_graph *g, int64_t *n, int64_t *nnz_offdiag, double *l
  *           groups of at most 128).
  *   m       number of products with L (block SpMMs), m >= 1 (KB_CHEB2: m >= 2).  The
  *           Lanczos methods return the degree m-1 polynomial p_{phi,m-1} (Algorithm 1,
- *           line 9); KB_CHEB returns the degree-m interpolant; KB_CHEB2 the square of the
+ *           final step); KB_CHEB returns the degree-m interpolant; KB_CHEB2 the square of the
  *           degree floor(m/2) interpolant of sqrt(phi).
  *   Y       device, n x M float32, row-major with leading dimension M (Y[i*M + j] is
  *           entry (node i, column j)); written completely; caller-owned.

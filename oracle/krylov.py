@@ -55,22 +55,22 @@ def matrix_function_sym(H: np.ndarray, f, F: np.ndarray) -> np.ndarray:
 
 
 def _three_term(L, Qk, Qprev, Hprev_k):
-    """Line 3 of Algorithm 1: X = L Q_k - Q_{k-1} H_{k-1,k}, H_{k-1,k} = H_{k,k-1}^T (A1)."""
+    """Algorithm 1, three-term product: X = L Q_k - Q_{k-1} H_{k-1,k}, H_{k-1,k} = H_{k,k-1}^T (A1)."""
     return L @ Qk - Qprev @ Hprev_k
 
 
 def _project(Qk, X):
-    """Line 4 of Algorithm 1: H_kk = Q_k^* X."""
+    """Algorithm 1, diagonal block: H_kk = Q_k^* X."""
     return Qk.T @ X
 
 
 def _subtract(X, Qk, Hkk):
-    """Line 5 of Algorithm 1: X = X - Q_k H_kk."""
+    """Algorithm 1, diagonal removal: X = X - Q_k H_kk."""
     return X - Qk @ Hkk
 
 
 def _reduced_qr(X):
-    """Line 6 of Algorithm 1: X = Q_{k+1} H_{k+1,k}, H_{k+1,k} upper triangular.  The
+    """Algorithm 1, reduced QR: X = Q_{k+1} H_{k+1,k}, H_{k+1,k} upper triangular.  The
     factor is fixed to a non-negative diagonal (the QR is unique only up to signs; A8)."""
     Q, R = np.linalg.qr(X, mode="reduced")
     sgn = np.where(np.diag(R) < 0, -1.0, 1.0)
@@ -87,7 +87,7 @@ def cbl(L: sp.csr_matrix, nodes, m: int, f, reorth: bool = False,
     Y = [Q_1..Q_m] U.  The QR at k = m is skipped because Q_{m+1} is unused (A9).
 
     ``reorth`` (not in the paper; reading A10): True or "full" subtracts Q_{1:k}(Q_{1:k}^T X)
-    twice after line 5; "local" subtracts Q_k(Q_k^T X) + Q_{k-1}(Q_{k-1}^T X) once more
+    twice, right after the diagonal block is subtracted; "local" subtracts Q_k(Q_k^T X) + Q_{k-1}(Q_{k-1}^T X) once more
     (a second Gram-Schmidt pass against the two blocks of the three-term recurrence).  Breakdown (A6): if X vanishes (||X||_F <= tol * Lambda * sqrt(N)) the block
     Krylov space is invariant, the process stops and H of the reached size is used (the
     result is then exact); a rank-deficient but non-zero X raises Breakdown.

@@ -205,6 +205,8 @@ struct RowArgs {
     const Ctrl *ctrl = nullptr;
     const int32_t *tgen = nullptr;    // frontier tiles (nullptr: all rows)
     int limit = 0;                    // process tiles with tgen <= limit (ASM: all tiles)
+    int kbase = 0;                    // ASM: index of the first block (frontier reach)
+    int accumulate = 0;               // ASM: y += product (the accumulator starts from y)
     ProfCount prof;
 };
 template <typename T>

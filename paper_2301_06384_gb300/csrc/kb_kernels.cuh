@@ -57,7 +57,7 @@ int axpy_max_grid();
 template <typename T>
 int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const double *omega,
                          int64_t n, float *Y, int64_t ldy, int mo, int64_t M_alg,
-                         const int32_t *tgen, cudaStream_t s);
+                         const int32_t *tgen, cudaStream_t s, int kbase = 0, int accumulate = 0);
 
 // Frontier restriction: hop distances from the node set (uint8, 255 = not reached) and
 // per-32-row tile minima; expand(k) marks the rows at distance k.

@@ -1,7 +1,7 @@
 // The five block Krylov drivers and the kb_krylov_apply entry points.
 //
 //   cbl   Algorithm 1 (classical block Lanczos) with CholeskyQR2 for the reduced QR of
-//         line 6 and the FP64 projected problem U = phi(H_m) F_1 (line 8).
+//         each new block and the FP64 projected problem U = phi(H_m) F_1.
 //   gbl   Algorithm 2 (global block Lanczos), Frobenius inner products.
 //   sbl   Section 3.3 (one ordinary Lanczos per column), run for all columns at once.
 //   cheb  Section 3.4: the degree-m Lobatto interpolant applied by Clenshaw's backward
@@ -146,22 +146,28 @@ template <typename T>
 struct CblBufs {
     using C = typename Cmp<T>::type;   // small matrices and Gram partials
     T *basis, *wbuf;
-    C *parts, *Cb, *B, *Rinv, *Ut, *Cstk;
+    C *parts, *Ut, *Cstk;
+    // per-step small matrices (one W x W slot per step), kept for the two-pass replay:
+    // H_kk as subtracted, H_{k,k+1} as subtracted at the next step, the two applied inverse
+    // Cholesky factors, and the two local reorthogonalisation coefficient blocks
+    C *Cbs, *Bs, *Rs1, *Rs2, *Cloc;
     double *Gsum, *Hd, *Hs, *R1, *V0, *V1, *V2, *U;
-    Ctrl *ctrl;
+    Ctrl *ctrl, *ctrl2;
     uint8_t *gen;
     int32_t *tgen;
 };
 
 template <typename T>
-void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_grid) {
-    b.basis = ar.take<T>(size_t(m) * n * W);
+void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_grid, bool two_pass) {
+    b.basis = ar.take<T>(size_t(two_pass ? 3 : m) * n * W);
     b.wbuf = ar.take<T>(size_t(n) * W);
     using C = typename Cmp<T>::type;
     b.parts = ar.take<C>(size_t(rb_grid) * W * W);
-    b.Cb = ar.take<C>(size_t(W) * W);
-    b.B = ar.take<C>(size_t(W) * W);
-    b.Rinv = ar.take<C>(size_t(W) * W);
+    b.Cbs = ar.take<C>(size_t(m) * W * W * 6);   // Cbs | Bs | Rs1 | Rs2 | Cloc (2 per step)
+    b.Bs = b.Cbs + size_t(m) * W * W;
+    b.Rs1 = b.Bs + size_t(m) * W * W;
+    b.Rs2 = b.Rs1 + size_t(m) * W * W;
+    b.Cloc = b.Rs2 + size_t(m) * W * W;
     b.Ut = ar.take<C>(size_t(m) * W * W);
     b.Gsum = ar.take<double>(size_t(W) * W);
     b.Hd = ar.take<double>(size_t(m) * M * M);
@@ -173,6 +179,7 @@ void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_g
     b.V2 = ar.take<double>(size_t(m) * M * M);
     b.U = ar.take<double>(size_t(m) * M * M);
     b.ctrl = ar.take<Ctrl>(1);
+    b.ctrl2 = ar.take<Ctrl>(1);
     b.gen = ar.take<uint8_t>(size_t(n));
     b.tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
 }
@@ -184,12 +191,13 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
     const int W = width_for(M);
     const bool f64 = sizeof(C) == 8;
     const int rb_grid = rowblock_max_grid<T>(W);
+    const bool two = c.p.two_pass != 0;
     Arena dry;
     CblBufs<T> b{};
-    plan_cbl<T>(dry, b, n, M, W, m, rb_grid);
+    plan_cbl<T>(dry, b, n, M, W, m, rb_grid, two);
     Arena ar;
     KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
-    plan_cbl<T>(ar, b, n, M, W, m, rb_grid);
+    plan_cbl<T>(ar, b, n, M, W, m, rb_grid, two);
     auto body = [&]() -> int {
         const double lam = c.g->lambda;
         const double tau_inv = f64 ? 1e-12 : 1e-6;
@@ -199,8 +207,11 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
         KB_TRY(launch_ctrl_init(b.ctrl, m, c.s));
         // with the frontier restriction only reached tiles are written, so every block
         // starts from zeros; otherwise each block is written in full
-        KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W * (c.frontier ? m : 1), c.s));
+        const int nbuf = two ? 3 : m;
+        KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W * (c.frontier ? nbuf : 1), c.s));
         KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
+        // slots of steps after a stop are never written: keep them zero
+        KB_CUDA_TRY(cudaMemsetAsync(b.Cbs, 0, sizeof(C) * size_t(m) * W * W * 6, c.s));
         const int32_t *tg = c.frontier ? b.tgen : nullptr;
         if (c.frontier) {
             KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
@@ -210,12 +221,19 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             KB_CUDA_TRY(cudaMemsetAsync(b.wbuf, 0, sizeof(T) * size_t(n) * W, c.s));
         }
         const int64_t bs = n * W;
+        const size_t WW = size_t(W) * W;
+        auto blk = [&](int j) { return b.basis + int64_t(two ? j % 3 : j) * bs; };
         for (int k = 1; k <= m; ++k) {
-            T *Qk = b.basis + (k - 1) * bs;
-            T *Qp = k >= 2 ? b.basis + (k - 2) * bs : nullptr;
+            T *Qk = blk(k - 1);
+            T *Qp = k >= 2 ? blk(k - 2) : nullptr;
+            C *Cb = b.Cbs + (k - 1) * WW;                     // H_kk
+            const C *Bp = k >= 2 ? b.Bs + (k - 2) * WW : nullptr;   // H_{k-1,k} (step k-1)
+            C *Bk = b.Bs + (k - 1) * WW;
+            C *S1 = b.Rs1 + (k - 1) * WW, *S2 = b.Rs2 + (k - 1) * WW;
+            C *Cl = b.Cloc + 2 * (k - 1) * WW;
             // Q_k is supported on rows within k-1 hops of W; L Q_k within k hops
             if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
-            // line 3 (first half): W = L Q_k
+            // block SpMM: W = L Q_k
             LinEpi<T> e;
             e.s1 = 1.0;
             e.out = b.wbuf;
@@ -224,19 +242,19 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             e.limit = k;
             KB_TRY(launch_spmm<T>(c.g->dev, W, Qk, e, c.s, nullptr, M, 0));
             ++c.spmm;
-            // line 4: H_kk = Q_k^T L Q_k
+            // diagonal block: H_kk = Q_k^T L Q_k
             int grid = 0;
             RowArgs<T> pa;
             pa.n = n; pa.x = b.wbuf; pa.qa = Qk; pa.partials = b.parts; pa.ctrl = b.ctrl;
             pa.tgen = tg; pa.limit = k;
             KB_TRY(launch_rowblock<T>(RB_PROJ, W, pa, c.s, &grid, M));
             KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
-            KB_TRY(launch_hkk<C>(b.Gsum, M, W, b.Hd + size_t(k - 1) * M * M, b.Cb, b.ctrl, c.s));
+            KB_TRY(launch_hkk<C>(b.Gsum, M, W, b.Hd + size_t(k - 1) * M * M, Cb, b.ctrl, c.s));
             if (k == m) break;   // Q_{m+1} is never used (reading A9)
-            // lines 3 and 5: X = L Q_k - Q_{k-1} H_{k-1,k} - Q_k H_kk, then Gram X^T X
-            T *X = b.basis + k * bs;
+            // three-term update: X = L Q_k - Q_{k-1} H_{k-1,k} - Q_k H_kk, then Gram X^T X
+            T *X = blk(k);
             RowArgs<T> ua;
-            ua.n = n; ua.x = b.wbuf; ua.qa = Qp; ua.ca = b.B; ua.qb = Qk; ua.cb = b.Cb;
+            ua.n = n; ua.x = b.wbuf; ua.qa = Qp; ua.ca = Bp; ua.qb = Qk; ua.cb = Cb;
             ua.out = X; ua.partials = b.parts; ua.ctrl = b.ctrl;
             ua.tgen = tg; ua.limit = k;
             KB_TRY(launch_rowblock<T>(RB_UPD, W, ua, c.s, &grid, M));
@@ -253,12 +271,11 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                     ra.n = n; ra.x = X; ra.qa = loc[j]; ra.partials = b.parts; ra.ctrl = b.ctrl;
                     ra.tgen = tg; ra.limit = k;
                     KB_TRY(launch_rowblock<T>(RB_PROJ, W, ra, c.s, &grid, M));
-                    KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl,
-                                            b.Cstk + size_t(j) * W * W));
+                    KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl, Cl + j * WW));
                 }
                 RowArgs<T> la;
-                la.n = n; la.x = X; la.qa = Qp; la.ca = b.Cstk + size_t(W) * W; la.qb = Qk;
-                la.cb = b.Cstk; la.out = X; la.partials = b.parts; la.ctrl = b.ctrl;
+                la.n = n; la.x = X; la.qa = Qp; la.ca = Cl + WW; la.qb = Qk;
+                la.cb = Cl; la.out = X; la.partials = b.parts; la.ctrl = b.ctrl;
                 la.tgen = tg; la.limit = k;
                 KB_TRY(launch_rowblock<T>(RB_UPD, W, la, c.s, &grid, M));
                 KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
@@ -285,22 +302,22 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                     KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
                 }
             }
-            // line 6: X = Q_{k+1} H_{k+1,k} by CholeskyQR2
-            KB_TRY(launch_chol<C>(b.Gsum, M, W, 1, k, inv_thresh2, piv2, b.R1, b.Rinv, nullptr,
+            // reduced QR: X = Q_{k+1} H_{k+1,k} by CholeskyQR2
+            KB_TRY(launch_chol<C>(b.Gsum, M, W, 1, k, inv_thresh2, piv2, b.R1, S1, nullptr,
                                   nullptr, b.ctrl, c.s));
             RowArgs<T> ma;
-            ma.n = n; ma.x = X; ma.ca = b.Rinv; ma.out = X; ma.partials = b.parts; ma.ctrl = b.ctrl;
+            ma.n = n; ma.x = X; ma.ca = S1; ma.out = X; ma.partials = b.parts; ma.ctrl = b.ctrl;
             ma.tgen = tg; ma.limit = k;
             KB_TRY(launch_rowblock<T>(RB_MULGRAM, W, ma, c.s, &grid, M));
             KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
-            KB_TRY(launch_chol<C>(b.Gsum, M, W, 2, k, inv_thresh2, piv2, b.R1, b.Rinv,
-                                  b.Hs + size_t(k - 1) * M * M, b.B, b.ctrl, c.s));
+            KB_TRY(launch_chol<C>(b.Gsum, M, W, 2, k, inv_thresh2, piv2, b.R1, S2,
+                                  b.Hs + size_t(k - 1) * M * M, Bk, b.ctrl, c.s));
             RowArgs<T> qa;
-            qa.n = n; qa.x = X; qa.ca = b.Rinv; qa.out = X; qa.ctrl = b.ctrl;
+            qa.n = n; qa.x = X; qa.ca = S2; qa.out = X; qa.ctrl = b.ctrl;
             qa.tgen = tg; qa.limit = k;
             KB_TRY(launch_rowblock<T>(RB_MUL, W, qa, c.s, &grid, M));
         }
-        // line 8: U = phi(H_m) F_1 in FP64
+        // projected problem: U = phi(H_m) F_1 in FP64
         if (c.phi == KB_PHI_EXP) {
             const std::vector<double> d = exp_series_coeffs(c.p.t, lam, 1e-17);
             KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam, d, b.V0, b.V1, b.V2, b.U, b.ctrl, c.s));
@@ -310,12 +327,61 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
         }
         KB_TRY(launch_check_projected(b.U, int64_t(m) * M * M, projected_bound(c), b.ctrl, c.s));
         KB_TRY(launch_u_convert<C>(b.U, M, W, m, b.Ut, b.ctrl, c.s));
-        // line 9: Y = [Q_1 .. Q_m] U
-        RowArgs<T> aa;
-        aa.n = n; aa.basis = b.basis; aa.block_stride = bs; aa.nblk = m; aa.ca = b.Ut;
-        aa.y = Y; aa.ldy = ldy; aa.mo = M; aa.ctrl = b.ctrl; aa.tgen = tg;
-        int grid = 0;
-        KB_TRY(launch_rowblock<T>(RB_ASM, W, aa, c.s, &grid, M));
+        // assembly: Y = [Q_1 .. Q_m] U
+        if (!two) {
+            RowArgs<T> aa;
+            aa.n = n; aa.basis = b.basis; aa.block_stride = bs; aa.nblk = m; aa.ca = b.Ut;
+            aa.y = Y; aa.ldy = ldy; aa.mo = M; aa.ctrl = b.ctrl; aa.tgen = tg;
+            int grid = 0;
+            KB_TRY(launch_rowblock<T>(RB_ASM, W, aa, c.s, &grid, M));
+        } else {
+            // second pass: the same products and updates with the recorded matrices
+            // (bit-identical blocks); Y += Q_k U_k as each block is recomputed
+            KB_TRY(launch_ctrl_init(b.ctrl2, m, c.s));
+            KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W * (c.frontier ? 3 : 1), c.s));
+            KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
+            if (c.frontier) {
+                KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
+                KB_CUDA_TRY(cudaMemsetAsync(b.wbuf, 0, sizeof(T) * size_t(n) * W, c.s));
+            }
+            for (int k = 1; k <= m; ++k) {
+                T *Qk = blk(k - 1);
+                T *Qp = k >= 2 ? blk(k - 2) : nullptr;
+                RowArgs<T> aa;
+                aa.n = n; aa.basis = Qk; aa.block_stride = bs; aa.nblk = 1;
+                aa.ca = b.Ut + (k - 1) * WW; aa.y = Y; aa.ldy = ldy; aa.mo = M; aa.tgen = tg;
+                aa.kbase = k - 1; aa.accumulate = k > 1 ? 1 : 0;
+                int grid = 0;
+                KB_TRY(launch_rowblock<T>(RB_ASM, W, aa, c.s, &grid, M));
+                if (k == m) break;
+                if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                LinEpi<T> e;
+                e.s1 = 1.0;
+                e.out = b.wbuf;
+                e.ctrl = b.ctrl2;
+                e.tgen = tg;
+                e.limit = k;
+                KB_TRY(launch_spmm<T>(c.g->dev, W, Qk, e, c.s, nullptr, M, 0));
+                ++c.spmm;
+                T *X = blk(k);
+                RowArgs<T> ua;
+                ua.n = n; ua.x = b.wbuf; ua.qa = Qp; ua.ca = k >= 2 ? b.Bs + (k - 2) * WW : nullptr;
+                ua.qb = Qk; ua.cb = b.Cbs + (k - 1) * WW;
+                ua.out = X; ua.partials = b.parts; ua.ctrl = b.ctrl2; ua.tgen = tg; ua.limit = k;
+                KB_TRY(launch_rowblock<T>(RB_UPD, W, ua, c.s, &grid, M));
+                if (c.p.reorth == 2) {
+                    RowArgs<T> la = ua;
+                    la.x = X; la.ca = b.Cloc + (2 * (k - 1) + 1) * WW; la.cb = b.Cloc + 2 * (k - 1) * WW;
+                    KB_TRY(launch_rowblock<T>(RB_UPD, W, la, c.s, &grid, M));
+                }
+                for (int pass = 0; pass < 2; ++pass) {
+                    RowArgs<T> qa;
+                    qa.n = n; qa.x = X; qa.ca = (pass == 0 ? b.Rs1 : b.Rs2) + (k - 1) * WW;
+                    qa.out = X; qa.ctrl = b.ctrl2; qa.tgen = tg; qa.limit = k;
+                    KB_TRY(launch_rowblock<T>(RB_MUL, W, qa, c.s, &grid, M));
+                }
+            }
+        }
         KB_TRY(launch_fill_nan(Y, n, ldy, M, b.ctrl, c.s));
         return 0;
     };
@@ -334,26 +400,28 @@ struct LzBufs {
     T *basis;
     double *parts, *sigma, *alpha, *beta, *work;
     int32_t *alive;
-    double *c1, *c2, *aupd, *omega;
-    Ctrl *ctrl;
+    double *c1, *c2, *aupd, *omega;   // c1, c2, aupd: one row of W per step
+    Ctrl *ctrl, *ctrl2;
     uint8_t *gen;
     int32_t *tgen;
 };
 
 template <typename T>
-void plan_lz(Arena &ar, LzBufs<T> &b, int64_t n, int W, int m, int pgrid) {
-    b.basis = ar.take<T>(size_t(m + 1) * n * W);
+void plan_lz(Arena &ar, LzBufs<T> &b, int64_t n, int W, int m, int pgrid, bool two_pass) {
+    // two-pass: three rotating blocks; the coefficients of every step are kept for the replay
+    b.basis = ar.take<T>(size_t(two_pass ? 3 : m + 1) * n * W);
     b.parts = ar.take<double>(size_t(pgrid) * W);
     b.sigma = ar.take<double>(size_t(m + 1) * W);
     b.alpha = ar.take<double>(size_t(m + 1) * W);
     b.beta = ar.take<double>(size_t(m + 1) * W);
     b.work = ar.take<double>(size_t(W) * 4 * m);
     b.alive = ar.take<int32_t>(W);
-    b.c1 = ar.take<double>(W);
-    b.c2 = ar.take<double>(W);
-    b.aupd = ar.take<double>(W);
+    b.c1 = ar.take<double>(size_t(m + 1) * W);
+    b.c2 = ar.take<double>(size_t(m + 1) * W);
+    b.aupd = ar.take<double>(size_t(m + 1) * W);
     b.omega = ar.take<double>(size_t(m) * W);
     b.ctrl = ar.take<Ctrl>(1);
+    b.ctrl2 = ar.take<Ctrl>(1);
     b.gen = ar.take<uint8_t>(size_t(n));
     b.tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
 }
@@ -373,35 +441,42 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
         cc.n = int(d.size());
         for (int j = 0; j < cc.n; ++j) cc.d[j] = d[j];
     }
+    const bool two = c.p.two_pass != 0;
     Arena dry;
     LzBufs<T> b{};
-    plan_lz<T>(dry, b, n, W, m, pgrid);
+    plan_lz<T>(dry, b, n, W, m, pgrid, two);
     Arena ar;
     KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
-    plan_lz<T>(ar, b, n, W, m, pgrid);
+    plan_lz<T>(ar, b, n, W, m, pgrid, two);
     auto body = [&]() -> int {
         const double thresh = (f64 ? 1e-12 : 1e-6) * c.g->lambda;
         KB_TRY(launch_ctrl_init(b.ctrl, m, c.s));
-        KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W * (c.frontier ? m + 1 : 1), c.s));
+        const int nbuf = two ? 3 : m + 1;
+        KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W * (c.frontier ? nbuf : 1), c.s));
         KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
         const int32_t *tg = c.frontier ? b.tgen : nullptr;
         if (c.frontier) KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
+        // coefficients of steps after an invariant stop are never written: keep them zero
+        KB_CUDA_TRY(cudaMemsetAsync(b.c1, 0, sizeof(double) * size_t(m + 1) * W, c.s));
+        KB_CUDA_TRY(cudaMemsetAsync(b.c2, 0, sizeof(double) * size_t(m + 1) * W, c.s));
+        KB_CUDA_TRY(cudaMemsetAsync(b.aupd, 0, sizeof(double) * size_t(m + 1) * W, c.s));
         KB_CUDA_TRY(cudaMemsetAsync(b.beta, 0, sizeof(double) * size_t(m + 1) * W, c.s));
         KB_CUDA_TRY(cudaMemsetAsync(b.alpha, 0, sizeof(double) * size_t(m + 1) * W, c.s));
         KB_CUDA_TRY(cudaMemsetAsync(b.sigma, 0, sizeof(double) * size_t(m + 1) * W, c.s));
         KB_TRY(launch_lanczos_init(W, M, gbl ? 1 : 0, f64 ? 0 : 1, b.sigma, b.alive, b.c1, b.c2, c.s));
         const int64_t bs = n * W;
+        auto blk = [&](int j) { return b.basis + int64_t(two ? j % 3 : j) * bs; };
         for (int k = 1; k <= m; ++k) {
-            T *Pk = b.basis + (k - 1) * bs;
-            T *Pp = k >= 2 ? b.basis + (k - 2) * bs : nullptr;
-            T *X = b.basis + k * bs;
+            T *Pk = blk(k - 1);
+            T *Pp = k >= 2 ? blk(k - 2) : nullptr;
+            T *X = blk(k);
             if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
             // X = L Q_k - h_{k,k-1} Q_{k-1}, with Q_k = sigma_k P_k; dots <P_k, X> per column
             LinEpi<T> e;
             e.tgen = tg;
             e.limit = k;
-            e.a1 = b.c1;
-            e.a2 = b.c2;
+            e.a1 = b.c1 + int64_t(k - 1) * W;
+            e.a2 = b.c2 + int64_t(k - 1) * W;
             e.s0 = 0.0;
             e.y = Pp;
             e.out = X;
@@ -411,17 +486,53 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
             KB_TRY(launch_spmm<T>(c.g->dev, W, Pk, e, c.s, &grid, M, Pp ? 1 : 0));
             ++c.spmm;
             KB_TRY(launch_lanczos_alpha(b.parts, grid, W, M, gbl ? 1 : 0, k - 1, f64 ? 0 : 1, b.sigma, b.alpha,
-                                        b.aupd, b.ctrl, c.s));
+                                        b.aupd + int64_t(k - 1) * W, b.ctrl, c.s));
             if (k == m) break;
             int grid2 = 0;
-            KB_TRY(launch_axpy_colnorm<T>(W, X, Pk, b.aupd, n, b.parts, &grid2, b.ctrl, tg, k, M, c.s));
+            KB_TRY(launch_axpy_colnorm<T>(W, X, Pk, b.aupd + int64_t(k - 1) * W, n, b.parts, &grid2,
+                                          b.ctrl, tg, k, M, c.s));
             KB_TRY(launch_lanczos_beta(b.parts, grid2, W, M, gbl ? 1 : 0, k - 1, f64 ? 0 : 1, thresh, b.beta,
-                                       b.sigma, b.alive, b.c1, b.c2, b.ctrl, c.s));
+                                       b.sigma, b.alive, b.c1 + int64_t(k) * W, b.c2 + int64_t(k) * W,
+                                       b.ctrl, c.s));
         }
         KB_TRY(launch_tridiag_phi(W, M, m, gbl ? 1 : 0, b.alpha, b.beta, b.sigma, int(c.phi),
                                   c.p.eps, c.s_int, c.g->lambda, cc, b.omega, b.work, b.ctrl,
                                   projected_bound(c), c.s));
-        KB_TRY(launch_assemble_diag<T>(W, b.basis, bs, m, b.omega, n, Y, ldy, M, M, tg, c.s));
+        if (!two) {
+            KB_TRY(launch_assemble_diag<T>(W, b.basis, bs, m, b.omega, n, Y, ldy, M, M, tg, c.s));
+        } else {
+            // second pass: the same products and updates with the recorded coefficients
+            // (bit-identical blocks), each block added to Y as soon as it exists
+            KB_TRY(launch_ctrl_init(b.ctrl2, m, c.s));
+            KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W * (c.frontier ? 3 : 1), c.s));
+            KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
+            if (c.frontier) KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
+            KB_TRY(launch_assemble_diag<T>(W, blk(0), bs, 1, b.omega, n, Y, ldy, M, M, nullptr, c.s, 0, 0));
+            for (int k = 1; k < m; ++k) {
+                T *Pk = blk(k - 1);
+                T *Pp = k >= 2 ? blk(k - 2) : nullptr;
+                T *X = blk(k);
+                if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                LinEpi<T> e;
+                e.tgen = tg;
+                e.limit = k;
+                e.a1 = b.c1 + int64_t(k - 1) * W;
+                e.a2 = b.c2 + int64_t(k - 1) * W;
+                e.s0 = 0.0;
+                e.y = Pp;
+                e.out = X;
+                e.dot_partials = b.parts;
+                e.ctrl = b.ctrl2;
+                int grid = 0;
+                KB_TRY(launch_spmm<T>(c.g->dev, W, Pk, e, c.s, &grid, M, Pp ? 1 : 0));
+                ++c.spmm;
+                int grid2 = 0;
+                KB_TRY(launch_axpy_colnorm<T>(W, X, Pk, b.aupd + int64_t(k - 1) * W, n, b.parts, &grid2,
+                                              b.ctrl2, tg, k, M, c.s));
+                KB_TRY(launch_assemble_diag<T>(W, X, bs, 1, b.omega + int64_t(k) * W, n, Y, ldy, M, M,
+                                               tg, c.s, k, 1));
+            }
+        }
         KB_TRY(launch_fill_nan(Y, n, ldy, M, b.ctrl, c.s));
         return 0;
     };
@@ -548,13 +659,13 @@ int run_cheb(Common &c, bool squared, const int32_t *nodes, int M, int m, float 
 
 // Scratch bytes of one solve (the same plans the runs allocate).
 template <typename T>
-size_t workspace_bytes_t(int64_t n, kb_method method, int M, int m) {
+size_t workspace_bytes_t(int64_t n, kb_method method, int M, int m, bool two) {
     Arena dry;
     const int W = width_for(M);
     switch (method) {
         case KB_CBL: {
             CblBufs<T> b{};
-            plan_cbl<T>(dry, b, n, M, W, m, rowblock_max_grid<T>(W));
+            plan_cbl<T>(dry, b, n, M, W, m, rowblock_max_grid<T>(W), two);
             break;
         }
         case KB_GBL:
@@ -563,7 +674,7 @@ size_t workspace_bytes_t(int64_t n, kb_method method, int M, int m) {
             const int Mg = method == KB_SBL ? std::min(M, sizeof(T) == 8 ? 64 : 128) : M;
             const int Wg = width_for(Mg);
             LzBufs<T> b{};
-            plan_lz<T>(dry, b, n, Wg, m, std::max(spmm_max_grid<T>(Wg), axpy_max_grid()));
+            plan_lz<T>(dry, b, n, Wg, m, std::max(spmm_max_grid<T>(Wg), axpy_max_grid()), two);
             break;
         }
         case KB_CHEB:
@@ -601,6 +712,9 @@ int validate(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
     if (params->basis != KB_F32 && params->basis != KB_F64 && params->basis != KB_BF16)
         return fail(KB_ERR_ARG, "bad basis dtype");
     if (params->reorth < 0 || params->reorth > 2) return fail(KB_ERR_ARG, "reorth must be 0, 1 or 2");
+    if (params->two_pass != 0 && params->two_pass != 1) return fail(KB_ERR_ARG, "two_pass must be 0 or 1");
+    if (params->two_pass && params->reorth == 1)
+        return fail(KB_ERR_UNSUPPORTED, "full reorthogonalisation needs the stored basis (two_pass = 0)");
     if (params->reorth && method != KB_CBL)
         return fail(KB_ERR_UNSUPPORTED, "reorthogonalisation is implemented for KB_CBL only");
     const int wmax = params->basis == KB_F64 ? 64 : 128;
@@ -752,9 +866,9 @@ extern "C" int kb_workspace_bytes(kb_graph *g, kb_method method, kb_phi phi, con
         if (rc) return rc;
         const int64_t n = g->dev.n;
         switch (params->basis) {
-            case KB_F64: *bytes = workspace_bytes_t<double>(n, method, M, m); break;
-            case KB_BF16: *bytes = workspace_bytes_t<__nv_bfloat16>(n, method, M, m); break;
-            default: *bytes = workspace_bytes_t<float>(n, method, M, m); break;
+            case KB_F64: *bytes = workspace_bytes_t<double>(n, method, M, m, params->two_pass != 0); break;
+            case KB_BF16: *bytes = workspace_bytes_t<__nv_bfloat16>(n, method, M, m, params->two_pass != 0); break;
+            default: *bytes = workspace_bytes_t<float>(n, method, M, m, params->two_pass != 0); break;
         }
         return KB_OK;
     } catch (...) {

@@ -1,5 +1,5 @@
 // The projected problem U = phi(H_m) F_1 of the classical block Lanczos method
-// (Algorithm 1, line 8), in FP64 on the device.
+// (the projected step of Algorithm 1), in FP64 on the device.
 //
 // H_m is block tridiagonal: diagonal blocks H_kk (symmetric) and sub-diagonal blocks
 // H_{k+1,k} = R (upper triangular), super-diagonal blocks R^T.  Its spectrum lies in

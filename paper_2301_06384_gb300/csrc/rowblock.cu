@@ -1,6 +1,6 @@
-// Tall-skinny block kernels of the classical block Lanczos step (Algorithm 1, lines 4-6)
-// and of its final assembly (line 9): products of n x W blocks with W x W matrices and
-// Gram matrices A^T B of n x W blocks.
+// Tall-skinny block kernels of the classical block Lanczos step (Algorithm 1: diagonal
+// block, three-term update, reduced QR) and of its final assembly: products of n x W
+// blocks with W x W matrices and Gram matrices A^T B of n x W blocks.
 //
 // One CTA of 256 threads owns a tile of TR = 4096/W consecutive rows (16 KB of FP32) at
 // a time and walks tiles with a persistent grid-stride loop.  Products are K-chunked:
@@ -133,7 +133,7 @@ k_rowblock(RowArgs<T> a) {
         if (a.tgen) {
             const int tmin = tile_min_gen(a.tgen, r0, rows_t);
             if (MODE == RB_ASM) {
-                kb0 = min(tmin, nkb);
+                kb0 = min(max(tmin - a.kbase, 0), nkb);
             } else {
                 if (tmin > a.limit) continue;
                 if (MODE == RB_ASMSUB) kb0 = min(tmin, nkb);
@@ -156,6 +156,16 @@ k_rowblock(RowArgs<T> a) {
             for (int r = 0; r < 4; ++r)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[r][q] = 0;
+            if (MODE == RB_ASM && a.accumulate) {
+                // continue the accumulation of the earlier blocks from y (FP32, as stored)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int64_t row = r0 + row0 + r;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (row < a.n && col4 + q < a.mo) acc[r][q] = C(a.y[row * a.ldy + col4 + q]);
+                }
+            }
             for (int kb = kb0; kb < nkb; ++kb) {
                 const T *src;
                 const C *cmat;

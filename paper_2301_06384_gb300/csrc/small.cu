@@ -1,15 +1,15 @@
 // Small dense FP64 kernels and element-wise kernels of the Krylov drivers.
 //
-//  * k_hkk          symmetrised diagonal block H_kk (Algorithm 1, line 4).
+//  * k_hkk          symmetrised diagonal block H_kk (Algorithm 1).
 //  * k_chol         reduced QR of the new block by CholeskyQR, FP64 Cholesky factor and its
-//                   inverse (Algorithm 1, line 6); the second pass forms H_{k+1,k} = R2 R1
-//                   and the transposed block used by the next three-term step (line 7,
+//                   inverse (the reduced QR of Algorithm 1); the second pass forms H_{k+1,k} = R2 R1
+//                   and the transposed block used by the next three-term step (Algorithm 1,
 //                   reading A1).  Invariant subspaces stop the process, rank-deficient
 //                   blocks report a breakdown (reading A6).
 //  * k_lanczos_*    scalar recurrences of the global (Algorithm 2) and sequential
 //                   (Section 3.3) Lanczos methods: h_kk, h_{k+1,k}, 1/h.
-//  * k_tridiag_phi  u = phi(H_m) f_1 for the tridiagonal Lanczos matrices (Algorithm 2,
-//                   line 8; Section 3.3 with phi applied, reading A2).
+//  * k_tridiag_phi  u = phi(H_m) f_1 for the tridiagonal Lanczos matrices (the projected
+//                   step of Algorithm 2; Section 3.3 with phi applied, reading A2).
 //  * element-wise   unit blocks E_W, node markers, column norms, scaled copies, the
 //                   diagonal assembly sum_k u_k Q_k, NaN fill on breakdown.
 #include <type_traits>
@@ -196,7 +196,7 @@ __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, d
     return true;
 }
 
-// Reduced QR of the new block by CholeskyQR (Algorithm 1, line 6), pass 1 or 2 of
+// Reduced QR of the new block by CholeskyQR (Algorithm 1), pass 1 or 2 of
 // CholeskyQR2.  Outputs: Rinv (W x W, basis precision) applied by the row-block kernels;
 // pass 1 records R1 = the FP64 inverse of the applied inverse; pass 2 records
 // H_{k+1,k} = R2 R1 (rounded to the basis precision) and B = H^T.
@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m
             atomicCAS(reinterpret_cast<int *>(&ctrl->status), KB_OK, KB_ERR_ORTHOGONALITY);
     }
     // E_W = P_1 and Q_1 = sigma_1 P_1, so Y = (1/sigma_1) [Q_1..Q_m] phi(T) e_1
-    // (sqrt(N) of Algorithm 2, line 8, for the global method)
+    // (the sqrt(N) factor of Algorithm 2's final step, for the global method)
     const double scale = 1.0 / sigma[c];
     if (gbl) {
         for (int idx = threadIdx.x; idx < m * W; idx += blockDim.x) {
@@ -780,12 +780,14 @@ __global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const do
 }
 
 // Y[i, c] = sum_k omega_k[c] P_k[i, c]  (global / sequential Lanczos assembly); with a
-// frontier, block k is zero in rows whose tile is more than k hops from W.
+// frontier, block kbase + k is zero in rows whose tile is more than kbase + k hops from W.
+// accumulate: Y is added to (the FP32 accumulator starts from Y, so adding the blocks one
+// launch at a time gives the same bits as one launch over all of them).
 template <typename T, int W>
 __global__ void __launch_bounds__(256) k_assemble_diag(const T *basis, int64_t stride, int nblk,
                                                         const double *omega, int64_t n, float *Y,
                                                         int64_t ldy, int mo, const int32_t *tgen,
-                                                        ProfCount pc) {
+                                                        int kbase, int accumulate, ProfCount pc) {
     constexpr int CG = W / 4;
     constexpr int RPP = 256 / CG;
     using C = typename Cmp<T>::type;
@@ -798,7 +800,11 @@ __global__ void __launch_bounds__(256) k_assemble_diag(const T *basis, int64_t s
     unsigned long long my_units = 0;
     for (int64_t row = int64_t(blockIdx.x) * RPP + rr; row < n; row += int64_t(gridDim.x) * RPP) {
         C acc[4] = {0, 0, 0, 0};
-        const int k0 = tgen ? min(__ldg(tgen + row / ACT_ROWS), nblk) : 0;
+        if (accumulate)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (c4 + q < mo) acc[q] = Y[row * ldy + c4 + q];
+        const int k0 = tgen ? min(max(__ldg(tgen + row / ACT_ROWS) - kbase, 0), nblk) : 0;
         if (cg == 0) my_units += nblk - k0;
         for (int k = k0; k < nblk; ++k) {
             C pv[4];
@@ -1063,13 +1069,13 @@ int axpy_max_grid() { return num_sms() * 4; }
         cudaFuncSetAttribute(k_assemble_diag<T, WW>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                              int(smem));                                                      \
         k_assemble_diag<T, WW><<<grid, 256, smem, s>>>(basis, stride, nblk, omega, n, Y, ldy, mo,  \
-                                                       tgen, pc);                             \
+                                                       tgen, kbase, accumulate, pc);          \
     } while (0)
 
 template <typename T>
 int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const double *omega,
                          int64_t n, float *Y, int64_t ldy, int mo, int64_t M_alg,
-                         const int32_t *tgen, cudaStream_t s) {
+                         const int32_t *tgen, cudaStream_t s, int kbase, int accumulate) {
     const int rpp = 256 / (W / 4);
     const int grid = std::max(1, int(std::min<int64_t>((n + rpp - 1) / rpp, int64_t(num_sms()) * 8)));
     const size_t smem = sizeof(typename Cmp<T>::type) * size_t(nblk) * W;
@@ -1110,7 +1116,7 @@ int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ct
                                         cudaStream_t);                                          \
     template int launch_assemble_diag<T>(int, const T *, int64_t, int, const double *, int64_t, \
                                          float *, int64_t, int, int64_t, const int32_t *,       \
-                                         cudaStream_t);                                         \
+                                         cudaStream_t, int, int);                               \
     template int launch_u_convert<T>(const double *, int, int, int, T *, const Ctrl *, cudaStream_t);
 KB_INST(float)
 KB_INST(double)
@@ -1126,6 +1132,6 @@ template int launch_axpy_colnorm<__nv_bfloat16>(int, __nv_bfloat16 *, const __nv
                                                 cudaStream_t);
 template int launch_assemble_diag<__nv_bfloat16>(int, const __nv_bfloat16 *, int64_t, int,
                                                  const double *, int64_t, float *, int64_t, int,
-                                                 int64_t, const int32_t *, cudaStream_t);
+                                                 int64_t, const int32_t *, cudaStream_t, int, int);
 
 }  // namespace kb

@@ -450,3 +450,44 @@ def test_local_reorth_keeps_fp32_on_the_oracle(kb, ba, phi, kw):
     print(f"BA 5e4 cbl {phi} reorth=2: rel err {err:.2e}")
     assert info["status"] == 0
     assert err < tol32(phi, lam, **kw)
+
+
+# ---------------------------------------------------------------- two-pass Lanczos
+@pytest.mark.parametrize("method,kw", [("gbl", {}), ("sbl", {}), ("cbl", {}), ("cbl", dict(reorth=2))])
+@pytest.mark.parametrize("nf", [0, 1])
+def test_two_pass_reproduces_the_stored_basis_result(kb, rgg, method, kw, nf):
+    # the second pass repeats the products and updates with the recorded coefficients, so
+    # the blocks are bit-identical, and the accumulator of Y continues from the stored
+    # partial sums: the result equals the one-pass result exactly
+    import torch
+    nodes = synth.sample_nodes(rgg.n, 48, seed=8)
+    with kb.Graph.from_csr(rgg) as G:
+        Y1, i1 = kb.kernel_columns(G, method, "exp", nodes, 24, info=True, t=2.0, no_frontier=nf, **kw)
+        Y2, i2 = kb.kernel_columns(G, method, "exp", nodes, 24, info=True, t=2.0, no_frontier=nf,
+                                   two_pass=1, **kw)
+        torch.cuda.synchronize()
+        p1 = kb.make_params(t=2.0, no_frontier=nf, **kw)
+        p2 = kb.make_params(t=2.0, no_frontier=nf, two_pass=1, **kw)
+        w1 = [kb.kb_workspace_bytes(G, method, "exp", p1, 48, m) for m in (24, 48)]
+        w2 = [kb.kb_workspace_bytes(G, method, "exp", p2, 48, m) for m in (24, 48)]
+    assert i2["spmm_launches"] == 2 * 24 - 1
+    assert torch.equal(Y1, Y2), float((Y1 - Y2).abs().max())
+    # scratch: a few n x W blocks instead of m of them; what still grows with m are the
+    # per-step W x W coefficient records, far less than one stored block per step
+    assert w2[0] < 0.3 * w1[0]
+    assert (w2[1] - w2[0]) < 0.2 * (w1[1] - w1[0])
+
+
+def test_two_pass_spline_and_errors(kb, rgg):
+    import torch
+    nodes = synth.sample_nodes(rgg.n, 16, seed=9)
+    with kb.Graph.from_csr(rgg) as G:
+        Y = _gpu(kb, G, "cbl", "spline", nodes, 16, eps=0.1, s=2.0, two_pass=1)
+        lam = G.lambda_max
+        Yr = torch.empty((rgg.n, 16), dtype=torch.float32, device="cuda")
+        with pytest.raises(kb.KbError) as ei:
+            kb.kb_krylov_apply(G, "cbl", "exp", kb.make_params(t=1.0, reorth=1, two_pass=1),
+                               nodes, 16, 8, Yr)
+        assert ei.value.code == -7
+    ref = _oracle(rgg, "cbl", nodes, 16, "spline", eps=0.1, s=2.0)
+    assert _rel(Y, ref) < tol32("spline", lam, eps=0.1, s=2.0)
