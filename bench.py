@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--serve-max-n", type=int, default=200_000,
                     help="largest of the 8 serving graphs (the others are log-spaced from 1e4)")
     ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--schedule", default="lpt", choices=["lpt", "rr"],
+                    help="assignment of the independent solves of a step to the streams: "
+                         "longest first onto the least loaded stream, or round robin")
     return ap.parse_args()
 
 
@@ -74,8 +77,29 @@ def workload_config(a):
             "t": [float(x) for x in a.ts.split(",")], "methods": a.methods.split(","),
             "graph_seed": a.graph_seed, "node_seed": a.node_seed, "basis": a.basis,
             "l2": "256 MiB flush write between steps; per-solve working set > L2",
-            "streams": a.streams,
+            "streams": a.streams, "schedule": a.schedule,
             "frontier": not a.no_frontier}
+
+
+# relative cost of one solve per method (single-stream solve times at n = 1e6, M = 64,
+# m = 30), used only to spread the independent solves of a step over the streams
+SOLVE_COST = {"cbl": 3.3, "gbl": 1.0, "sbl": 1.0, "cheb": 0.65, "cheb2": 0.74}
+
+
+def assign_streams(solves, nstreams, policy):
+    """Stream index per solve, and the launch order.  'lpt': solves sorted by decreasing
+    cost, each onto the stream with the least cost so far; 'rr': solve i onto stream
+    i mod nstreams in the given order."""
+    if policy == "rr" or nstreams <= 1:
+        return [i % nstreams for i in range(len(solves))], list(range(len(solves)))
+    order = sorted(range(len(solves)), key=lambda i: -SOLVE_COST.get(solves[i][0], 1.0))
+    load = [0.0] * nstreams
+    where = [0] * len(solves)
+    for i in order:
+        j = min(range(nstreams), key=lambda q: (load[q], q))
+        where[i] = j
+        load[j] += SOLVE_COST.get(solves[i][0], 1.0)
+    return where, order
 
 
 # ----------------------------------------------------------------------------- small config
@@ -403,14 +427,17 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     params = {t: kb.make_params(t=t, basis=a.basis, no_frontier=int(a.no_frontier)) for t in ts}
 
+    where, order = assign_streams(solves, len(streams), a.schedule)
+
     def step(pr=params):
-        # independent solves round-robin over the streams; every stream joins the main one
+        # independent solves spread over the streams; every stream joins the main one
         ev = torch.cuda.Event()
         ev.record(stream)
         for s2 in streams[1:]:
             s2.wait_event(ev)
-        for i, ((mth, t), Y) in enumerate(zip(solves, Ys)):
-            kb.kb_krylov_apply(G, mth, "exp", pr[t], nodes, a.M, a.m, Y, stream=streams[i % len(streams)])
+        for i in order:
+            mth, t = solves[i]
+            kb.kb_krylov_apply(G, mth, "exp", pr[t], nodes, a.M, a.m, Ys[i], stream=streams[where[i]])
         for s2 in streams[1:]:
             e2 = torch.cuda.Event()
             e2.record(s2)
@@ -501,7 +528,7 @@ def main():
         pool = ThreadPoolExecutor(max_workers=len(streams))
 
         def run_share(j):
-            for i in range(j, len(solves), len(streams)):
+            for i in (q for q in order if where[q] == j):
                 mth, t = solves[i]
                 kb.kb_krylov_apply_host(G, mth, "exp", params[t], nodes, a.M, a.m, Yh[i],
                                         stream=streams[j])

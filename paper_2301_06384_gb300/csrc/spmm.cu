@@ -89,12 +89,30 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Four consecutive coefficients from shared memory in one 16-byte (FP32) or two 16-byte
+// (FP64) loads; c is a multiple of 4 and the arrays are 16-byte aligned.
+template <typename C>
+__device__ __forceinline__ void lds4(const C *p, C (&v)[4]) {
+    if constexpr (sizeof(C) == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0];
+        const double2 b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+}
+
+#ifndef KB_SPMM_OCC
+#define KB_SPMM_OCC 5   // FP32 / BF16 kernel without column dots
+#endif
 template <typename T, bool DOT>
 struct SpmmOcc {
-    static constexpr int value = sizeof(typename Cmp<T>::type) == 8 ? 3 : (DOT ? 4 : 5);
+    static constexpr int value = sizeof(typename Cmp<T>::type) == 8 ? 3 : (DOT ? 4 : KB_SPMM_OCC);
 };
 
-template <typename T, int W, bool DOT>
+// WGT: the graph stores edge weights (false: unit weights, w_ij = 1)
+template <typename T, int W, bool DOT, bool WGT>
 __global__ void __launch_bounds__(SPMM_THREADS, (SpmmOcc<T, DOT>::value))
 k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
     using G = SpmmGeo<W>;
@@ -107,9 +125,12 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
     __shared__ __align__(16) C s_coef[5][W];       // c1 hi, c1 lo, c0, c2 hi, c2 lo
     __shared__ C s_sc[2];                          // s3, wE in the arithmetic type
     __shared__ double s_dot[WARPS][W];
+    __shared__ unsigned long long s_cnt[2];       // rows, stored nonzeros processed
     if (threadIdx.x == 0) {
         s_sc[0] = C(e.s3);
         s_sc[1] = C(e.wE);
+        s_cnt[0] = 0ull;
+        s_cnt[1] = 0ull;
     }
     for (int c = threadIdx.x; c < W; c += blockDim.x) {
         const double d1 = e.a1 ? e.a1[c] : e.s1;
@@ -136,7 +157,6 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) dot[v][q] = C(0);
     const int64_t ntiles = (g.n + TR - 1) / TR;
-    unsigned long long my_rows = 0, my_nnz = 0;
 
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t r0 = tile * TR;
@@ -174,11 +194,11 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
         const int base = s_rp[0];
         const int cnt = s_rp[rows] - base;
         const bool staged = cnt <= CAP;
-        if (threadIdx.x == 0) { my_rows += rows; my_nnz += cnt; }
+        if (threadIdx.x == 0) { s_cnt[0] += unsigned(rows); s_cnt[1] += unsigned(cnt); }
         if (staged) {
             for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
                 s_col[i] = __ldg(g.col + base + i);
-                if (g.w) s_w[i] = __ldg(g.w + base + i);
+                if (WGT) s_w[i] = __ldg(g.w + base + i);
             }
         }
         __syncthreads();
@@ -204,7 +224,7 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                 for (int u = 0; u < U; ++u) {
                     if (p + u < end) {
                         const int j = staged ? s_col[p + u] : __ldg(g.col + base + p + u);
-                        wv[u] = g.w ? C(staged ? s_w[p + u] : __ldg(g.w + base + p + u)) : C(1);
+                        wv[u] = WGT ? C(staged ? s_w[p + u] : __ldg(g.w + base + p + u)) : C(1);
 #pragma unroll
                         for (int v = 0; v < VPL; ++v) xj[u][v] = V4<T>::load(x + int64_t(j) * W + KB_COL(v));
                     }
@@ -216,31 +236,40 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                         for (int v = 0; v < VPL; ++v)
 #pragma unroll
                             for (int q = 0; q < 4; ++q)
-                                acc[v][q] = fma(wv[u], xi[v].v[q] - xj[u][v].v[q], acc[v][q]);
+                                acc[v][q] = WGT ? fma(wv[u], xi[v].v[q] - xj[u][v].v[q], acc[v][q])
+                                                : acc[v][q] + (xi[v].v[q] - xj[u][v].v[q]);
             }
             const C r = g.rdiag ? C(__ldg(g.rdiag + row)) : C(0);
             const int mk = e.marker ? __ldg(e.marker + row) : -1;
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
                 const int c = KB_COL(v);
-                C o[4];
+                C o[4], k1h[4], k1l[4], k0[4];
+                lds4(&s_coef[0][c], k1h);
+                lds4(&s_coef[1][c], k1l);
+                lds4(&s_coef[2][c], k0);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const C a = fma(r, xi[v].v[q], acc[v][q]);
-                    o[q] = fma(s_coef[0][c + q], a, fma(s_coef[1][c + q], a, s_coef[2][c + q] * xi[v].v[q]));
+                    o[q] = fma(k1h[q], a, fma(k1l[q], a, k0[q] * xi[v].v[q]));
                 }
                 if (e.y) {
                     const V4<T> yi = V4<T>::load(e.y + row * W + c);
+                    C k2h[4], k2l[4];
+                    lds4(&s_coef[3][c], k2h);
+                    lds4(&s_coef[4][c], k2l);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        o[q] = fma(s_coef[3][c + q], yi.v[q], fma(s_coef[4][c + q], yi.v[q], o[q]));
+                    for (int q = 0; q < 4; ++q) o[q] = fma(k2h[q], yi.v[q], fma(k2l[q], yi.v[q], o[q]));
                 }
                 if (e.z) {
                     const V4<T> zi = V4<T>::load(e.z + row * W + c);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) o[q] = fma(s_sc[0], zi.v[q], o[q]);
                 }
-                if (mk >= c && mk < c + 4) o[mk - c] += s_sc[1];
+                // (constant indices: a computed index would put o in local memory)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (mk == c + q) o[q] += s_sc[1];
                 if (!e.yout) {
                     // narrowed blocks: the dot below is that of the stored values
                     if constexpr (!std::is_same<T, C>::value) {
@@ -264,8 +293,8 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
         }
     }
     if (threadIdx.x == 0 && e.prof.rows) {
-        atomicAdd(e.prof.rows, my_rows);
-        atomicAdd(e.prof.nnz, my_nnz);
+        atomicAdd(e.prof.rows, s_cnt[0]);
+        atomicAdd(e.prof.nnz, s_cnt[1]);
     }
     if constexpr (DOT && std::is_same<C, float>::value) {
         // double-float combination on the FP32 pipe; partials written as DF pairs
@@ -312,10 +341,11 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
 
 template <typename T, int W, bool DOT>
 int occupancy_spmm() {
+    // the weighted and unweighted kernels share the launch bounds
     static int per_sm = -1;
     if (per_sm < 0) {
         int v = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmm<T, W, DOT>, SPMM_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmm<T, W, DOT, true>, SPMM_THREADS, 0);
         per_sm = v < 1 ? 1 : v;
     }
     return per_sm;
@@ -328,7 +358,8 @@ int launch_wd(const GraphDev &g, const T *x, const LinEpi<T> &e, int64_t ldo, in
     int grid = int(std::min<int64_t>(ntiles, int64_t(num_sms()) * occupancy_spmm<T, W, DOT>()));
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = grid;
-    k_spmm<T, W, DOT><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
+    if (g.w) k_spmm<T, W, DOT, true><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
+    else k_spmm<T, W, DOT, false><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
     return 0;
 }
 

@@ -58,3 +58,22 @@ def test_reference_arm_only_runs_on_rank_zero(capsys):
         pass
     bench.run_reference(A(), 1, 2)                # rank 1: returns without work or output
     assert capsys.readouterr().out == ""
+
+
+def test_stream_assignment_balances_the_solves():
+    import bench
+    solves = [(m, t) for m in ["cbl", "gbl", "sbl", "cheb", "cheb2"] for t in (0.5, 2.0)]
+    where, order = bench.assign_streams(solves, 5, "lpt")
+    assert sorted(order) == list(range(len(solves)))
+    load = [0.0] * 5
+    for i, j in enumerate(where):
+        load[j] += bench.SOLVE_COST[solves[i][0]]
+    # the two long solves get a stream each; no stream carries more than the longest solve
+    assert where[0] != where[1]
+    assert max(load) <= bench.SOLVE_COST["cbl"] + 1e-9
+    # round robin keeps the given order
+    rr, rorder = bench.assign_streams(solves, 5, "rr")
+    assert rr == [i % 5 for i in range(10)] and rorder == list(range(10))
+    # one stream: everything in order on stream 0
+    one, _ = bench.assign_streams(solves, 1, "lpt")
+    assert one == [0] * 10
