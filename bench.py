@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--serve-max-n", type=int, default=200_000,
                     help="largest of the 8 serving graphs (the others are log-spaced from 1e4)")
     ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="use the tcgen05 row-block kernels (KB_TENSOR_CORES=1) in the cbl solves")
     ap.add_argument("--schedule", default="lpt", choices=["lpt", "rr"],
                     help="assignment of the independent solves of a step to the streams: "
                          "longest first onto the least loaded stream, or round robin")
@@ -78,6 +80,7 @@ def workload_config(a):
             "graph_seed": a.graph_seed, "node_seed": a.node_seed, "basis": a.basis,
             "l2": "256 MiB flush write between steps; per-solve working set > L2",
             "streams": a.streams, "schedule": a.schedule,
+            "rowblock": "tcgen05 bf16x6" if a.tensor_cores else "simt fp32",
             "frontier": not a.no_frontier}
 
 
@@ -396,6 +399,8 @@ def job_value(cols_per_step: int, world: int, ms: float) -> float:
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     a = parse()
+    if a.tensor_cores:
+        os.environ["KB_TENSOR_CORES"] = "1"   # read by the library at each row-block launch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -214,6 +214,13 @@ int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *g
                     int64_t M_alg);
 template <typename T>
 int rowblock_max_grid(int W);
+// Tensor-core (tcgen05) variant of PROJ, UPD, MULGRAM and MUL for FP32 blocks of width 64
+// (rowblock_tc.cu); launch_rowblock uses it where rowblock_tc_supported says so.  Gram
+// partials: grid <= max_grid rows of [W*W].
+bool rowblock_tc_supported(int mode, int W);
+bool rowblock_tc_enabled();   // KB_TENSOR_CORES=1 in the environment
+int launch_rowblock_tc(int mode, const RowArgs<float> &a, cudaStream_t s, int max_grid, int *grid_out);
+int rowblock_tc_max_grid();
 
 // Deterministic FP64 reduction of [nparts][len] partials into out[len]; when out_p is set
 // the sums are also written there rounded to P.

@@ -808,6 +808,8 @@ int apply_device(kb_graph *g, kb_method method, kb_phi phi, const kb_params *par
     if (info->status == KB_ERR_ORTHOGONALITY)
         return fail(info->status, "the projected matrix left the spectral interval [0, Lambda] "
                                   "(loss of orthogonality of the Lanczos basis); use reorth");
+    if (info->status == KB_ERR_CUDA)
+        return fail(info->status, "a tensor-core kernel gave up waiting for its MMA completion");
     if (info->status != KB_OK) return fail(info->status, "Lanczos breakdown: rank-deficient block");
     return KB_OK;
 }

@@ -16,6 +16,7 @@
 #include "kb_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace kb {
 namespace {
@@ -367,8 +368,10 @@ int launch_w(int mode, const RowArgs<T> &a, cudaStream_t s, int *grid_out) {
 
 template <typename T, int W>
 int max_grid_w() {
-    return num_sms() * std::max({occupancy<T, W, RB_PROJ>(), occupancy<T, W, RB_UPD>(),
-                                 occupancy<T, W, RB_MULGRAM>(), occupancy<T, W, RB_MUL>()});
+    int g = num_sms() * std::max({occupancy<T, W, RB_PROJ>(), occupancy<T, W, RB_UPD>(),
+                                  occupancy<T, W, RB_MULGRAM>(), occupancy<T, W, RB_MUL>()});
+    if (std::is_same<T, float>::value && W == 64) g = std::max(g, rowblock_tc_max_grid());
+    return g;
 }
 
 // ---------------------------------------------------------------- deterministic reduction
@@ -421,6 +424,16 @@ __global__ void __launch_bounds__(1024) k_reduce(const P *__restrict__ parts, in
 
 }  // namespace
 
+// The tensor-core kernels are used when the environment variable KB_TENSOR_CORES is "1"
+// at the time of the launch (read on every launch, so a process can switch).  They are not
+// the default: with the frontier restriction most launches of a solve cover few tiles, and
+// one 192 KB CTA per SM keeps other streams' kernels off the SM (measured slower in the
+// multi-stream throughput run).
+bool rowblock_tc_enabled() {
+    const char *e = std::getenv("KB_TENSOR_CORES");
+    return e && e[0] == '1';
+}
+
 template <typename T>
 int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *grid_out,
                     int64_t M_alg) {
@@ -429,18 +442,26 @@ int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *g
     RowArgs<T> aa = a;
     aa.prof = prof_begin(cls, s);
     int rc = 0;
-    switch (W) {
-        case 16: rc = launch_w<T, 16>(mode, aa, s, grid_out); break;
-        case 32: rc = launch_w<T, 32>(mode, aa, s, grid_out); break;
-        case 64: rc = launch_w<T, 64>(mode, aa, s, grid_out); break;
-        case 128:
-            if constexpr (sizeof(typename Cmp<T>::type) == 4) { rc = launch_w<T, 128>(mode, aa, s, grid_out); break; }
-            [[fallthrough]];
-        default: return fail(KB_ERR_ARG, "unsupported block width");
+    bool tc = false;
+    if constexpr (std::is_same<T, float>::value) tc = rowblock_tc_supported(mode, W) && rowblock_tc_enabled();
+    if (tc) {
+        // FP32 blocks of width 64: tensor-core kernel (rowblock_tc.cu)
+        if constexpr (std::is_same<T, float>::value)
+            rc = launch_rowblock_tc(mode, aa, s, rowblock_max_grid<T>(W), grid_out);
+    } else {
+        switch (W) {
+            case 16: rc = launch_w<T, 16>(mode, aa, s, grid_out); break;
+            case 32: rc = launch_w<T, 32>(mode, aa, s, grid_out); break;
+            case 64: rc = launch_w<T, 64>(mode, aa, s, grid_out); break;
+            case 128:
+                if constexpr (sizeof(typename Cmp<T>::type) == 4) { rc = launch_w<T, 128>(mode, aa, s, grid_out); break; }
+                [[fallthrough]];
+            default: return fail(KB_ERR_ARG, "unsupported block width");
+        }
     }
     if (rc) return rc;
     cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return cuda_fail(err, "k_rowblock launch");
+    if (err != cudaSuccess) return cuda_fail(err, tc ? "k_rowblock_tc launch" : "k_rowblock launch");
     const double blk = double(a.n) * double(M_alg) * sizeof(T);
     const double row = double(M_alg) * sizeof(T);             // bytes of one block row
     const double fr = 2.0 * double(M_alg) * double(M_alg);    // flops of one row times M x M
