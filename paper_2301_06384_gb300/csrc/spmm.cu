@@ -179,7 +179,10 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
         {
             const char *xb = reinterpret_cast<const char *>(x + r0 * W);
             const int64_t tile_bytes = int64_t(rows) * W * int64_t(sizeof(T));
+            constexpr int64_t row_bytes = int64_t(W) * int64_t(sizeof(T));
             for (int64_t off = int64_t(threadIdx.x) * 128; off < tile_bytes; off += int64_t(blockDim.x) * 128) {
+                // rows of 32-row frontier tiles beyond the limit are skipped below: no prefetch
+                if (e.tgen && __ldg(e.tgen + (r0 + off / row_bytes) / ACT_ROWS) > e.limit) continue;
                 prefetch_l2(xb + off);
                 if (e.y) prefetch_l2(reinterpret_cast<const char *>(e.y + r0 * W) + off);
                 if (e.z) prefetch_l2(reinterpret_cast<const char *>(e.z + r0 * W) + off);
@@ -194,7 +197,6 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
         const int base = s_rp[0];
         const int cnt = s_rp[rows] - base;
         const bool staged = cnt <= CAP;
-        if (threadIdx.x == 0) { s_cnt[0] += unsigned(rows); s_cnt[1] += unsigned(cnt); }
         if (staged) {
             for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
                 s_col[i] = __ldg(g.col + base + i);
@@ -204,7 +206,33 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
         __syncthreads();
 #pragma unroll 1
         for (int rr = 0; rr < RPG; ++rr) {
-            const int lrow = rr * NG + gid;
+            // rows rr*NG .. rr*NG+NG-1 of the tile (one lane group each); with the frontier
+            // restriction a chunk whose 32-row frontier tiles are all beyond the limit is
+            // exactly zero and skipped (CTA-uniform)
+            const int c0r = rr * NG;
+            if (c0r >= rows) break;
+            const int crows = rows - c0r < NG ? rows - c0r : NG;
+            const int lrow = c0r + gid;
+            if (e.tgen && tile_min_gen(e.tgen, r0 + c0r, crows) > e.limit) {
+                if (e.zero_inactive && lrow < rows) {
+#pragma unroll
+                    for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int c = KB_COL(v) + q;
+                            if (e.yout) {
+                                if (c < mo) e.yout[(r0 + lrow) * ldo + c] = 0.f;
+                            } else {
+                                e.out[(r0 + lrow) * W + c] = T(0.f);
+                            }
+                        }
+                }
+                continue;
+            }
+            if (threadIdx.x == 0) {
+                s_cnt[0] += unsigned(crows);
+                s_cnt[1] += unsigned(s_rp[c0r + crows] - s_rp[c0r]);
+            }
             if (lrow >= rows) continue;
             const int64_t row = r0 + lrow;
             const int beg = s_rp[lrow] - base;
