@@ -160,6 +160,8 @@ struct LinEpi {
                                       // the arithmetic is FP32, doubles for FP64)
     const Ctrl *ctrl = nullptr;
     const int32_t *tgen = nullptr;    // frontier tiles (nullptr: all rows)
+    const uint8_t *gen = nullptr;     // hop distance per row (with tgen): a warp whose rows
+                                      // all lie beyond the limit skips them
     int limit = 0;                    // process tiles with tgen <= limit
     int zero_inactive = 0;            // write zeros for skipped tiles (final output)
     ProfCount prof;

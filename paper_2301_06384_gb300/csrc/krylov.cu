@@ -239,6 +239,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             e.out = b.wbuf;
             e.ctrl = b.ctrl;
             e.tgen = tg;
+            e.gen = tg ? b.gen : nullptr;
             e.limit = k;
             KB_TRY(launch_spmm<T>(c.g->dev, W, Qk, e, c.s, nullptr, M, 0));
             ++c.spmm;
@@ -360,6 +361,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                 e.out = b.wbuf;
                 e.ctrl = b.ctrl2;
                 e.tgen = tg;
+                e.gen = tg ? b.gen : nullptr;
                 e.limit = k;
                 KB_TRY(launch_spmm<T>(c.g->dev, W, Qk, e, c.s, nullptr, M, 0));
                 ++c.spmm;
@@ -474,6 +476,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
             // X = L Q_k - h_{k,k-1} Q_{k-1}, with Q_k = sigma_k P_k; dots <P_k, X> per column
             LinEpi<T> e;
             e.tgen = tg;
+            e.gen = tg ? b.gen : nullptr;
             e.limit = k;
             e.a1 = b.c1 + int64_t(k - 1) * W;
             e.a2 = b.c2 + int64_t(k - 1) * W;
@@ -515,6 +518,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
                 if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
                 LinEpi<T> e;
                 e.tgen = tg;
+                e.gen = tg ? b.gen : nullptr;
                 e.limit = k;
                 e.a1 = b.c1 + int64_t(k - 1) * W;
                 e.a2 = b.c2 + int64_t(k - 1) * W;
@@ -575,6 +579,7 @@ int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int
         if (tgen) KB_TRY(launch_frontier_expand(c.g->dev, gen, tgen, hop, c.s));
         LinEpi<T> e;
         e.tgen = tgen;
+        e.gen = tgen ? gen : nullptr;
         e.limit = hop;
         e.zero_inactive = last ? 1 : 0;
         e.s1 = (last ? -2.0 : -4.0) / lam;

@@ -213,7 +213,21 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
             if (c0r >= rows) break;
             const int crows = rows - c0r < NG ? rows - c0r : NG;
             const int lrow = c0r + gid;
-            if (e.tgen && tile_min_gen(e.tgen, r0 + c0r, crows) > e.limit) {
+            bool skip_rows = e.tgen && tile_min_gen(e.tgen, r0 + c0r, crows) > e.limit;
+            if (!skip_rows && e.gen) {
+                // this warp's RPW rows of the chunk: skipped (warp-uniform) when every one
+                // of them lies beyond the limit (the rr loop has no barrier)
+                const int wr0 = c0r + warp * RPW;
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < RPW; ++q)
+                    if (wr0 + q < rows && int(__ldg(e.gen + r0 + wr0 + q)) <= e.limit) any = true;
+                skip_rows = !any;
+            } else if (!skip_rows && threadIdx.x == 0) {
+                s_cnt[0] += unsigned(crows);
+                s_cnt[1] += unsigned(s_rp[c0r + crows] - s_rp[c0r]);
+            }
+            if (skip_rows) {
                 if (e.zero_inactive && lrow < rows) {
 #pragma unroll
                     for (int v = 0; v < VPL; ++v)
@@ -229,9 +243,14 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                 }
                 continue;
             }
-            if (threadIdx.x == 0) {
-                s_cnt[0] += unsigned(crows);
-                s_cnt[1] += unsigned(s_rp[c0r + crows] - s_rp[c0r]);
+            if (e.gen && lane == 0) {
+                // rows and stored nonzeros this warp processes
+                const int wr0 = c0r + warp * RPW;
+                const int wr1 = wr0 + RPW < rows ? wr0 + RPW : rows;
+                if (wr1 > wr0) {
+                    atomicAdd(&s_cnt[0], (unsigned long long)(wr1 - wr0));
+                    atomicAdd(&s_cnt[1], (unsigned long long)(s_rp[wr1] - s_rp[wr0]));
+                }
             }
             if (lrow >= rows) continue;
             const int64_t row = r0 + lrow;
