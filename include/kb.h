@@ -309,6 +309,13 @@ typedef struct {
     int32_t streams;         /* concurrent solves, 1..64                                          */
     int32_t queue_capacity;  /* maximum requests submitted and not yet polled as finished         */
     int64_t memory_budget;   /* bytes of scratch the running requests may hold together          */
+    int32_t fallback_sbl;    /* 1: a KB_CBL or KB_GBL request whose block becomes rank deficient
+                                (KB_ERR_BREAKDOWN, e.g. nodes whose neighbourhoods are tiny
+                                components) is run again as KB_SBL, one Lanczos process per
+                                column, which has no block rank deficiency (reorth off; only
+                                when its scratch fits the request's admission); poll then reports
+                                the KB_SBL status, with info->breakdown_step set to the step of
+                                the block breakdown.  0: the breakdown is reported.            */
 } kb_server_config;
 int kb_server_create(int32_t device, const kb_server_config *cfg, kb_server **out);
 int kb_server_submit(kb_server *sv, kb_graph *g, kb_method method, kb_phi phi,

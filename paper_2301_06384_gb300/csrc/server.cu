@@ -46,6 +46,7 @@ struct kb_server {
     size_t budget = 0;
     size_t in_use = 0;
     int32_t capacity = 0;
+    int32_t fallback_sbl = 0;
     bool stopping = false;
     int64_t next_ticket = 1;
     std::mutex mu;
@@ -82,9 +83,24 @@ void worker_loop(kb_server *sv, int w) {
         const int32_t M = int32_t(r.nodes.size());
         const int32_t m = r.m;
         float *Y = r.Y;
+        const uint64_t r_bytes = r.bytes;
         lk.unlock();
         kb_info info{};
-        const int rc = kb_krylov_apply(g, method, phi, &params, nodes, M, m, Y, sv->streams[w], &info);
+        int rc = kb_krylov_apply(g, method, phi, &params, nodes, M, m, Y, sv->streams[w], &info);
+        if (rc == KB_ERR_BREAKDOWN && sv->fallback_sbl && (method == KB_CBL || method == KB_GBL)) {
+            // rank-deficient block: one Lanczos process per column instead, when its scratch
+            // fits what the request was admitted with
+            kb_params p2 = params;
+            p2.reorth = 0;
+            uint64_t need = 0;
+            if (kb_workspace_bytes(g, KB_SBL, phi, &p2, M, m, &need) == KB_OK && need <= r_bytes) {
+                const int32_t bstep = info.breakdown_step;
+                kb_info info2{};
+                rc = kb_krylov_apply(g, KB_SBL, phi, &p2, nodes, M, m, Y, sv->streams[w], &info2);
+                info = info2;
+                info.breakdown_step = bstep;
+            }
+        }
         std::string msg = rc ? std::string(kb_last_error()) : std::string();
         const Clock::time_point t = Clock::now();
         lk.lock();
@@ -122,6 +138,7 @@ extern "C" int kb_server_create(int32_t device, const kb_server_config *cfg, kb_
         sv->device = device;
         sv->budget = budget;
         sv->capacity = cfg->queue_capacity;
+        sv->fallback_sbl = cfg->fallback_sbl ? 1 : 0;
         for (int i = 0; i < cfg->streams; ++i) {
             cudaStream_t s = nullptr;
             cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);

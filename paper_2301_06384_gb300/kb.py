@@ -48,7 +48,7 @@ class kb_info(ctypes.Structure):
 
 class kb_server_config(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_int32), ("queue_capacity", ctypes.c_int32),
-                ("memory_budget", ctypes.c_int64)]
+                ("memory_budget", ctypes.c_int64), ("fallback_sbl", ctypes.c_int32)]
 
 
 class kb_kernel_stats(ctypes.Structure):
@@ -316,8 +316,9 @@ class Server:
     """Request queue over kb_krylov_apply (kb_server_create / submit / poll / destroy)."""
 
     def __init__(self, streams: int = 4, queue_capacity: int = 4096, memory_budget: int = 0,
-                 device: int = 0):
-        cfg = kb_server_config(int(streams), int(queue_capacity), int(memory_budget))
+                 device: int = 0, fallback_sbl: bool = False):
+        cfg = kb_server_config(int(streams), int(queue_capacity), int(memory_budget),
+                               int(bool(fallback_sbl)))
         h = ctypes.c_void_p()
         _check(lib().kb_server_create(int(device), ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h

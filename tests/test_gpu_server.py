@@ -138,3 +138,26 @@ def test_workspace_bytes_matches_layout(kb, graphs):
     assert abs((c20 - c10) - 10 * g.n * 64 * 4) < 0.05 * (c20 - c10)
     with pytest.raises(kb.KbError):
         kb.kb_workspace_bytes(G, "cbl", "spline", kb.make_params(eps=0.1, s=1.5), 4, 5)
+
+
+def test_server_falls_back_to_sbl_on_block_breakdown(kb):
+    # path 0-1-2 with W = {0, 2}: the classical block process meets a rank-one block; with
+    # fallback_sbl the server reruns the request as one Lanczos process per column and the
+    # result equals the direct sbl call bit for bit
+    import torch
+    g = synth.path_graph(3)
+    with kb.Graph.from_csr(g) as G:
+        Y = torch.empty((3, 2), dtype=torch.float32, device="cuda")
+        p = kb.make_params(t=1.0)
+        with kb.Server(streams=1, queue_capacity=4) as sv:
+            t = sv.submit(G, "cbl", "exp", p, np.array([0, 2]), 3, Y)
+            with pytest.raises(kb.KbError) as ei:
+                sv.poll(t, wait_ms=-1)
+            assert ei.value.code == -6
+        with kb.Server(streams=1, queue_capacity=4, fallback_sbl=True) as sv:
+            t = sv.submit(G, "cbl", "exp", p, np.array([0, 2]), 3, Y)
+            info, _ = sv.poll(t, wait_ms=-1)
+        assert info["status"] == 0 and info["breakdown_step"] >= 0
+        Yd = kb.kernel_columns(G, "sbl", "exp", [0, 2], 3, t=1.0)
+        torch.cuda.synchronize()
+        assert torch.equal(Y, Yd)
