@@ -136,6 +136,9 @@ def small_config(kb, torch):
 
 
 # ----------------------------------------------------------------------------- serving
+M_MAX = 100   # serving: largest number of cbl steps (the stopping rule ends most requests earlier)
+
+
 def serving_sample(a, kb, torch):
     """Latency of kernel-column requests through the serving front end (kb_server_*).
 
@@ -160,12 +163,13 @@ def serving_sample(a, kb, torch):
         k = int(rng.integers(0, K))
         M = int(rng.integers(1, 129))
         # local reorthogonalisation keeps the FP32 basis usable on the hub-heavy graphs
+        # cbl with the stopping rule tol = 1e-6, at most 100 steps
         if rng.random() < 0.5:
-            p = kb.make_params(t=float(rng.uniform(0.1, 5.0)), reorth=2)
+            p = kb.make_params(t=float(rng.uniform(0.1, 5.0)), reorth=2, tol=1e-6)
             phi = "exp"
         else:
             p = kb.make_params(eps=float(10 ** rng.uniform(-3, -1)), s=float(rng.integers(1, 3)),
-                               reorth=2)
+                               reorth=2, tol=1e-6)
             phi = "spline"
         nodes = synth.sample_nodes(ns[k], M, seed=1000 + i)
         reqs.append((k, phi, p, nodes))
@@ -174,6 +178,7 @@ def serving_sample(a, kb, torch):
 
     failed = [0]
     retried = [0]
+    steps = []
 
     def finish(sv, tk, lat):
         # a request whose block Lanczos process meets a rank-deficient block (a node set
@@ -182,6 +187,7 @@ def serving_sample(a, kb, torch):
         try:
             info, ms = sv.poll(tk, wait_ms=-1)
             lat.append(ms)
+            steps.append(info["steps_done"])
             if info["breakdown_step"] >= 0:
                 retried[0] += 1
         except kb.KbError:
@@ -204,7 +210,7 @@ def serving_sample(a, kb, torch):
                     free.append(sl)
                 sl = free.pop()
                 Y = slots[sl][: ns[k] * nodes.size].view(ns[k], nodes.size)
-                outstanding.append((sv.submit(Gs[k], "cbl", phi, p, nodes, 30, Y), sl))
+                outstanding.append((sv.submit(Gs[k], "cbl", phi, p, nodes, M_MAX, Y), sl))
             for tk, sl in outstanding:
                 finish(sv, tk, lat)
             wall = time.perf_counter() - t0
@@ -213,10 +219,12 @@ def serving_sample(a, kb, torch):
     run(None)                                  # warm-up (pool growth, lazy module loads)
     failed[0] = 0
     retried[0] = 0
+    steps.clear()
     _, wall = run(None)
     failed_sat = failed[0]
     failed[0] = 0
     retried[0] = 0
+    steps.clear()
     sat = R / wall
     rate = 0.8 * sat
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=R))
@@ -227,12 +235,14 @@ def serving_sample(a, kb, torch):
     alone = []
     with kb.Server(streams=a.serve_streams, queue_capacity=4) as sv:
         for _ in range(5):
-            tk = sv.submit(Gs[kmid], "cbl", "exp", kb.make_params(t=1.0), ref_nodes, 30, Yref)
+            tk = sv.submit(Gs[kmid], "cbl", "exp", kb.make_params(t=1.0, tol=1e-6), ref_nodes, M_MAX, Yref)
             alone.append(sv.poll(tk, wait_ms=-1)[1])
     for G in Gs:
         G.destroy()
     q = np.percentile(np.array(lat), [50, 99])
-    return {"requests": R, "graph_n": ns, "streams": a.serve_streams, "method": "cbl reorth=2", "m": 30,
+    return {"requests": R, "graph_n": ns, "streams": a.serve_streams,
+            "method": "cbl reorth=2, stopping rule tol=1e-6", "m_max": M_MAX,
+            "steps_done_mean": round(float(np.mean(steps)), 1) if steps else None,
             "mix": "M~U{1..128}; exp t~U[0.1,5] | spline eps~logU[1e-3,1e-1], s in {1,2}",
             "saturated_rps": round(sat, 2), "rate_rps": round(rate, 2),
             "p50_ms": round(float(q[0]), 3), "p99_ms": round(float(q[1]), 3),
@@ -240,7 +250,7 @@ def serving_sample(a, kb, torch):
             "failed_breakdown": failed[0], "failed_breakdown_saturated_run": failed_sat,
             "retried_as_sbl": retried[0],
             "reference_alone_ms": round(float(np.median(alone)), 3),
-            "reference": f"n={ns[kmid]} M=64 exp t=1 cbl m=30 on an idle server"}
+            "reference": f"n={ns[kmid]} M=64 exp t=1 cbl tol=1e-6 on an idle server"}
 
 
 # ----------------------------------------------------------------------------- clocks

@@ -82,6 +82,13 @@ typedef struct {
                            to Y as it is recomputed (twice the products with L, O(n W) memory
                            instead of the m n W of Table 2).  Not with reorth = 1; no effect
                            for KB_CHEB / KB_CHEB2, which never store a basis                    */
+    double tol;         /* KB_CBL only (a stopping rule for serving; the paper fixes m):
+                           0 (default) runs m steps.  > 0: m is the largest number of steps;
+                           after steps k = 8, 12, 16, 24, 32, 48, 64, 96 (those below m) the
+                           projected result U_k = phi(H_k) F_1 is formed in FP64 and the process
+                           stops at the first k with ||U_k - [U_k'; 0]||_F <= tol ||U_k||_F,
+                           k' the previous such step (info->steps_done = k; the result is then
+                           the one of the fixed-m call with m = k).  Not with two_pass        */
 } kb_params;
 
 typedef struct {
@@ -312,10 +319,10 @@ typedef struct {
     int32_t fallback_sbl;    /* 1: a KB_CBL or KB_GBL request whose block becomes rank deficient
                                 (KB_ERR_BREAKDOWN, e.g. nodes whose neighbourhoods are tiny
                                 components) is run again as KB_SBL, one Lanczos process per
-                                column, which has no block rank deficiency (reorth off; only
-                                when its scratch fits the request's admission); poll then reports
-                                the KB_SBL status, with info->breakdown_step set to the step of
-                                the block breakdown.  0: the breakdown is reported.            */
+                                column, which has no block rank deficiency (reorth off, all m
+                                steps; only when its scratch fits the request's admission); poll
+                                then reports the KB_SBL status, with info->breakdown_step set to
+                                the step of the block breakdown.  0: the breakdown is reported. */
 } kb_server_config;
 int kb_server_create(int32_t device, const kb_server_config *cfg, kb_server **out);
 int kb_server_submit(kb_server *sv, kb_graph *g, kb_method method, kb_phi phi,

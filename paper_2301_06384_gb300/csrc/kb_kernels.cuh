@@ -23,6 +23,13 @@ struct ChebCoef {
 };
 
 int launch_ctrl_init(Ctrl *c, int steps, cudaStream_t s);
+// dst = src with steps = min(src->steps, k) (the projected problem of the first k steps)
+int launch_ctrl_snapshot(Ctrl *dst, const Ctrl *src, int k, cudaStream_t s);
+// Stopping rule of the serving workload: with steps = chk->steps and p = *prev_steps,
+// stops ctrl (stop = 1, steps) when p > 0 and ||U - [Up; 0]||_F <= tol ||U||_F (U, Up:
+// (steps M) x M and (p M) x M row-major); then *prev_steps = steps.  No-op once ctrl stopped.
+int launch_conv_check(const double *U, const double *Up, int M, const Ctrl *chk, int32_t *prev_steps,
+                      double tol, Ctrl *ctrl, cudaStream_t s);
 template <typename T>
 int launch_scatter(T *block, int64_t ld, const int32_t *nodes, int M, int col0, T val, cudaStream_t s);
 int launch_marker(int32_t *marker, const int32_t *nodes, int M, cudaStream_t s);

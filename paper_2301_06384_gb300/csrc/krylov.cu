@@ -152,7 +152,9 @@ struct CblBufs {
     // Cholesky factors, and the two local reorthogonalisation coefficient blocks
     C *Cbs, *Bs, *Rs1, *Rs2, *Cloc;
     double *Gsum, *Hd, *Hs, *R1, *V0, *V1, *V2, *U;
-    Ctrl *ctrl, *ctrl2;
+    double *Uc;          // stopping rule: two U_k of the checks (alternating)
+    int32_t *chk_prev;   // steps of the previous check (0: none yet)
+    Ctrl *ctrl, *ctrl2, *ctrl_chk;
     uint8_t *gen;
     int32_t *tgen;
 };
@@ -178,8 +180,11 @@ void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_g
     b.V1 = ar.take<double>(size_t(m) * M * M);
     b.V2 = ar.take<double>(size_t(m) * M * M);
     b.U = ar.take<double>(size_t(m) * M * M);
+    b.Uc = ar.take<double>(size_t(2) * m * M * M);
+    b.chk_prev = ar.take<int32_t>(1);
     b.ctrl = ar.take<Ctrl>(1);
     b.ctrl2 = ar.take<Ctrl>(1);
+    b.ctrl_chk = ar.take<Ctrl>(1);
     b.gen = ar.take<uint8_t>(size_t(n));
     b.tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
 }
@@ -223,6 +228,8 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
         const int64_t bs = n * W;
         const size_t WW = size_t(W) * W;
         auto blk = [&](int j) { return b.basis + int64_t(two ? j % 3 : j) * bs; };
+        int nchk = 0;
+        if (c.p.tol > 0.0) KB_CUDA_TRY(cudaMemsetAsync(b.chk_prev, 0, sizeof(int32_t), c.s));
         for (int k = 1; k <= m; ++k) {
             T *Qk = blk(k - 1);
             T *Qp = k >= 2 ? blk(k - 2) : nullptr;
@@ -317,6 +324,22 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             qa.n = n; qa.x = X; qa.ca = S2; qa.out = X; qa.ctrl = b.ctrl;
             qa.tgen = tg; qa.limit = k;
             KB_TRY(launch_rowblock<T>(RB_MUL, W, qa, c.s, &grid, M));
+            // stopping rule: U_k at the check steps, compared with the previous check's
+            if (c.p.tol > 0.0 && k < m && (k == 8 || k == 12 || k == 16 || k == 24 || k == 32 ||
+                                           k == 48 || k == 64 || k == 96)) {
+                double *Ucur = b.Uc + size_t(nchk % 2) * m * M * M;
+                const double *Uprev = b.Uc + size_t((nchk + 1) % 2) * m * M * M;
+                KB_TRY(launch_ctrl_snapshot(b.ctrl_chk, b.ctrl, k, c.s));
+                if (c.phi == KB_PHI_EXP) {
+                    const std::vector<double> d = exp_series_coeffs(c.p.t, lam, 1e-17);
+                    KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam, d, b.V0, b.V1, b.V2, Ucur, b.ctrl_chk, c.s));
+                } else {
+                    KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, Ucur,
+                                            b.ctrl_chk, c.s));
+                }
+                KB_TRY(launch_conv_check(Ucur, Uprev, M, b.ctrl_chk, b.chk_prev, c.p.tol, b.ctrl, c.s));
+                ++nchk;
+            }
         }
         // projected problem: U = phi(H_m) F_1 in FP64
         if (c.phi == KB_PHI_EXP) {
@@ -722,6 +745,11 @@ int validate(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
         return fail(KB_ERR_UNSUPPORTED, "full reorthogonalisation needs the stored basis (two_pass = 0)");
     if (params->reorth && method != KB_CBL)
         return fail(KB_ERR_UNSUPPORTED, "reorthogonalisation is implemented for KB_CBL only");
+    if (!(params->tol >= 0.0) || !std::isfinite(params->tol)) return fail(KB_ERR_ARG, "tol must be finite and >= 0");
+    if (params->tol > 0.0 && method != KB_CBL)
+        return fail(KB_ERR_UNSUPPORTED, "the stopping rule (tol > 0) is implemented for KB_CBL only");
+    if (params->tol > 0.0 && params->two_pass)
+        return fail(KB_ERR_UNSUPPORTED, "the stopping rule (tol > 0) needs the stored basis (two_pass = 0)");
     const int wmax = params->basis == KB_F64 ? 64 : 128;
     if ((method == KB_CBL || method == KB_GBL) && M > wmax)
         return fail(KB_ERR_UNSUPPORTED, "block width too large for this method and dtype");

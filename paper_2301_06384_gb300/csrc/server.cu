@@ -92,6 +92,7 @@ void worker_loop(kb_server *sv, int w) {
             // fits what the request was admitted with
             kb_params p2 = params;
             p2.reorth = 0;
+            p2.tol = 0.0;   // the stopping rule is a cbl feature: sbl runs the m steps
             uint64_t need = 0;
             if (kb_workspace_bytes(g, KB_SBL, phi, &p2, M, m, &need) == KB_OK && need <= r_bytes) {
                 const int32_t bstep = info.breakdown_step;

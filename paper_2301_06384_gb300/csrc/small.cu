@@ -881,6 +881,63 @@ int launch_check_projected(const double *U, int64_t count, double bound, Ctrl *c
     return 0;
 }
 
+namespace {
+__global__ void k_ctrl_snapshot(Ctrl *dst, const Ctrl *src, int k) {
+    Ctrl c = *src;
+    c.steps = min(c.steps, k);
+    c.stop = 0;
+    *dst = c;
+}
+
+__global__ void __launch_bounds__(1024) k_conv_check(const double *U, const double *Up, int M,
+                                                     const Ctrl *chk, int32_t *prev_steps,
+                                                     double tol, Ctrl *ctrl) {
+    if (ctrl->stop) return;   // already stopped (invariant space, breakdown or converged)
+    __shared__ double sd[32], sn[32];
+    const int steps = chk->steps, ps = *prev_steps;
+    const int64_t cnt = int64_t(steps) * M * M, pcnt = int64_t(ps) * M * M;
+    double d2 = 0.0, n2 = 0.0;
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const double u = U[i];
+        const double e = u - (i < pcnt ? Up[i] : 0.0);
+        d2 = fma(e, e, d2);
+        n2 = fma(u, u, n2);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        d2 += __shfl_xor_sync(0xffffffffu, d2, off);
+        n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { sd[warp] = d2; sn[warp] = n2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double D = 0.0, N = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) { D += sd[w]; N += sn[w]; }
+        if (ps > 0 && sqrt(D) <= tol * sqrt(N)) {
+            ctrl->stop = 1;
+            ctrl->steps = steps;
+        }
+        *prev_steps = steps;
+    }
+}
+}  // namespace
+
+int launch_ctrl_snapshot(Ctrl *dst, const Ctrl *src, int k, cudaStream_t s) {
+    k_ctrl_snapshot<<<1, 1, 0, s>>>(dst, src, k);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int launch_conv_check(const double *U, const double *Up, int M, const Ctrl *chk, int32_t *prev_steps,
+                      double tol, Ctrl *ctrl, cudaStream_t s) {
+    prof_begin(KernelClass::SMALL, s);
+    k_conv_check<<<1, 1024, 0, s>>>(U, Up, M, chk, prev_steps, tol, ctrl);
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::SMALL, s, 0, 0);
+    return 0;
+}
+
 int launch_ctrl_init(Ctrl *c, int steps, cudaStream_t s) {
     k_ctrl_init<<<1, 1, 0, s>>>(c, steps);
     count_launches(1);

@@ -37,7 +37,7 @@ class kb_params(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("eps", ctypes.c_double), ("s", ctypes.c_double),
                 ("lambda_max", ctypes.c_double), ("reorth", ctypes.c_int32),
                 ("basis", ctypes.c_int32), ("no_frontier", ctypes.c_int32),
-                ("two_pass", ctypes.c_int32)]
+                ("two_pass", ctypes.c_int32), ("tol", ctypes.c_double)]
 
 
 class kb_info(ctypes.Structure):
@@ -144,10 +144,10 @@ def _ptr(a) -> int:
 
 
 def make_params(t=1.0, eps=0.01, s=1.0, lambda_max=0.0, reorth=0, basis="f32",
-                no_frontier=0, two_pass=0) -> kb_params:
+                no_frontier=0, two_pass=0, tol=0.0) -> kb_params:
     return kb_params(float(t), float(eps), float(s), float(lambda_max), int(reorth),
                      DTYPES[basis] if isinstance(basis, str) else int(basis), int(no_frontier),
-                     int(two_pass))
+                     int(two_pass), float(tol))
 
 
 class Graph:
