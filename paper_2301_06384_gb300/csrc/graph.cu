@@ -32,13 +32,13 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 int num_sms() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
+    // function-local static: computed once, thread-safe (several serving workers)
+    static const int sms = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v <= 0 ? 1 : v;
+    }();
     return sms;
 }
 

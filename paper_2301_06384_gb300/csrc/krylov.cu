@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <mutex>
 
 namespace kb {
 
@@ -100,14 +101,17 @@ struct Arena {
 };
 
 void ensure_pool(int dev) {
-    static int done_for = -1;
-    if (done_for == dev) return;
+    // once per device; callers may run on several host threads (the serving workers)
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t thr = std::numeric_limits<uint64_t>::max();
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
-    done_for = dev;
+    done.push_back(dev);
 }
 
 struct Common {

@@ -187,12 +187,10 @@ int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
     KB_CUDA_TRY(cudaMemsetAsync(U, 0, bytes, s));
     k_cheb_bt_seed<<<(M + 127) / 128, 128, 0, s>>>(V0, U, M, d[0]);
     const size_t smem = sizeof(double) * 3 * M * TC;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_cheb_bt_iter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(sizeof(double) * 3 * 128 * TC));
-        attr = true;
-    }
+    // function-local static: initialised once, thread-safe (several serving workers)
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_cheb_bt_iter, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(double) * 3 * 128 * TC));
+    (void)attr;
     double *pp = V2, *pc = V0, *pn = V1;
     const double g = 2.0 / lam;
     for (size_t j = 0; j + 1 < d.size(); ++j) {

@@ -170,12 +170,9 @@ extern "C" int kb_rls_predict(kb_graph *g, kb_method method, kb_phi phi, const k
             KB_CUDA_TRY(cudaMemcpyAsync(dn, nodes, sizeof(int32_t) * M, cudaMemcpyHostToDevice, s));
             KB_CUDA_TRY(cudaMemcpyAsync(dl, labels, sizeof(double) * M, cudaMemcpyHostToDevice, s));
             const size_t smem = sizeof(double) * (size_t(M) * (M + 1) + M);
-            static bool attr = false;
-            if (!attr) {
-                cudaFuncSetAttribute(k_rls_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(sizeof(double) * (128 * 129 + 128)));
-                attr = true;
-            }
+            static const cudaError_t attr = cudaFuncSetAttribute(
+                k_rls_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(double) * (128 * 129 + 128)));
+            (void)attr;
             prof_begin(KernelClass::SMALL, s);
             k_rls_solve<<<1, RLS_THREADS, smem, s>>>(Yw, M, dn, dl, gamma * M, dc, dst);
             KB_CUDA_TRY(cudaGetLastError());

@@ -329,15 +329,15 @@ k_rowblock(RowArgs<T> a) {
 template <typename T, int W, int MODE>
 int occupancy() {
     using G = Geo<T, W>;
-    static int cached = -1;
-    if (cached < 0) {
+    // function-local static: computed once, thread-safe (several serving workers)
+    static const int cached = [] {
         cudaFuncSetAttribute(k_rowblock<T, W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(G::smem));
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowblock<T, W, MODE>, RB_THREADS,
                                                       G::smem);
-        cached = std::max(per_sm, 1);
-    }
+        return std::max(per_sm, 1);
+    }();
     return cached;
 }
 

@@ -508,11 +508,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_rowblock_tc(RowArgs<float> a)
 
 template <int MODE>
 void tc_setup() {
-    static bool done = false;
-    if (!done) {
-        cudaFuncSetAttribute(k_rowblock_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<MODE>::SMEM);
-        done = true;
-    }
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_rowblock_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<MODE>::SMEM);
+    (void)attr;
 }
 
 template <int MODE>

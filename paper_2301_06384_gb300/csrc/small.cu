@@ -1033,13 +1033,10 @@ int launch_chol(const double *G, int M, int W, int pass, int step, double inv_th
                (newton ? (sizeof(double) + 2 * sizeof(float)) * size_t(m) * (m + 1) : 0);
     };
     const size_t smem = bytes_for(M);
-    static bool attr = false;
-    if (!attr) {
-        // FP64 blocks are at most 64 wide
-        cudaFuncSetAttribute(k_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(bytes_for(sizeof(T) == 8 ? 64 : 128)));
-        attr = true;
-    }
+    // FP64 blocks are at most 64 wide; function-local static: set once, thread-safe
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes_for(sizeof(T) == 8 ? 64 : 128)));
+    (void)attr;
     prof_begin(KernelClass::SMALL, s);
     k_chol<T><<<1, 256, smem, s>>>(G, M, W, pass, step, inv_thresh2, piv_rel2, R1, Rinv, Hs,
                                    Bout, ctrl);
@@ -1083,12 +1080,9 @@ int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const 
                        double bound, cudaStream_t s) {
     prof_begin(KernelClass::PROJECTED, s);
     const size_t smem = m <= TRI_SMEM_M ? sizeof(double) * 6 * size_t(m) : 0;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_tridiag_phi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(sizeof(double) * 6 * TRI_SMEM_M));
-        attr = true;
-    }
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_tridiag_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(double) * 6 * TRI_SMEM_M));
+    (void)attr;
     k_tridiag_phi<<<gbl ? 1 : W, TRI_THREADS, smem, s>>>(W, M, m, gbl, alpha, beta, sigma,
                                                          phi_kind, eps, s_int, lam, cc, omega,
                                                          work, ctrl, bound);

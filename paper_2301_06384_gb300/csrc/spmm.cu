@@ -389,12 +389,12 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
 template <typename T, int W, bool DOT>
 int occupancy_spmm() {
     // the weighted and unweighted kernels share the launch bounds
-    static int per_sm = -1;
-    if (per_sm < 0) {
+    // function-local static: computed once, thread-safe (several serving workers)
+    static const int per_sm = [] {
         int v = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmm<T, W, DOT, true>, SPMM_THREADS, 0);
-        per_sm = v < 1 ? 1 : v;
-    }
+        return v < 1 ? 1 : v;
+    }();
     return per_sm;
 }
 
