@@ -104,3 +104,36 @@ def test_exp_series_reproduces_exponential(kb, t, lam):
     lmb = 0.5 * lam * (1 - x)
     ref = np.exp(-t * lmb)
     assert np.max(np.abs(T @ d - ref) / np.maximum(ref, 1e-300 + np.abs(ref).max())) < 1e-14
+
+
+def test_binding_struct_layouts_match_the_header(kb, tmp_path):
+    # the ctypes mirrors of the ABI structs have the C sizes and field offsets (a plain C
+    # program compiled against include/kb.h prints them; gcc, no CUDA)
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"kb_params": kb.kb_params, "kb_info": kb.kb_info,
+               "kb_server_config": kb.kb_server_config}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "kb.h"', "int main(void) {"]
+    for sname, cls in structs.items():
+        lines.append(f'printf("{sname} size %zu\\n", sizeof({sname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{sname} {fname} %zu\\n", offsetof({sname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            sname, key, val = line.split()
+            got[(sname, key)] = int(val)
+    for sname, cls in structs.items():
+        assert got[(sname, "size")] == ctypes.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert got[(sname, fname)] == getattr(cls, fname).offset, (sname, fname)
