@@ -504,13 +504,26 @@ def main():
         # DRAM bytes per launch: the captured traffic/algorithmic ratio times this run's
         # algorithmic bytes per launch
         tr = round(ratio * s["alg_bytes"] / max(s["launches"], 1)) if ratio else None
-        return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(gbs / peak, 4), "traffic": tr,
-                "kernel": name, "launches_per_step": s["launches"] / a.steps,
-                "avg_launch_ms": s["total_ms"] / max(s["launches"], 1),
-                "share_of_step": round(s["total_ms"] / a.steps / ms, 4),
-                "peak_kind": f"{peak_kind} hbm_gbs",
-                "frac_of_nominal_7900_gbs": round(gbs / 7900.0, 4)}
+        out = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+               "frac": round(gbs / peak, 4), "traffic": tr,
+               "kernel": name, "launches_per_step": s["launches"] / a.steps,
+               "avg_launch_ms": s["total_ms"] / max(s["launches"], 1),
+               "share_of_step": round(s["total_ms"] / a.steps / ms, 4),
+               "peak_kind": f"{peak_kind} hbm_gbs",
+               "frac_of_nominal_7900_gbs": round(gbs / 7900.0, 4)}
+        if name == "rowblock" and not a.tensor_cores:
+            # the SIMT tall-skinny kernels are bound by FP32 FMA issue and shared memory,
+            # not by DRAM: roofline against the FP32 SIMT peak of the part (152 SMs x 128
+            # FMA lanes x 2 flops x the sampled SM clock), the DRAM view kept beside it
+            sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+            alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+            tfs = s["alg_flops"] / (s["total_ms"] / 1e3) / 1e12
+            out.update({"bound": "alu", "achieved": round(tfs, 2), "peak": round(alu_peak, 1),
+                        "unit": "TFLOP/s", "frac": round(tfs / alu_peak, 4),
+                        "peak_kind": f"FP32 SIMT FMA peak at {sm_mhz:.0f} MHz (unit counts x clock)",
+                        "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)})
+            out.pop("frac_of_nominal_7900_gbs", None)
+        return out
 
     dom = max(stats.items(), key=lambda kv: kv[1]["total_ms"])[0] if stats else None
     shares = {k: round(v["total_ms"] / a.steps / ms, 4) for k, v in stats.items() if v["launches"]}
@@ -541,6 +554,17 @@ def main():
                            "share_of_step": round(spmm1["total_ms"] / ms1, 4),
                            "peak_kind": f"{peak_kind} hbm_gbs (launch duration alone on the GPU)"}
     shares_one_stream = {k: round(v["total_ms"] / ms1, 4) for k, v in stats1.items() if v["launches"]}
+    rb1 = stats1.get("rowblock")
+    rowblock_one_stream = None
+    if rb1 and rb1["total_ms"] > 0 and not a.tensor_cores:
+        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        tfs1 = rb1["alg_flops"] / (rb1["total_ms"] / 1e3) / 1e12
+        rowblock_one_stream = {"bound": "alu", "achieved": round(tfs1, 2), "peak": round(alu_peak, 1),
+                               "unit": "TFLOP/s", "frac": round(tfs1 / alu_peak, 4), "kernel": "rowblock",
+                               "avg_launch_ms": rb1["total_ms"] / max(rb1["launches"], 1),
+                               "share_of_step": round(rb1["total_ms"] / ms1, 4),
+                               "peak_kind": "FP32 SIMT FMA peak (launch duration alone on the GPU)"}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed
     # region; one host thread per stream, each running its share of the solves
@@ -610,7 +634,8 @@ def main():
             "spmm_roofline": roof("spmm"),
             "kernel_shares": shares,
             "e2e": e2e, "fp64_plain": fp64, "solve_ms_one_stream": solve_ms,
-            "spmm_roofline_one_stream": spmm_one_stream, "kernel_shares_one_stream": shares_one_stream,
+            "spmm_roofline_one_stream": spmm_one_stream,
+            "rowblock_roofline_one_stream": rowblock_one_stream, "kernel_shares_one_stream": shares_one_stream,
             "serving": serving, "graph_create_ms": round(graph_create_ms, 1),
         }
         if world == 1 and not a.no_cpu_baseline:

@@ -467,13 +467,16 @@ int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *g
     const double fr = 2.0 * double(M_alg) * double(M_alg);    // flops of one row times M x M
     double bytes = 0, flops = 0, per_row = 0, per_unit = 0, frow = 0, fixed = 0;
     const double mm = double(a.n) * fr;
+    // algorithmic flops count the structure of the small matrices: a product with a
+    // triangular factor (H_{k-1,k}, R^{-1}) is half of a general one, a Gram X^T X is
+    // symmetric (half); the kernels compute more than this (full products, full Gram)
     switch (mode) {
         case RB_PROJ: bytes = 2 * blk; flops = mm; per_row = 2 * row; frow = fr; break;
         case RB_UPD:
-            bytes = (a.qa ? 4 : 3) * blk; flops = (a.qa ? 3 : 2) * mm;
-            per_row = (a.qa ? 4 : 3) * row; frow = (a.qa ? 3 : 2) * fr; break;
-        case RB_MULGRAM: bytes = 2 * blk; flops = 2 * mm; per_row = 2 * row; frow = 2 * fr; break;
-        case RB_MUL: bytes = 2 * blk; flops = mm; per_row = 2 * row; frow = fr; break;
+            bytes = (a.qa ? 4 : 3) * blk; flops = (a.qa ? 2.0 : 1.5) * mm;
+            per_row = (a.qa ? 4 : 3) * row; frow = (a.qa ? 2.0 : 1.5) * fr; break;
+        case RB_MULGRAM: bytes = 2 * blk; flops = mm; per_row = 2 * row; frow = fr; break;
+        case RB_MUL: bytes = 2 * blk; flops = 0.5 * mm; per_row = 2 * row; frow = 0.5 * fr; break;
         case RB_ASM:
             // block rows read (counted per tile and block) + the FP32 output written in full
             bytes = (a.nblk + 1) * blk; flops = a.nblk * mm;
