@@ -171,7 +171,14 @@ int kb_graph_info(const kb_graph *g, int64_t *n, int64_t *nnz_offdiag, double *l
  * Not implemented (KB_ERR_UNSUPPORTED): the Lanczos methods with KB_PHI_SPLINE and
  * non-integer s (or s > 64); reorth with methods other than KB_CBL; KB_CBL / KB_GBL with
  * M > 128 (M > 64 for KB_F64).
- * Other errors: KB_ERR_ARG, KB_ERR_NODES, KB_ERR_NOMEM, KB_ERR_CUDA.
+ * Other errors: KB_ERR_ARG, KB_ERR_NODES, KB_ERR_NOMEM, KB_ERR_CUDA (also when an opt-in
+ * tensor-core kernel gives up waiting for its MMA completion).
+ *
+ * Environment: KB_TENSOR_CORES=1 (read at every launch) runs the tall-skinny products of
+ * KB_CBL with FP32 blocks of width 64 (M in 33..64) on the tcgen05 tensor cores (BF16 x 6
+ * split products, FP32 accumulation).  It is not the default: with the frontier restriction
+ * it is slower than the SIMT kernels, and on sensitive kernels its error is several times
+ * theirs (e.g. (0.1 I + L)^{-2}: 8.6e-5 against 2.0e-5 on a 2e4-node RGG).
  */
 int kb_krylov_apply(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
                     const int32_t *nodes, int32_t M, int32_t m, float *Y, void *stream,
