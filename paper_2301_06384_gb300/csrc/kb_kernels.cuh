@@ -23,7 +23,8 @@ struct ChebCoef {
 };
 
 int launch_ctrl_init(Ctrl *c, int steps, cudaStream_t s);
-// dst = src with steps = min(src->steps, k) (the projected problem of the first k steps)
+// dst = src with steps = min(src->steps, k) (the projected problem of the first k steps),
+// or 0 once src stopped
 int launch_ctrl_snapshot(Ctrl *dst, const Ctrl *src, int k, cudaStream_t s);
 // Stopping rule of the serving workload: with steps = chk->steps and p = *prev_steps,
 // stops ctrl (stop = 1, steps) when p > 0 and ||U - [Up; 0]||_F <= tol ||U||_F (U, Up:

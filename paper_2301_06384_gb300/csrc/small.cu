@@ -884,7 +884,9 @@ int launch_check_projected(const double *U, int64_t count, double bound, Ctrl *c
 namespace {
 __global__ void k_ctrl_snapshot(Ctrl *dst, const Ctrl *src, int k) {
     Ctrl c = *src;
-    c.steps = min(c.steps, k);
+    // once the process stopped (converged, invariant space, breakdown) later checks have
+    // nothing to decide: zero steps make the projected kernels return at once
+    c.steps = src->stop ? 0 : min(c.steps, k);
     c.stop = 0;
     *dst = c;
 }
