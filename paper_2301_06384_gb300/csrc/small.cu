@@ -144,53 +144,79 @@ __device__ void tri_inv_upper_inplace(S *A, int lda, int M, S *t) {
 // and the lower part zeroed.  Square-root-free form: step j needs the pivot d_j (the
 // diagonal of the current Schur complement) and one reciprocal; the Schur complement update
 // is A_ab -= u_ja u_jb / d_j with the unscaled pivot row u_j.  The square roots and the row
-// scaling R_j = u_j / sqrt(d_j) are applied at the end, for all rows at once, which keeps
-// the serial FP64 work per column to one division.  Returns false (all threads) on a pivot
-// <= piv_rel2 * max diag.  t: shared scratch of 2 M doubles.
+// scaling R_j = u_j / sqrt(d_j) are applied at the end, for all rows at once.  Look-ahead:
+// during step j warp 0 updates only the next pivot row j+1, takes its pivot and the one
+// FP64 division and forms the scaled row u_{j+1} / d_{j+1} (into the other half of a double
+// buffer), while the other warps update rows j+2..; so each column costs one barrier and
+// the division overlaps the bulk of the update.  Returns false (all threads) on a pivot
+// <= piv_rel2 * max diag.  t: shared scratch of 3 M doubles.  Needs blockDim.x >= 64.
 __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, double maxdiag,
                                    double *t, int *bad) {
-    double *srow = t;       // u_j / d_j
-    double *piv = t + M;    // d_j
-    const int lane = threadIdx.x & 31;
+    double *srow[2] = {t, t + M};   // u_j / d_j, double-buffered by the parity of j
+    double *piv = t + 2 * M;        // d_j
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double thr = piv_rel2 * maxdiag;
+    // pivot row 0
+    if (warp == 0) {
+        const double d = A[0];
+        if (!(d > thr)) {
+            if (lane == 0) *bad = 1;
+        } else {
+            const double dinv = 1.0 / d;
+            for (int c = 1 + lane; c < M; c += 32) srow[0][c] = A[c] * dinv;
+            if (lane == 0) piv[0] = d;
+        }
+    }
+    __syncthreads();
     for (int j = 0; j < M; ++j) {
-        if (threadIdx.x < 32) {
-            const double d = A[j * lda + j];
-            if (!(d > piv_rel2 * maxdiag)) {
-                if (lane == 0) *bad = 1;
-            } else {
-                const double dinv = 1.0 / d;
-                for (int c = j + 1 + lane; c < M; c += 32) srow[c] = A[j * lda + c] * dinv;
-                if (lane == 0) piv[j] = d;
+        if (*bad) return false;
+        const double *sr = srow[j & 1];
+        if (warp == 0) {
+            if (j + 1 < M) {
+                // the next pivot row: A[j+1][c] -= u_{j,j+1} u_{j,c} / d_j, c >= j+1
+                const double ujn = A[j * lda + j + 1];
+                for (int c = j + 1 + lane; c < M; c += 32) A[(j + 1) * lda + c] -= ujn * sr[c];
+                __syncwarp();
+                const double d = A[(j + 1) * lda + j + 1];
+                if (!(d > thr)) {
+                    if (lane == 0) *bad = 1;
+                } else {
+                    const double dinv = 1.0 / d;
+                    double *sn = srow[(j + 1) & 1];
+                    for (int c = j + 2 + lane; c < M; c += 32) sn[c] = A[(j + 1) * lda + c] * dinv;
+                    if (lane == 0) piv[j + 1] = d;
+                }
+            }
+        } else {
+            // rows j+2.. of the trailing upper triangle
+            const int L = M - j - 2;
+            const int npairs = L > 0 ? L * (L + 1) / 2 : 0;
+            for (int idx = threadIdx.x - 32; idx < npairs; idx += blockDim.x - 32) {
+                // idx -> (a, b), b <= a (FP32 root estimate, corrected exactly in integers)
+                int a = int((sqrtf(8.f * float(idx) + 1.f) - 1.f) * 0.5f);
+                while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+                while (a * (a + 1) / 2 > idx) --a;
+                const int b = idx - a * (a + 1) / 2;
+                const int ra = j + 2 + b, rb = j + 2 + a;   // ra <= rb
+                A[ra * lda + rb] -= A[j * lda + ra] * sr[rb];
             }
         }
         __syncthreads();
-        if (*bad) return false;
-        const int L = M - j - 1;
-        const int npairs = L * (L + 1) / 2;
-        for (int idx = threadIdx.x; idx < npairs; idx += blockDim.x) {
-            // idx -> (a, b), b <= a, in the trailing upper triangle (FP32 root estimate,
-            // corrected exactly in integers)
-            int a = int((sqrtf(8.f * float(idx) + 1.f) - 1.f) * 0.5f);
-            while ((a + 1) * (a + 2) / 2 <= idx) ++a;
-            while (a * (a + 1) / 2 > idx) --a;
-            const int b = idx - a * (a + 1) / 2;
-            const int ra = j + 1 + b, rb = j + 1 + a;   // ra <= rb
-            A[ra * lda + rb] -= A[j * lda + ra] * srow[rb];
-        }
-        __syncthreads();
     }
+    if (*bad) return false;
     // R_jj = sqrt(d_j), R_jc = u_jc / sqrt(d_j)
+    double *rinv = srow[0];
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const double r = sqrt(piv[j]);
         piv[j] = r;
-        srow[j] = 1.0 / r;
+        rinv[j] = 1.0 / r;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
         const int i = idx / M, j = idx % M;
         if (j < i) A[i * lda + j] = 0.0;
         else if (j == i) A[i * lda + j] = piv[i];
-        else A[i * lda + j] *= srow[i];
+        else A[i * lda + j] *= rinv[i];
     }
     __syncthreads();
     return true;
@@ -220,7 +246,7 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
                                               double inv_thresh2, double piv_rel2, double *R1,
                                               T *Rinv, double *Hs, T *Bout, Ctrl *ctrl) {
     if (ctrl->stop) return;
-    // [M][M+1] FP64, then [M][M+1] T, then 2 M + 2 doubles of scratch
+    // [M][M+1] FP64, then [M][M+1] T, then 3 M + 2 doubles of scratch
     extern __shared__ __align__(16) double A[];
     __shared__ int bad, small;
     __shared__ double maxdiag;
@@ -337,7 +363,7 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
         return;
     }
     const bool newton = sizeof(T) == 4 && M <= CHOL_NEWTON_MAX;
-    double *Sd = t + 2 * M + 2;                               // [M][M+1] (newton only)
+    double *Sd = t + 3 * M + 2;                               // [M][M+1] (newton only)
     float *Rf = reinterpret_cast<float *>(Sd + M * lda);      // [M][M+1]
     float *C1 = Rf + M * lda;                                 // [M][M+1]
     for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
@@ -1031,7 +1057,7 @@ int launch_chol(const double *G, int M, int W, int pass, int step, double inv_th
     auto bytes_for = [](int m) {
         const bool newton = sizeof(T) == 4 && m <= CHOL_NEWTON_MAX;
         return sizeof(double) * size_t(m) * (m + 1) + sizeof(T) * (size_t(m) * (m + 1) + 2) +
-               sizeof(double) * size_t(2 * m + 2) +
+               sizeof(double) * size_t(3 * m + 2) +
                (newton ? (sizeof(double) + 2 * sizeof(float)) * size_t(m) * (m + 1) : 0);
     };
     const size_t smem = bytes_for(M);
