@@ -145,6 +145,10 @@ def _ptr(a) -> int:
 
 def make_params(t=1.0, eps=0.01, s=1.0, lambda_max=0.0, reorth=0, basis="f32",
                 no_frontier=0, two_pass=0, tol=0.0) -> kb_params:
+    """kb_params with the C defaults (fields as documented in include/kb.h): reorth 0/1/2
+    (none / full / local, cbl), basis "f32" / "bf16" / "f64", two_pass 1 keeps three blocks
+    and runs the recurrence twice, tol > 0 (cbl) stops at the first check step whose projected
+    result changed by at most tol (m is then the largest number of steps)."""
     return kb_params(float(t), float(eps), float(s), float(lambda_max), int(reorth),
                      DTYPES[basis] if isinstance(basis, str) else int(basis), int(no_frontier),
                      int(two_pass), float(tol))
@@ -313,7 +317,10 @@ def kb_workspace_bytes(graph: Graph, method: str, phi: str, params: kb_params, M
 
 
 class Server:
-    """Request queue over kb_krylov_apply (kb_server_create / submit / poll / destroy)."""
+    """Request queue over kb_krylov_apply (kb_server_create / submit / poll / destroy).
+
+    fallback_sbl: rerun a cbl / gbl request that ends in a rank-deficient block
+    (KB_ERR_BREAKDOWN) as sbl; its info then carries the block breakdown step."""
 
     def __init__(self, streams: int = 4, queue_capacity: int = 4096, memory_budget: int = 0,
                  device: int = 0, fallback_sbl: bool = False):
