@@ -69,6 +69,17 @@ def _subtract(X, Qk, Hkk):
     return X - Qk @ Hkk
 
 
+def _reorthogonalise(X, Q):
+    """Full reorthogonalisation (not in the paper; reading A10): classical Gram-Schmidt of
+    X against every stored block Q_1..Q_k, X = X - [Q_1..Q_k]([Q_1..Q_k]^T X), applied twice
+    (one pass leaves a component of relative size u * ||X_in|| / ||X_out|| along the basis
+    when X is nearly inside its span; the second pass removes it)."""
+    B = np.hstack(Q)
+    for _ in range(2):
+        X = X - B @ (B.T @ X)
+    return X
+
+
 def _reduced_qr(X):
     """Algorithm 1, reduced QR: X = Q_{k+1} H_{k+1,k}, H_{k+1,k} upper triangular.  The
     factor is fixed to a non-negative diagonal (the QR is unique only up to signs; A8)."""
@@ -109,9 +120,7 @@ def cbl(L: sp.csr_matrix, nodes, m: int, f, reorth: bool = False,
         if reorth == "local":
             X = X - Qk @ (Qk.T @ X) - Qprev @ (Qprev.T @ X)
         elif reorth:
-            B = np.hstack(Q)
-            for _ in range(2):
-                X = X - B @ (B.T @ X)
+            X = _reorthogonalise(X, Q)
         diag_blocks.append(Hkk)
         if k == m:
             break

@@ -150,6 +150,11 @@ __device__ void tri_inv_upper_inplace(S *A, int lda, int M, S *t) {
 // buffer), while the other warps update rows j+2..; so each column costs one barrier and
 // the division overlaps the bulk of the update.  Returns false (all threads) on a pivot
 // <= piv_rel2 * max diag.  t: shared scratch of 3 M doubles.  Needs blockDim.x >= 64.
+// bad: two shared flags, zero on entry.  The failure of pivot j is recorded in bad[j & 1]
+// (by warp 0 during step j-1) and read by every thread at the top of step j, after the
+// barrier that ends step j-1; the flag warp 0 writes during step j is the other one, so no
+// thread can read a flag in the same barrier interval in which it is written (all threads
+// leave at the same step).
 __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, double maxdiag,
                                    double *t, int *bad) {
     double *srow[2] = {t, t + M};   // u_j / d_j, double-buffered by the parity of j
@@ -160,7 +165,7 @@ __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, d
     if (warp == 0) {
         const double d = A[0];
         if (!(d > thr)) {
-            if (lane == 0) *bad = 1;
+            if (lane == 0) bad[0] = 1;
         } else {
             const double dinv = 1.0 / d;
             for (int c = 1 + lane; c < M; c += 32) srow[0][c] = A[c] * dinv;
@@ -169,7 +174,7 @@ __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, d
     }
     __syncthreads();
     for (int j = 0; j < M; ++j) {
-        if (*bad) return false;
+        if (bad[j & 1]) return false;
         const double *sr = srow[j & 1];
         if (warp == 0) {
             if (j + 1 < M) {
@@ -179,7 +184,7 @@ __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, d
                 __syncwarp();
                 const double d = A[(j + 1) * lda + j + 1];
                 if (!(d > thr)) {
-                    if (lane == 0) *bad = 1;
+                    if (lane == 0) bad[(j + 1) & 1] = 1;
                 } else {
                     const double dinv = 1.0 / d;
                     double *sn = srow[(j + 1) & 1];
@@ -203,7 +208,8 @@ __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, d
         }
         __syncthreads();
     }
-    if (*bad) return false;
+    // (no pivot is examined during the last step: the flags are final here)
+    if (bad[0] | bad[1]) return false;
     // R_jj = sqrt(d_j), R_jc = u_jc / sqrt(d_j)
     double *rinv = srow[0];
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
@@ -249,6 +255,7 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
     // [M][M+1] FP64, then [M][M+1] T, then 3 M + 2 doubles of scratch
     extern __shared__ __align__(16) double A[];
     __shared__ int bad, small;
+    __shared__ int pivot_bad[2];   // chol_upper_inplace's per-parity pivot failure flags
     __shared__ double maxdiag;
     __shared__ unsigned long long emax_bits;
     const int lda = M + 1;
@@ -258,6 +265,8 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
     if (threadIdx.x == 0) {
         emax_bits = 0ull;
         bad = 0;
+        pivot_bad[0] = 0;
+        pivot_bad[1] = 0;
     }
     __syncthreads();
     unsigned long long my_e = 0ull;
@@ -353,7 +362,7 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
         return;
     }
     // ---- general CholeskyQR pass
-    if (!chol_upper_inplace(A, lda, M, piv_rel2, maxdiag, t, &bad)) {
+    if (!chol_upper_inplace(A, lda, M, piv_rel2, maxdiag, t, pivot_bad)) {
         if (threadIdx.x == 0) {
             ctrl->status = KB_ERR_BREAKDOWN;
             ctrl->stop = 1;

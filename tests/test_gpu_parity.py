@@ -201,6 +201,32 @@ def test_breakdown_is_reported(kb):
         _oracle(g, "cbl", [0, 2], 3, "exp", t=1.0)
 
 
+@pytest.mark.parametrize("M", [4, 16, 64])
+def test_breakdown_at_a_middle_pivot(kb, M):
+    # an isolated node in the second column of the block: L e_w = 0, so column 1 of the new
+    # block X is exactly zero while the others are not; the Cholesky factorisation of X^T X
+    # meets a zero pivot at index 1 <= M - 2, found by the look-ahead warp while the other
+    # warps still update the trailing rows
+    b = synth.barabasi_albert_graph(3000, 5, seed=12)   # connected: no small components
+    rows = np.repeat(np.arange(b.n), np.diff(b.rowptr))
+    up = rows < b.col
+    n = b.n + 1                                            # node n - 1 has no edges
+    g = synth.from_edges(n, rows[up], b.col[up])
+    nodes = [int(x) for x in synth.sample_nodes(b.n, M, seed=11)]
+    nodes[1] = n - 1
+    with kb.Graph.from_csr(g) as G:
+        for _ in range(2):   # the same status twice: the context survives the breakdown
+            with pytest.raises(kb.KbError) as ei:
+                _gpu(kb, G, "cbl", "exp", nodes, 6, t=1.0)
+            assert ei.value.code == -6
+        # a node set without the isolated node still runs
+        ok = [x for x in nodes if x != n - 1][: M - 1]
+        Y = _gpu(kb, G, "cbl", "exp", ok, 6, t=1.0)
+    assert _rel(Y, _oracle(g, "cbl", ok, 6, "exp", t=1.0)) < TOL32
+    with pytest.raises(krylov.Breakdown):
+        _oracle(g, "cbl", nodes, 6, "exp", t=1.0)
+
+
 def test_path_single_column_all_lanczos_agree(kb):
     # the path graph of the paper's first experiment (n = 201, centre node), standard
     # Laplacian, e^{-20 L}

@@ -423,3 +423,94 @@ def test_local_reorth_is_a_no_op_in_exact_arithmetic():
     a = krylov.apply("cbl", L, nodes, 8, "exp", t=1.0).Y
     b = krylov.apply("cbl", L, nodes, 8, "exp", t=1.0, reorth="local").Y
     assert _rel(b, a) < 1e-12
+
+
+# ----------------------------------------------------------------------------- full reorthogonalisation
+# reorth=True is not in the paper (reading A10): X -= Q_{1:k}(Q_{1:k}^T X), twice.  It is
+# pinned by what it must achieve: it changes nothing in exact arithmetic (the Lanczos blocks
+# are orthonormal, Theorem 3.1's setting), its output is the orthogonal projection of X onto
+# the complement of the basis (orthogonal to the basis, and differing from X by an element of
+# its span), and it keeps a long FP64 run orthonormal where the plain recurrence is not.
+def _orth_defect(basis):
+    B = np.hstack(basis)
+    return float(np.linalg.norm(B.T @ B - np.eye(B.shape[1])))
+
+
+def _projection_defects(seed=40, n=300, N=4, k=6, scale=1e-9):
+    # X = B C + scale Z: almost inside the span of the basis, where one Gram-Schmidt pass
+    # leaves a component of relative size u / scale along it
+    rng = np.random.default_rng(seed)
+    B, _ = np.linalg.qr(rng.standard_normal((n, k * N)))
+    Q = [B[:, i * N:(i + 1) * N] for i in range(k)]
+    X = B @ rng.standard_normal((k * N, N)) + scale * rng.standard_normal((n, N))
+    out = krylov._reorthogonalise(X, Q)
+    along = float(np.linalg.norm(B.T @ out) / np.linalg.norm(out))
+    D = X - out
+    coef = np.linalg.lstsq(B, D, rcond=None)[0]
+    outside = float(np.linalg.norm(D - B @ coef) / np.linalg.norm(X))
+    return along, outside
+
+
+def _long_run_defects(m=40):
+    # weighted Barabasi-Albert: a few hub eigenvalues converge within a few steps and the
+    # FP64 three-term recurrence loses orthogonality (defect O(1) at m = 40)
+    g = synth.barabasi_albert_graph(2000, 5, seed=3, weighted=True)
+    L = _L(g)
+    nodes = synth.sample_nodes(g.n, 2, seed=4)
+    f = dense.phi_function("exp", t=1.0)
+    plain = krylov.cbl(L, nodes, m, f)
+    full = krylov.cbl(L, nodes, m, f, reorth=True)
+    return _orth_defect(plain.basis), _orth_defect(full.basis)
+
+
+def test_full_reorth_is_a_no_op_in_exact_arithmetic():
+    g = synth.grid_graph((20, 20))
+    L = _L(g)
+    nodes = synth.sample_nodes(g.n, 5, seed=31)
+    a = krylov.apply("cbl", L, nodes, 8, "exp", t=1.0)
+    b = krylov.apply("cbl", L, nodes, 8, "exp", t=1.0, reorth=True)
+    assert _rel(b.Y, a.Y) < 1e-12
+    assert _orth_defect(a.basis) < 1e-13 and _orth_defect(b.basis) < 1e-13
+
+
+def test_full_reorth_is_the_orthogonal_projection():
+    along, outside = _projection_defects()
+    assert along < 1e-12      # one pass: about 1e-7 here
+    assert outside < 1e-13
+
+
+def test_full_reorth_keeps_a_long_run_orthonormal():
+    plain, full = _long_run_defects()
+    assert plain > 1e-2       # the plain recurrence drifts (Paige)
+    assert full < 1e-12
+
+
+def _reorth_pins_hold():
+    along, outside = _projection_defects()
+    _, full = _long_run_defects()
+    return along < 1e-12 and outside < 1e-13 and full < 1e-12
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")   # the flipped process overflows
+def test_planted_reorth_sign_flip_is_caught(monkeypatch):
+    def bad(X, Q):
+        B = np.hstack(Q)
+        for _ in range(2):
+            X = X + B @ (B.T @ X)
+        return X
+    monkeypatch.setattr(krylov, "_reorthogonalise", bad)
+    assert not _reorth_pins_hold()
+
+
+def test_planted_reorth_single_pass_is_caught(monkeypatch):
+    def bad(X, Q):
+        B = np.hstack(Q)
+        return X - B @ (B.T @ X)
+    monkeypatch.setattr(krylov, "_reorthogonalise", bad)
+    assert not _reorth_pins_hold()
+
+
+def test_planted_reorth_without_newest_block_is_caught(monkeypatch):
+    real = krylov._reorthogonalise
+    monkeypatch.setattr(krylov, "_reorthogonalise", lambda X, Q: real(X, Q[:-1]) if len(Q) > 1 else X)
+    assert not _reorth_pins_hold()
