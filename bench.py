@@ -313,8 +313,8 @@ def measured_peaks():
 
 
 def ncu_traffic():
-    """DRAM traffic per algorithmic byte (kernel class -> ratio) from the committed ncu
-    summaries, if any."""
+    """DRAM traffic per algorithmic byte (kernel class -> (ratio, capture summary file))
+    from the committed ncu summaries, if any."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     out = {}
     if os.path.exists(p):
@@ -322,9 +322,9 @@ def ncu_traffic():
             line = line.strip()
             if line and not line.startswith("#"):
                 parts = line.split()
-                if len(parts) >= 2:
+                if len(parts) >= 3:
                     try:
-                        out[parts[0]] = float(parts[1])
+                        out[parts[0]] = (float(parts[1]), parts[2])
                     except ValueError:
                         pass
     return out
@@ -369,7 +369,9 @@ def run_reference(a, rank, world):
 
 
 def cpu_baseline(a, budget_s=25.0):
-    """The oracle as it stands on a bounded sample: the step's solves with 4 columns."""
+    """The oracle as it stands on a bounded sample: the step's solves with the first
+    ref_sample_cols columns.  Also returns the oracle's columns of the methods whose
+    columns are independent (sbl, cheb, cheb2), which equal the GPU's first columns."""
     import synth
     from oracle import krylov
     ts = [float(x) for x in a.ts.split(",")]
@@ -379,16 +381,32 @@ def cpu_baseline(a, budget_s=25.0):
     L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
     t0 = time.perf_counter()
     cols = 0
+    ref_cols = {}
     for mth in methods:
         for t in ts:
-            krylov.apply(mth, L, nodes, a.m, "exp", t=t)
+            Y = krylov.apply(mth, L, nodes, a.m, "exp", t=t).Y
             cols += len(nodes)
+            if mth in ("sbl", "cheb", "cheb2"):
+                ref_cols[(mth, t)] = Y
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": cols / dt, "unit": "kernel_columns/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{cols // len(nodes)} solves (methods {methods}, t {ts}) with the first "
-                      f"{len(nodes)} of {a.M} nodes, m={a.m}, full graph, {dt:.1f} s"}
+    return ({"value": cols / dt, "unit": "kernel_columns/s", "cores": os.cpu_count(), "kind": "oracle",
+             "sample": f"{cols // len(nodes)} solves (methods {methods}, t {ts}) with the first "
+                       f"{len(nodes)} of {a.M} nodes, m={a.m}, full graph, {dt:.1f} s"}, ref_cols)
+
+
+def accuracy_vs_oracle(ref_cols, first_cols, solves):
+    """Relative Frobenius error of the timed solves' first columns against the oracle's
+    columns for the methods with independent columns (the metric's 1e-6 gate)."""
+    out = {}
+    for (mth, t), Y in zip(solves, first_cols):
+        ref = ref_cols.get((mth, t))
+        if ref is None:
+            continue
+        y = Y.numpy().astype(np.float64)
+        out[f"{mth} t={t:g}"] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    return out
 
 
 # ----------------------------------------------------------------------------- replicas
@@ -491,41 +509,12 @@ def main():
     cols_per_step = len(solves) * a.M
     value = job_value(cols_per_step, world, ms)
 
-    # roofline of the dominant kernel class and of the SpMM
+    # Kernel-class profile of the timed region (five streams): the classes' launch
+    # durations overlap there (a class's summed time can exceed the step), so the roofline
+    # line below takes its launch durations from a one-stream pass of the same solves.
     peak, peak_kind = measured_peaks()
     traffic = ncu_traffic()
-
-    def roof(name):
-        s = stats.get(name)
-        if not s or s["total_ms"] <= 0:
-            return None
-        gbs = s["alg_bytes"] / (s["total_ms"] / 1e3) / 1e9
-        ratio = traffic.get(name)
-        # DRAM bytes per launch: the captured traffic/algorithmic ratio times this run's
-        # algorithmic bytes per launch
-        tr = round(ratio * s["alg_bytes"] / max(s["launches"], 1)) if ratio else None
-        out = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-               "frac": round(gbs / peak, 4), "traffic": tr,
-               "kernel": name, "launches_per_step": s["launches"] / a.steps,
-               "avg_launch_ms": s["total_ms"] / max(s["launches"], 1),
-               "share_of_step": round(s["total_ms"] / a.steps / ms, 4),
-               "peak_kind": f"{peak_kind} hbm_gbs",
-               "frac_of_nominal_7900_gbs": round(gbs / 7900.0, 4)}
-        if name == "rowblock" and not a.tensor_cores:
-            # the SIMT tall-skinny kernels are bound by FP32 FMA issue and shared memory,
-            # not by DRAM: roofline against the FP32 SIMT peak of the part (152 SMs x 128
-            # FMA lanes x 2 flops x the sampled SM clock), the DRAM view kept beside it
-            sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-            alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-            tfs = s["alg_flops"] / (s["total_ms"] / 1e3) / 1e12
-            out.update({"bound": "alu", "achieved": round(tfs, 2), "peak": round(alu_peak, 1),
-                        "unit": "TFLOP/s", "frac": round(tfs / alu_peak, 4),
-                        "peak_kind": f"FP32 SIMT FMA peak at {sm_mhz:.0f} MHz (unit counts x clock)",
-                        "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)})
-            out.pop("frac_of_nominal_7900_gbs", None)
-        return out
-
-    dom = max(stats.items(), key=lambda kv: kv[1]["total_ms"])[0] if stats else None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     shares = {k: round(v["total_ms"] / a.steps / ms, 4) for k, v in stats.items() if v["launches"]}
 
     # time of each solve alone (one stream, after the timed region; not part of value), with
@@ -544,27 +533,55 @@ def main():
     for i, (mth, t) in enumerate(solves):
         solve_ms[f"{mth} t={t:g}"] = round(evs[i].elapsed_time(evs[i + 1]), 3)
     ms1 = evs[0].elapsed_time(evs[-1])
-    spmm1 = stats1.get("spmm")
-    spmm_one_stream = None
-    if spmm1 and spmm1["total_ms"] > 0:
-        gbs1 = spmm1["alg_bytes"] / (spmm1["total_ms"] / 1e3) / 1e9
-        spmm_one_stream = {"bound": "hbm", "achieved": round(gbs1, 1), "peak": peak, "unit": "GB/s",
-                           "frac": round(gbs1 / peak, 4), "kernel": "spmm",
-                           "avg_launch_ms": spmm1["total_ms"] / max(spmm1["launches"], 1),
-                           "share_of_step": round(spmm1["total_ms"] / ms1, 4),
-                           "peak_kind": f"{peak_kind} hbm_gbs (launch duration alone on the GPU)"}
+    # the FP32 results' first columns, kept for the accuracy check against the oracle (the
+    # FP64 comparator below reuses the output buffers)
+    first_cols = [Y[:, : a.ref_sample_cols].cpu() for Y in Ys]
     shares_one_stream = {k: round(v["total_ms"] / ms1, 4) for k, v in stats1.items() if v["launches"]}
-    rb1 = stats1.get("rowblock")
-    rowblock_one_stream = None
-    if rb1 and rb1["total_ms"] > 0 and not a.tensor_cores:
-        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        tfs1 = rb1["alg_flops"] / (rb1["total_ms"] / 1e3) / 1e12
-        rowblock_one_stream = {"bound": "alu", "achieved": round(tfs1, 2), "peak": round(alu_peak, 1),
-                               "unit": "TFLOP/s", "frac": round(tfs1 / alu_peak, 4), "kernel": "rowblock",
-                               "avg_launch_ms": rb1["total_ms"] / max(rb1["launches"], 1),
-                               "share_of_step": round(rb1["total_ms"] / ms1, 4),
-                               "peak_kind": "FP32 SIMT FMA peak (launch duration alone on the GPU)"}
+
+    def roof(st, name, total_ms, timing):
+        """HBM roofline of one kernel class: algorithmic bytes per launch / mean launch time
+        against the measured copy bandwidth; traffic = DRAM bytes per launch scaled from
+        the ncu capture named in profiles/traffic.txt (ratio x this run's algorithmic
+        bytes), null when no capture covers the class."""
+        s = st.get(name)
+        if not s or s["total_ms"] <= 0:
+            return None
+        nl = max(s["launches"], 1)
+        gbs = s["alg_bytes"] / (s["total_ms"] / 1e3) / 1e9
+        ratio = traffic.get(name)
+        out = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+               "frac": round(gbs / peak, 4),
+               "traffic": round(ratio[0] * s["alg_bytes"] / nl) if ratio else None,
+               "traffic_source": (f"scaled: DRAM/algorithmic ratio {ratio[0]} of the capture "
+                                  f"profiles/{ratio[1]} x this run's algorithmic bytes per launch")
+                                 if ratio else None,
+               "kernel": name, "launches": s["launches"],
+               "alg_bytes_per_launch": round(s["alg_bytes"] / nl),
+               "avg_launch_ms": round(s["total_ms"] / nl, 5),
+               "share_of_step": round(s["total_ms"] / total_ms, 4),
+               "timing": timing, "peak_kind": f"{peak_kind} hbm_gbs",
+               "frac_of_nominal_7900_gbs": round(gbs / 7900.0, 4)}
+        if s["alg_flops"] > 0 and name == "rowblock":
+            # the SIMT tall-skinny products also meet the FP32 FMA issue limit: unit counts
+            # (SMs queried from the device x 128 FP32 lanes x 2 flops) x the sampled clock
+            sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+            alu_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+            tfs = s["alg_flops"] / (s["total_ms"] / 1e3) / 1e12
+            out["alu_view"] = {"achieved_tflops": round(tfs, 2), "peak_tflops": round(alu_peak, 1),
+                               "frac": round(tfs / alu_peak, 4),
+                               "peak_kind": f"FP32 FMA peak: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz"}
+        return out
+
+    one = "one-stream pass of the step's solves after the timed region (launches alone on the GPU)"
+    five = ("timed region, five streams: launch durations overlap other streams' kernels, so "
+            "share_of_step can exceed 1 and achieved is a lower bound")
+    # dominant class among those that move HBM bytes (the FP64 single-CTA classes have none)
+    hbm_classes = {k: v for k, v in stats1.items() if v["alg_bytes"] > 0}
+    dom1 = max(hbm_classes.items(), key=lambda kv: kv[1]["total_ms"])[0] if hbm_classes else None
+    roofline = roof(stats1, dom1, ms1, one) if dom1 else None
+    spmm_one_stream = roof(stats1, "spmm", ms1, one)
+    rowblock_one_stream = roof(stats1, "rowblock", ms1, one)
+    spmm_five_stream = roof(stats, "spmm", ms * a.steps, five)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed
     # region; one host thread per stream, each running its share of the solves
@@ -630,19 +647,29 @@ def main():
             "dtype": "f32" if a.basis == "f32" else a.basis, "data": "synthetic",
             "config": workload_config(a),
             "clocks": clocks, "gpu_launches": int(launches),
-            "roofline": roof(dom) if dom else None,
-            "spmm_roofline": roof("spmm"),
+            "roofline": roofline,
+            "spmm_roofline": spmm_one_stream,
+            "spmm_roofline_five_stream": spmm_five_stream,
             "kernel_shares": shares,
             "e2e": e2e, "fp64_plain": fp64, "solve_ms_one_stream": solve_ms,
-            "spmm_roofline_one_stream": spmm_one_stream,
-            "rowblock_roofline_one_stream": rowblock_one_stream, "kernel_shares_one_stream": shares_one_stream,
+            "rowblock_roofline": rowblock_one_stream, "kernel_shares_one_stream": shares_one_stream,
             "serving": serving, "graph_create_ms": round(graph_create_ms, 1),
         }
+        acc_fail = False
         if world == 1 and not a.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(a)
+            out["cpu_baseline"], ref_cols = cpu_baseline(a)
+            errs = accuracy_vs_oracle(ref_cols, first_cols, solves)
+            out["rel_err_vs_oracle"] = {
+                "max": max(errs.values()) if errs else None, "per_solve": errs, "gate": 1e-6,
+                "what": (f"first {a.ref_sample_cols} columns of the timed sbl / cheb / cheb2 solves "
+                         "(independent columns) against the FP64 oracle's columns")}
+            acc_fail = bool(errs) and max(errs.values()) > 1e-6
             # the small grid case with its dense-eigendecomposition baseline
             out["cpu_baseline_small_config"] = small_config(kb, torch)
         print(json.dumps(out))
+        if acc_fail:
+            sys.stdout.flush()
+            sys.exit("accuracy gate failed: relative error above 1e-6 against the FP64 oracle")
     G.destroy()
     if world > 1:
         dist.destroy_process_group()

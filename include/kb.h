@@ -98,6 +98,10 @@ typedef struct {
     int32_t breakdown_step;  /* step of a rank-deficient block, or -1                             */
     int32_t spmm_launches;   /* SpMM kernels launched by the call                                  */
     double  lambda_used;     /* Lambda used for the Chebyshev methods (0 for Lanczos)              */
+    double  est_change;      /* KB_CBL with params.tol > 0: ||U_k - [U_k'; 0]||_F / ||U_k||_F at the
+                                last stopping-rule check that ran (the estimate of the change of Y
+                                since the previous check, Q being orthonormal); -1 when no check
+                                compared two results (tol = 0, other methods, m <= 12)           */
 } kb_info;
 
 typedef struct kb_graph kb_graph;   /* opaque; owned by the library */
@@ -205,9 +209,11 @@ int kb_krylov_apply_host(kb_graph *g, kb_method method, kb_phi phi, const kb_par
  * reserved the device memory for its own allocator, latency-critical loops that must not
  * enter an allocator after start-up, and processes sharing a device under a fixed memory
  * budget.  It computes exactly what kb_krylov_apply(g, KB_CHEB, phi, params, nodes, M, m,
- * Y, stream, NULL) computes (same kernels, same order of operations), but its scratch is a
- * file-scope device array of KB_FIXED_SCRATCH_BYTES (32 MiB) that every GPU loading the
- * library holds until the process exits; the call performs no cudaMalloc, cudaMallocAsync
+ * Y, stream, NULL) computes, bit for bit: it runs the same SpMM kernel with the same
+ * coefficients on every row at every step (KB_CHEB also skips rows beyond the frontier,
+ * whose values are exactly zero).  Its scratch is a file-scope device array of
+ * KB_FIXED_SCRATCH_BYTES (32 MiB) that every GPU loading the library holds until the
+ * process exits; the call performs no cudaMalloc, cudaMallocAsync
  * or cudaFree and calls no allocating library routine.
  *
  *   Arguments as kb_krylov_apply, restricted to 1 <= M <= 128, 1 <= m <= 1024 and

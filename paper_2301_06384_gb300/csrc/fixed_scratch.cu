@@ -9,8 +9,11 @@
 // cudaMalloc / cudaMallocAsync / cudaFree and calls no allocating library routine.
 //
 // The paper has no counterpart of this entry point; it is a deployment variant of the
-// Chebyshev method of Section 3.4 and returns the same result as kb_krylov_apply with
-// KB_CHEB (same kernels, same order of operations).
+// Chebyshev method of Section 3.4.  It runs the Clenshaw recurrence of kb_krylov_apply with
+// KB_CHEB on all n rows at every step (no frontier restriction, which would need more
+// scratch).  The frontier restriction only skips rows whose values are exactly zero, and
+// every other row goes through the same SpMM kernel with the same coefficients, so the two
+// entry points return bitwise equal results.
 #include "kb_internal.cuh"
 #include "kb_kernels.cuh"
 
@@ -56,13 +59,7 @@ extern "C" int kb_cheb_apply_fixed_scratch(kb_graph *g, kb_phi phi, const kb_par
     if (M < 1 || M > 128 || M > g->dev.n) return fail(KB_ERR_ARG, "M must be in [1, min(128, n)]");
     if (m < 1 || m > MAX_M_STEPS) return fail(KB_ERR_ARG, "m must be in [1, 1024]");
     if (params->basis != KB_F32) return fail(KB_ERR_UNSUPPORTED, "fixed-scratch solve is FP32 only");
-    if (phi == KB_PHI_EXP) {
-        if (!std::isfinite(params->t)) return fail(KB_ERR_ARG, "t not finite");
-    } else if (phi == KB_PHI_SPLINE) {
-        if (!(params->eps > 0) || !(params->s > 0)) return fail(KB_ERR_ARG, "eps and s must be > 0");
-    } else {
-        return fail(KB_ERR_ARG, "bad phi");
-    }
+    if (int rc = validate_phi(phi, *params)) return rc;
     for (int i = 0; i < M; ++i) {
         if (nodes[i] < 0 || nodes[i] >= g->dev.n) return fail(KB_ERR_NODES, "node index out of range");
         for (int j = 0; j < i; ++j)
@@ -76,7 +73,8 @@ extern "C" int kb_cheb_apply_fixed_scratch(kb_graph *g, kb_phi phi, const kb_par
         return fail(KB_ERR_ARG, "problem needs " + std::to_string(need) +
                                     " bytes of scratch; the fixed scratch holds " +
                                     std::to_string(FIXED_SCRATCH_BYTES));
-    KB_CUDA_TRY(cudaSetDevice(g->device));
+    DeviceGuard dg;
+    KB_CUDA_TRY(dg.set(g->device));
     void *base = nullptr;
     int rc = scratch_address(g->device, &base);
     if (rc) return rc;
@@ -86,21 +84,13 @@ extern "C" int kb_cheb_apply_fixed_scratch(kb_graph *g, kb_phi phi, const kb_par
     int32_t *marker = reinterpret_cast<int32_t *>(static_cast<char *>(base) + 3 * blk);
 
     // Lobatto interpolation coefficients of phi on [0, Lambda] (Eq. (chebcoeff), reading
-    // A3), in a fixed host array; the series weights halve c_0 and c_m.
+    // A3), computed by the routine KB_CHEB uses, into fixed host arrays; the series weights
+    // halve c_0 and c_m.
     const double lam = params->lambda_max > 0 ? params->lambda_max : g->lambda;
     double f[MAX_M_STEPS + 1], w[MAX_M_STEPS + 1];
-    for (int j = 0; j <= m; ++j) {
-        const double x = 0.5 * lam * (1.0 - std::cos(M_PI * j / m));
-        f[j] = phi == KB_PHI_EXP ? std::exp(-params->t * x) : std::pow(params->eps + x, -params->s);
-    }
-    for (int k = 0; k <= m; ++k) {
-        double acc = 0.0;
-        for (int j = 0; j <= m; ++j) {
-            const long r = (long(j) * k) % (2L * m);
-            acc += ((j == 0 || j == m) ? 0.5 : 1.0) * f[j] * std::cos(M_PI * double(r) / m);
-        }
-        w[k] = 2.0 / m * acc * ((k == 0 || k == m) ? 0.5 : 1.0);
-    }
+    lobatto_coeffs_into(phi, *params, m, lam, false, f, w);
+    w[0] *= 0.5;
+    w[m] *= 0.5;
 
     // Clenshaw: b_m = w_m E_W; b_k = w_k E_W + 2 A b_{k+1} - b_{k+2}; Y = w_0 E_W + A b_1 - b_2,
     // A = I - (2/Lambda) L.  Every buffer that is read is written first in this call.

@@ -66,6 +66,25 @@ struct Ctrl {
     int32_t stop;            // 1 once the process stopped (invariant space or breakdown)
     int32_t steps;           // blocks entering the result
     int32_t breakdown_step;  // -1 or step index
+    double est_change;       // stopping rule: relative change at the last check, -1 if none
+};
+
+// Makes a device current for the lifetime of the object and restores the caller's current
+// device afterwards (entry points switch to the graph's device and must not leave the
+// calling thread on it).
+class DeviceGuard {
+  public:
+    DeviceGuard() { ok_ = cudaGetDevice(&prev_) == cudaSuccess; }
+    cudaError_t set(int dev) { return cudaSetDevice(dev); }
+    ~DeviceGuard() {
+        if (ok_) cudaSetDevice(prev_);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+
+  private:
+    int prev_ = 0;
+    bool ok_ = false;
 };
 
 // ------------------------------------------------------------------ profiling (events)
@@ -223,6 +242,14 @@ bool rowblock_tc_supported(int mode, int W);
 bool rowblock_tc_enabled();   // KB_TENSOR_CORES=1 in the environment
 int launch_rowblock_tc(int mode, const RowArgs<float> &a, cudaStream_t s, int max_grid, int *grid_out);
 int rowblock_tc_max_grid();
+
+// Host coefficient math shared by the entry points (krylov.cu).  lobatto_coeffs_into: the
+// Lobatto interpolation coefficients c_0..c_m of phi (or sqrt(phi)) on [0, lam] into the
+// caller's arrays f (samples) and c, m + 1 doubles each, without allocating.  validate_phi:
+// KB_OK, or KB_ERR_ARG for a bad kernel choice or non-finite / non-positive parameters.
+void lobatto_coeffs_into(kb_phi phi, const kb_params &p, int m, double lam, bool sqrt_phi, double *f,
+                         double *c);
+int validate_phi(kb_phi phi, const kb_params &p);
 
 // Deterministic FP64 reduction of [nparts][len] partials into out[len]; when out_p is set
 // the sums are also written there rounded to P.

@@ -69,8 +69,10 @@ static double phi_value(kb_phi phi, const kb_params &p, double lam, bool sqrt_ph
 //   c_k = (2/m) sum_{j=0..m}'' f(lambda_j) cos(pi j k / m),  lambda_j = lam/2 (1 - cos(pi j/m)),
 // the double prime halving the j = 0 and j = m terms.  The series sum_k'' c_k T_k (c_0 and
 // c_m halved) interpolates f on the grid.
-std::vector<double> lobatto_coeffs(kb_phi phi, const kb_params &p, int m, double lam, bool sqrt_phi) {
-    std::vector<double> f(m + 1), c(m + 1);
+// f and c: caller arrays of m + 1 doubles (f receives the samples); no allocation, so the
+// fixed-scratch entry point shares it.
+void lobatto_coeffs_into(kb_phi phi, const kb_params &p, int m, double lam, bool sqrt_phi, double *f,
+                         double *c) {
     for (int j = 0; j <= m; ++j)
         f[j] = phi_value(phi, p, 0.5 * lam * (1.0 - std::cos(M_PI * j / m)), sqrt_phi);
     for (int k = 0; k <= m; ++k) {
@@ -83,7 +85,26 @@ std::vector<double> lobatto_coeffs(kb_phi phi, const kb_params &p, int m, double
         }
         c[k] = 2.0 / m * s;
     }
+}
+
+std::vector<double> lobatto_coeffs(kb_phi phi, const kb_params &p, int m, double lam, bool sqrt_phi) {
+    std::vector<double> f(m + 1), c(m + 1);
+    lobatto_coeffs_into(phi, p, m, lam, sqrt_phi, f.data(), c.data());
     return c;
+}
+
+// The kernel choice and its parameters (Section 2.4): t finite for e^{-t lambda}; eps > 0 and
+// s > 0, both finite, for (eps + lambda)^{-s}.
+int validate_phi(kb_phi phi, const kb_params &p) {
+    if (phi == KB_PHI_EXP) {
+        if (!std::isfinite(p.t)) return fail(KB_ERR_ARG, "t not finite");
+    } else if (phi == KB_PHI_SPLINE) {
+        if (!(p.eps > 0) || !std::isfinite(p.eps)) return fail(KB_ERR_ARG, "eps must be > 0");
+        if (!(p.s > 0) || !std::isfinite(p.s)) return fail(KB_ERR_ARG, "s must be > 0");
+    } else {
+        return fail(KB_ERR_ARG, "bad phi");
+    }
+    return KB_OK;
 }
 
 // ---------------------------------------------------------------- workspace
@@ -737,7 +758,6 @@ int validate(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
     if (!nodes) return fail(KB_ERR_ARG, "nodes is NULL");
     if (!Y) return fail(KB_ERR_ARG, "Y is NULL");
     if (method < KB_CBL || method > KB_CHEB2) return fail(KB_ERR_ARG, "bad method");
-    if (phi != KB_PHI_EXP && phi != KB_PHI_SPLINE) return fail(KB_ERR_ARG, "bad phi");
     if (M < 1 || M > g->dev.n) return fail(KB_ERR_ARG, "M out of range");
     if (m < 1 || m > 100000) return fail(KB_ERR_ARG, "m out of range");
     if (method == KB_CHEB2 && m < 2) return fail(KB_ERR_ARG, "KB_CHEB2 needs m >= 2");
@@ -757,12 +777,7 @@ int validate(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
     const int wmax = params->basis == KB_F64 ? 64 : 128;
     if ((method == KB_CBL || method == KB_GBL) && M > wmax)
         return fail(KB_ERR_UNSUPPORTED, "block width too large for this method and dtype");
-    if (phi == KB_PHI_EXP) {
-        if (!std::isfinite(params->t)) return fail(KB_ERR_ARG, "t not finite");
-    } else {
-        if (!(params->eps > 0) || !std::isfinite(params->eps)) return fail(KB_ERR_ARG, "eps must be > 0");
-        if (!(params->s > 0) || !std::isfinite(params->s)) return fail(KB_ERR_ARG, "s must be > 0");
-    }
+    if (int rc = validate_phi(phi, *params)) return rc;
     *s_int = 0;
     if (phi == KB_PHI_SPLINE && (method == KB_CBL || method == KB_GBL || method == KB_SBL)) {
         if (params->s != std::floor(params->s) || params->s > 64)
@@ -784,7 +799,8 @@ int apply_device(kb_graph *g, kb_method method, kb_phi phi, const kb_params *par
     int s_int = 0;
     int rc = validate(g, method, phi, params, nodes, M, m, Y, &s_int);
     if (rc) return rc;
-    KB_CUDA_TRY(cudaSetDevice(g->device));
+    DeviceGuard dg;
+    KB_CUDA_TRY(dg.set(g->device));
     ensure_pool(g->device);
     Common c{g, phi, *params, s_int, static_cast<cudaStream_t>(stream), 0, nullptr, true};
     // exact restriction of the per-step kernels to rows reached from W (hop distances are
@@ -796,7 +812,7 @@ int apply_device(kb_graph *g, kb_method method, kb_phi phi, const kb_params *par
     // one host control block per column group (sbl may run several groups)
     std::vector<Ctrl> hc;
     const int ngroups = method == KB_SBL ? (M + chunk - 1) / chunk : 1;
-    if (info) hc.assign(ngroups, Ctrl{KB_OK, 0, m, -1});
+    if (info) hc.assign(ngroups, Ctrl{KB_OK, 0, m, -1, -1.0});
     switch (method) {
         case KB_CBL:
             c.hctrl = info ? &hc[0] : nullptr;
@@ -832,11 +848,13 @@ int apply_device(kb_graph *g, kb_method method, kb_phi phi, const kb_params *par
     info->status = KB_OK;
     info->steps_done = m;
     info->breakdown_step = -1;
+    info->est_change = -1.0;
     for (const Ctrl &h : hc) {
         if (h.status != KB_OK) info->status = h.status;
         if (h.breakdown_step >= 0) info->breakdown_step = h.breakdown_step;
         if (method != KB_SBL) info->steps_done = h.steps;
     }
+    if (method == KB_CBL && params->tol > 0.0) info->est_change = hc[0].est_change;
     if (method == KB_CHEB2) info->steps_done = 2 * (m / 2);
     info->spmm_launches = c.spmm;
     info->lambda_used = (method == KB_CHEB || method == KB_CHEB2)
@@ -871,7 +889,8 @@ extern "C" int kb_krylov_apply_host(kb_graph *g, kb_method method, kb_phi phi,
     try {
         if (!g || !Y_host) return fail(KB_ERR_ARG, "graph or Y_host is NULL");
         if (M < 1 || M > g->dev.n) return fail(KB_ERR_ARG, "M out of range");
-        KB_CUDA_TRY(cudaSetDevice(g->device));
+        DeviceGuard dg;
+        KB_CUDA_TRY(dg.set(g->device));
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         float *dY = nullptr;
         const size_t bytes = sizeof(float) * size_t(g->dev.n) * size_t(M);

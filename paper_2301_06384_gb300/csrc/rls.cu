@@ -150,7 +150,8 @@ extern "C" int kb_rls_predict(kb_graph *g, kb_method method, kb_phi phi, const k
         if (!g || !params || !nodes || !labels || !y_pred) return fail(KB_ERR_ARG, "NULL argument");
         if (M < 1 || M > 128 || M > g->dev.n) return fail(KB_ERR_ARG, "M must be in [1, min(128, n)]");
         if (!(gamma >= 0) || !std::isfinite(gamma)) return fail(KB_ERR_ARG, "gamma must be >= 0");
-        KB_CUDA_TRY(cudaSetDevice(g->device));
+        DeviceGuard dg;
+        KB_CUDA_TRY(dg.set(g->device));
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const int64_t n = g->dev.n;
         // scratch: Y (n x M float), nodes, labels, c, status

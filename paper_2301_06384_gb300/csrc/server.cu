@@ -126,7 +126,8 @@ extern "C" int kb_server_create(int32_t device, const kb_server_config *cfg, kb_
         if (!cfg || !out) return fail(KB_ERR_ARG, "config or out is NULL");
         if (cfg->streams < 1 || cfg->streams > 64) return fail(KB_ERR_ARG, "streams must be in [1, 64]");
         if (cfg->queue_capacity < 1) return fail(KB_ERR_ARG, "queue_capacity must be >= 1");
-        KB_CUDA_TRY(cudaSetDevice(device));
+        DeviceGuard dg;
+        KB_CUDA_TRY(dg.set(device));
         size_t budget = 0;
         if (cfg->memory_budget > 0) {
             budget = size_t(cfg->memory_budget);

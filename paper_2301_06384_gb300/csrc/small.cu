@@ -61,6 +61,7 @@ __global__ void k_ctrl_init(Ctrl *c, int steps) {
     c->stop = 0;
     c->steps = steps;
     c->breakdown_step = -1;
+    c->est_change = -1.0;
 }
 
 template <typename T>
@@ -950,9 +951,13 @@ __global__ void __launch_bounds__(1024) k_conv_check(const double *U, const doub
     if (threadIdx.x == 0) {
         double D = 0.0, N = 0.0;
         for (int w = 0; w < int(blockDim.x >> 5); ++w) { D += sd[w]; N += sn[w]; }
-        if (ps > 0 && sqrt(D) <= tol * sqrt(N)) {
-            ctrl->stop = 1;
-            ctrl->steps = steps;
+        if (ps > 0) {
+            const double change = N > 0.0 ? sqrt(D) / sqrt(N) : 0.0;
+            ctrl->est_change = change;
+            if (change <= tol) {
+                ctrl->stop = 1;
+                ctrl->steps = steps;
+            }
         }
         *prev_steps = steps;
     }

@@ -23,7 +23,7 @@ KB_GRAPH_SKIP_SYMMETRY_CHECK = 1
 KB_GRAPH_NORMALIZED = 2
 STATUS = {0: "KB_OK", -1: "KB_ERR_ARG", -2: "KB_ERR_CSR", -3: "KB_ERR_NODES", -4: "KB_ERR_CUDA",
           -5: "KB_ERR_NOMEM", -6: "KB_ERR_BREAKDOWN", -7: "KB_ERR_UNSUPPORTED", -8: "KB_ERR_BUSY",
-          1: "KB_PENDING"}
+          -9: "KB_ERR_ORTHOGONALITY", 1: "KB_PENDING"}
 KB_PENDING = 1
 
 
@@ -43,7 +43,7 @@ class kb_params(ctypes.Structure):
 class kb_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("steps_done", ctypes.c_int32),
                 ("breakdown_step", ctypes.c_int32), ("spmm_launches", ctypes.c_int32),
-                ("lambda_used", ctypes.c_double)]
+                ("lambda_used", ctypes.c_double), ("est_change", ctypes.c_double)]
 
 
 class kb_server_config(ctypes.Structure):
@@ -224,7 +224,7 @@ def kb_krylov_apply(graph: Graph, method: str, phi: str, params: kb_params, node
     if info:
         return {"status": inf.status, "steps_done": inf.steps_done,
                 "breakdown_step": inf.breakdown_step, "spmm_launches": inf.spmm_launches,
-                "lambda_used": inf.lambda_used}
+                "lambda_used": inf.lambda_used, "est_change": inf.est_change}
     return None
 
 
@@ -240,7 +240,7 @@ def kb_krylov_apply_host(graph: Graph, method: str, phi: str, params: kb_params,
     if info:
         return {"status": inf.status, "steps_done": inf.steps_done,
                 "breakdown_step": inf.breakdown_step, "spmm_launches": inf.spmm_launches,
-                "lambda_used": inf.lambda_used}
+                "lambda_used": inf.lambda_used, "est_change": inf.est_change}
     return None
 
 
@@ -352,7 +352,7 @@ class Server:
         _check(rc)
         return ({"status": inf.status, "steps_done": inf.steps_done,
                  "breakdown_step": inf.breakdown_step, "spmm_launches": inf.spmm_launches,
-                 "lambda_used": inf.lambda_used}, lat.value)
+                 "lambda_used": inf.lambda_used, "est_change": inf.est_change}, lat.value)
 
     def close(self):
         if self.handle:

@@ -46,6 +46,9 @@ def test_stopping_rule_matches_fixed_m(kb, rgg, phi, kw):
     assert k in CHECKS
     assert fi["steps_done"] == k
     assert torch.equal(Ya, Yf)
+    # the estimate that stopped the process is reported; the fixed-m call ran no check
+    assert 0.0 <= ia["est_change"] <= 1e-6
+    assert fi["est_change"] == -1.0
     Y = Ya.cpu().numpy().astype(np.float64)
     assert _rel(Y, _oracle(rgg, "cbl", nodes, k, phi, **kw)) < tol32(phi, lam, **kw)
     # the stopped result is within a small multiple of tol of the converged one
@@ -67,3 +70,5 @@ def test_stopping_rule_errors(kb, rgg):
         # a tolerance no check meets: all m steps run
         Y2, info = kb.kernel_columns(G, "cbl", "exp", nodes, 20, info=True, t=1.0, tol=1e-30)
         assert info["steps_done"] == 20
+        # checks ran at steps 8, 12 and 16: the last one compared 16 with 12
+        assert 1e-30 < info["est_change"] < 1.0
