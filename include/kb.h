@@ -172,9 +172,15 @@ int kb_graph_info(const kb_graph *g, int64_t *n, int64_t *nnz_offdiag, double *l
  *           then filled with NaN.  With info == NULL the call does not synchronise, and
  *           these failures show only as NaN in Y.
  *
- * Not implemented (KB_ERR_UNSUPPORTED): the Lanczos methods with KB_PHI_SPLINE and
- * non-integer s (or s > 64); reorth with methods other than KB_CBL; KB_CBL / KB_GBL with
- * M > 128 (M > 64 for KB_F64).
+ * Spline kernel with the Lanczos methods: phi(H_m) F_1 = (eps I + H_m)^{-s} F_1 is formed by
+ * floor(s) block Cholesky solves with eps I + H_m and, for non-integer s, a quadrature of
+ * the fractional power over real shifts sigma_k > eps (Gauss-Jacobi rule of the Stieltjes
+ * integral of z^{-alpha}, relative accuracy 1e-14 on [0, Lambda]), one solve with
+ * sigma_k I + H_m per node (kb_spline_quadrature gives the rule).
+ *
+ * Not implemented (KB_ERR_UNSUPPORTED): the Lanczos methods with KB_PHI_SPLINE and s >= 65,
+ * or with (eps + Lambda) / eps so large that 240 quadrature nodes do not reach 1e-14;
+ * reorth with methods other than KB_CBL; KB_CBL / KB_GBL with M > 128 (M > 64 for KB_F64).
  * Other errors: KB_ERR_ARG, KB_ERR_NODES, KB_ERR_NOMEM, KB_ERR_CUDA (also when an opt-in
  * tensor-core kernel gives up waiting for its MMA completion).
  *
@@ -259,6 +265,18 @@ int kb_cheb_lobatto_coeffs(kb_phi phi, const kb_params *params, int32_t m, doubl
  * fails with KB_ERR_ARG when it exceeds cap). */
 int kb_exp_series_coeffs(double t, double lam, double tol, double *d, int32_t cap,
                          int32_t *count);
+
+/* Quadrature form of the spline kernel for non-integer s (Section 2.4), as the Lanczos methods
+ * use it: (eps + lambda)^{-s} ~ (eps + lambda)^{-s_int} sum_k weight_k / (shift_k + lambda) on
+ * [0, lam], s_int = floor(s), relative error <= tol (checked on a grid of [0, lam]).  The
+ * nodes are a Gauss-Jacobi rule of the Stieltjes integral
+ * z^{-alpha} = sin(pi alpha)/pi int_0^inf t^{-alpha} / (t + z) dt, alpha = s - s_int, after
+ * the substitution t = c ((1-x)/(1+x))^3, c = sqrt(eps (eps + lam)).  shift, weight: host
+ * arrays of cap doubles; *count receives the number of nodes (0 for integer s), *s_int
+ * floor(s).  Errors: KB_ERR_ARG (bad arguments, cap too small), KB_ERR_UNSUPPORTED (240
+ * nodes do not reach tol). */
+int kb_spline_quadrature(double eps, double s, double lam, double tol, double *shift, double *weight,
+                         int32_t cap, int32_t *count, int32_t *s_int);
 
 /* ------------------------------------------------------------------ measurement aids
  * Optional CUDA-event timing of every kernel launch class (not part of the method).

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkb.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["graph.cu", "spmm.cu", "rowblock.cu", "rowblock_tc.cu", "small.cu", "projected.cu", "krylov.cu",
-           "fixed_scratch.cu", "server.cu", "rls.cu"]
+           "fixed_scratch.cu", "server.cu", "rls.cu", "quadrature.cu"]
 
 
 def nvcc() -> str:

@@ -22,6 +22,34 @@ struct ChebCoef {
     double d[CAP];
 };
 
+// Rational (quadrature) form of the fractional spline power, used for non-integer s:
+//   (eps + lambda)^{-s} = (eps + lambda)^{-s_int} * sum_k weight_k / (shift_k + lambda),
+// s_int = floor(s); the sum approximates (eps + lambda)^{-alpha}, alpha = s - s_int, on
+// [0, lam] by Gauss-Jacobi quadrature of the Stieltjes integral of z^{-alpha}
+// (quadrature.cu).  n = 0 when s is an integer.  Passed to kernels by value.
+struct QuadRule {
+    static constexpr int CAP = 240;   // keeps the struct under 4 KB of kernel parameters
+    int32_t n;
+    int32_t s_int;
+    double shift[CAP];
+    double weight[CAP];
+};
+// Fills q for (eps, s) on the spectral interval [0, lam] such that the relative error of the
+// sum on [0, lam] is at most tol (checked on a grid); KB_ERR_UNSUPPORTED when CAP nodes do
+// not reach tol, KB_ERR_ARG for bad arguments.  Host only.
+int spline_quadrature(double eps, double s, double lam, double tol, QuadRule &q);
+
+// Coefficients of the projected step of gbl / sbl passed to the tridiagonal kernel: the
+// Chebyshev series of e^{-t lambda} (diffusion kernel) or, for the spline kernel with
+// non-integer s, the quadrature rule of the fractional power.
+struct TriCoef {
+    union {
+        ChebCoef cc;
+        QuadRule q;
+    };
+};
+static_assert(sizeof(TriCoef) <= 3900, "projected-step coefficients must fit the 4 KB kernel parameter space");
+
 int launch_ctrl_init(Ctrl *c, int steps, cudaStream_t s);
 // dst = src with steps = min(src->steps, k) (the projected problem of the first k steps),
 // or 0 once src stopped
@@ -53,9 +81,12 @@ int launch_lanczos_alpha(const double *parts, int nparts, int W, int M, int gbl,
 int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, int k, int round32,
                         double thresh, double *beta, double *sigma, int32_t *alive, double *c1,
                         double *c2, Ctrl *ctrl, cudaStream_t s);
+// phi(T) e_1 per tridiagonal T (one for gbl, one per column for sbl).  Spline kernel:
+// (eps I + T)^{-s_int} applied after the fractional factor sum_k W_k (sigma_k I + T)^{-1}
+// when tc.q.n > 0; qwork: 2 m tc.q.n doubles per column (nullptr when tc.q.n == 0).
 int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const double *beta,
                        const double *sigma, int phi_kind, double eps, int s_int, double lam,
-                       const ChebCoef &cc, double *omega, double *work, Ctrl *ctrl,
+                       const TriCoef &tc, double *omega, double *work, double *qwork, Ctrl *ctrl,
                        double bound, cudaStream_t s);
 template <typename T>
 int launch_axpy_colnorm(int W, T *X, const T *P, const double *a, int64_t n, double *parts,
@@ -79,9 +110,18 @@ int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ct
 int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
                    const std::vector<double> &d, double *V0, double *V1, double *V2, double *U,
                    const Ctrl *ctrl, cudaStream_t s);
+// U = (eps I + H_m)^{-s} F_1.  Integer s: s_int block Cholesky solves (q == nullptr or
+// q->n == 0).  Non-integer s: the quadrature rule q gives the fractional factor
+// sum_k W_k (sigma_k I + H_m)^{-1} F_1, one block Cholesky factorisation and solve per node
+// (qbatch nodes at a time, one CTA each, in qscr: qbatch * bt_quad_node_doubles(M, m)
+// doubles), then s_int solves with eps I + H_m.
+__host__ __device__ inline size_t bt_quad_node_doubles(int M, int m) {
+    return 3 * size_t(m) * M * M + size_t(m) * M;   // Ld, Ls, Y blocks and reciprocal diagonals
+}
 int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double eps, int s_int,
                      double *Ld, double *Ls, double *Yw, double *U, const Ctrl *ctrl,
-                     cudaStream_t s);
+                     cudaStream_t s, const QuadRule *q = nullptr, double *qscr = nullptr,
+                     int qbatch = 0);
 
 // Graph utilities.
 int launch_gershgorin(const GraphDev &g, double *out, cudaStream_t s);

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <memory>
 #include <mutex>
 
 namespace kb {
@@ -144,7 +145,27 @@ struct Common {
     int spmm = 0;
     Ctrl *hctrl = nullptr;   // host copy of the control block when the caller wants info
     bool frontier = true;    // restrict the per-step kernels to the reached rows
+    const QuadRule *quad = nullptr;   // spline kernel with non-integer s (Lanczos methods)
 };
+
+// The quadrature rule of the fractional spline power for the Lanczos methods (q->n = 0 when
+// it is not needed: diffusion kernel, Chebyshev methods, integer s).  Relative accuracy
+// 1e-14 on [0, Lambda], far below the FP64 rounding of the projected solves it feeds.
+int quad_setup(const kb_graph *g, kb_method method, kb_phi phi, const kb_params &p, QuadRule &q) {
+    q.n = 0;
+    q.s_int = 0;
+    if (phi != KB_PHI_SPLINE || method == KB_CHEB || method == KB_CHEB2) return KB_OK;
+    return spline_quadrature(p.eps, p.s, g->lambda, 1e-14, q);
+}
+
+// Quadrature nodes processed at once by the cbl projected step (one CTA and one scratch
+// region of bt_quad_node_doubles(M, m) doubles each), at most 1 GiB of scratch.
+int quad_batch(const QuadRule *q, int M, int m) {
+    if (!q || q->n == 0) return 0;
+    const size_t per = bt_quad_node_doubles(M, m) * sizeof(double);
+    const size_t cap = std::max<size_t>(1, (size_t(1) << 30) / per);
+    return int(std::min<size_t>({size_t(q->n), size_t(2 * num_sms()), cap}));
+}
 #define KB_TRY(x)                \
     do {                         \
         int _rc = (x);           \
@@ -178,6 +199,7 @@ struct CblBufs {
     C *Cbs, *Bs, *Rs1, *Rs2, *Cloc;
     double *Gsum, *Hd, *Hs, *R1, *V0, *V1, *V2, *U;
     double *Uc;          // stopping rule: two U_k of the checks (alternating)
+    double *qscr;        // projected step with non-integer s: per-node block solves
     int32_t *chk_prev;   // steps of the previous check (0: none yet)
     Ctrl *ctrl, *ctrl2, *ctrl_chk;
     uint8_t *gen;
@@ -185,7 +207,8 @@ struct CblBufs {
 };
 
 template <typename T>
-void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_grid, bool two_pass) {
+void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_grid, bool two_pass,
+              int qbatch) {
     b.basis = ar.take<T>(size_t(two_pass ? 3 : m) * n * W);
     b.wbuf = ar.take<T>(size_t(n) * W);
     using C = typename Cmp<T>::type;
@@ -206,6 +229,7 @@ void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_g
     b.V2 = ar.take<double>(size_t(m) * M * M);
     b.U = ar.take<double>(size_t(m) * M * M);
     b.Uc = ar.take<double>(size_t(2) * m * M * M);
+    b.qscr = qbatch > 0 ? ar.take<double>(size_t(qbatch) * bt_quad_node_doubles(M, m)) : nullptr;
     b.chk_prev = ar.take<int32_t>(1);
     b.ctrl = ar.take<Ctrl>(1);
     b.ctrl2 = ar.take<Ctrl>(1);
@@ -222,12 +246,13 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
     const bool f64 = sizeof(C) == 8;
     const int rb_grid = rowblock_max_grid<T>(W);
     const bool two = c.p.two_pass != 0;
+    const int qbatch = quad_batch(c.quad, M, m);
     Arena dry;
     CblBufs<T> b{};
-    plan_cbl<T>(dry, b, n, M, W, m, rb_grid, two);
+    plan_cbl<T>(dry, b, n, M, W, m, rb_grid, two, qbatch);
     Arena ar;
     KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
-    plan_cbl<T>(ar, b, n, M, W, m, rb_grid, two);
+    plan_cbl<T>(ar, b, n, M, W, m, rb_grid, two, qbatch);
     auto body = [&]() -> int {
         const double lam = c.g->lambda;
         const double tau_inv = f64 ? 1e-12 : 1e-6;
@@ -360,7 +385,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                     KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam, d, b.V0, b.V1, b.V2, Ucur, b.ctrl_chk, c.s));
                 } else {
                     KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, Ucur,
-                                            b.ctrl_chk, c.s));
+                                            b.ctrl_chk, c.s, c.quad, b.qscr, qbatch));
                 }
                 KB_TRY(launch_conv_check(Ucur, Uprev, M, b.ctrl_chk, b.chk_prev, c.p.tol, b.ctrl, c.s));
                 ++nchk;
@@ -372,7 +397,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam, d, b.V0, b.V1, b.V2, b.U, b.ctrl, c.s));
         } else {
             KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, b.U,
-                                    b.ctrl, c.s));
+                                    b.ctrl, c.s, c.quad, b.qscr, qbatch));
         }
         KB_TRY(launch_check_projected(b.U, int64_t(m) * M * M, projected_bound(c), b.ctrl, c.s));
         KB_TRY(launch_u_convert<C>(b.U, M, W, m, b.Ut, b.ctrl, c.s));
@@ -449,6 +474,7 @@ template <typename T>
 struct LzBufs {
     T *basis;
     double *parts, *sigma, *alpha, *beta, *work;
+    double *qwork;                    // fractional spline factor: 2 m nodes per column
     int32_t *alive;
     double *c1, *c2, *aupd, *omega;   // c1, c2, aupd: one row of W per step
     Ctrl *ctrl, *ctrl2;
@@ -457,7 +483,7 @@ struct LzBufs {
 };
 
 template <typename T>
-void plan_lz(Arena &ar, LzBufs<T> &b, int64_t n, int W, int m, int pgrid, bool two_pass) {
+void plan_lz(Arena &ar, LzBufs<T> &b, int64_t n, int W, int m, int pgrid, bool two_pass, int nquad) {
     // two-pass: three rotating blocks; the coefficients of every step are kept for the replay
     b.basis = ar.take<T>(size_t(two_pass ? 3 : m + 1) * n * W);
     b.parts = ar.take<double>(size_t(pgrid) * W);
@@ -465,6 +491,7 @@ void plan_lz(Arena &ar, LzBufs<T> &b, int64_t n, int W, int m, int pgrid, bool t
     b.alpha = ar.take<double>(size_t(m + 1) * W);
     b.beta = ar.take<double>(size_t(m + 1) * W);
     b.work = ar.take<double>(size_t(W) * 4 * m);
+    b.qwork = nquad > 0 ? ar.take<double>(size_t(W) * 2 * m * nquad) : nullptr;
     b.alive = ar.take<int32_t>(W);
     b.c1 = ar.take<double>(size_t(m + 1) * W);
     b.c2 = ar.take<double>(size_t(m + 1) * W);
@@ -483,21 +510,29 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
     const int W = width_for(M);
     const bool f64 = sizeof(T) == 8;
     const int pgrid = std::max(spmm_max_grid<T>(W), axpy_max_grid());
-    ChebCoef cc{};
+    auto tc = std::make_unique<TriCoef>();
+    int nquad = 0;
     if (c.phi == KB_PHI_EXP) {
         const std::vector<double> d = exp_series_coeffs(c.p.t, c.g->lambda, 1e-17);
         if (int(d.size()) > ChebCoef::CAP)
             return fail(KB_ERR_UNSUPPORTED, "t * Lambda too large for the tridiagonal Chebyshev series");
-        cc.n = int(d.size());
-        for (int j = 0; j < cc.n; ++j) cc.d[j] = d[j];
+        tc->cc.n = int(d.size());
+        for (int j = 0; j < tc->cc.n; ++j) tc->cc.d[j] = d[j];
+    } else {
+        tc->q.n = 0;
+        tc->q.s_int = c.s_int;
+        if (c.quad) {
+            tc->q = *c.quad;
+            nquad = c.quad->n;
+        }
     }
     const bool two = c.p.two_pass != 0;
     Arena dry;
     LzBufs<T> b{};
-    plan_lz<T>(dry, b, n, W, m, pgrid, two);
+    plan_lz<T>(dry, b, n, W, m, pgrid, two, nquad);
     Arena ar;
     KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
-    plan_lz<T>(ar, b, n, W, m, pgrid, two);
+    plan_lz<T>(ar, b, n, W, m, pgrid, two, nquad);
     auto body = [&]() -> int {
         const double thresh = (f64 ? 1e-12 : 1e-6) * c.g->lambda;
         KB_TRY(launch_ctrl_init(b.ctrl, m, c.s));
@@ -547,7 +582,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
                                        b.ctrl, c.s));
         }
         KB_TRY(launch_tridiag_phi(W, M, m, gbl ? 1 : 0, b.alpha, b.beta, b.sigma, int(c.phi),
-                                  c.p.eps, c.s_int, c.g->lambda, cc, b.omega, b.work, b.ctrl,
+                                  c.p.eps, c.s_int, c.g->lambda, *tc, b.omega, b.work, b.qwork, b.ctrl,
                                   projected_bound(c), c.s));
         if (!two) {
             KB_TRY(launch_assemble_diag<T>(W, b.basis, bs, m, b.omega, n, Y, ldy, M, M, tg, c.s));
@@ -712,13 +747,13 @@ int run_cheb(Common &c, bool squared, const int32_t *nodes, int M, int m, float 
 
 // Scratch bytes of one solve (the same plans the runs allocate).
 template <typename T>
-size_t workspace_bytes_t(int64_t n, kb_method method, int M, int m, bool two) {
+size_t workspace_bytes_t(int64_t n, kb_method method, int M, int m, bool two, const QuadRule *q) {
     Arena dry;
     const int W = width_for(M);
     switch (method) {
         case KB_CBL: {
             CblBufs<T> b{};
-            plan_cbl<T>(dry, b, n, M, W, m, rowblock_max_grid<T>(W), two);
+            plan_cbl<T>(dry, b, n, M, W, m, rowblock_max_grid<T>(W), two, quad_batch(q, M, m));
             break;
         }
         case KB_GBL:
@@ -727,7 +762,8 @@ size_t workspace_bytes_t(int64_t n, kb_method method, int M, int m, bool two) {
             const int Mg = method == KB_SBL ? std::min(M, sizeof(T) == 8 ? 64 : 128) : M;
             const int Wg = width_for(Mg);
             LzBufs<T> b{};
-            plan_lz<T>(dry, b, n, Wg, m, std::max(spmm_max_grid<T>(Wg), axpy_max_grid()), two);
+            plan_lz<T>(dry, b, n, Wg, m, std::max(spmm_max_grid<T>(Wg), axpy_max_grid()), two,
+                       q ? q->n : 0);
             break;
         }
         case KB_CHEB:
@@ -780,9 +816,9 @@ int validate(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
     if (int rc = validate_phi(phi, *params)) return rc;
     *s_int = 0;
     if (phi == KB_PHI_SPLINE && (method == KB_CBL || method == KB_GBL || method == KB_SBL)) {
-        if (params->s != std::floor(params->s) || params->s > 64)
-            return fail(KB_ERR_UNSUPPORTED, "Lanczos methods support integer s <= 64 only");
-        *s_int = int(params->s);
+        // floor(s) block solves with eps I + H_m, the fractional rest by quadrature
+        if (params->s >= 65) return fail(KB_ERR_UNSUPPORTED, "Lanczos methods support s < 65");
+        *s_int = int(std::floor(params->s));
     }
     if (method == KB_CBL && phi == KB_PHI_EXP && std::fabs(params->t) * g->lambda > 2e5)
         return fail(KB_ERR_UNSUPPORTED, "t * Lambda too large for the Chebyshev projected solve");
@@ -802,7 +838,11 @@ int apply_device(kb_graph *g, kb_method method, kb_phi phi, const kb_params *par
     DeviceGuard dg;
     KB_CUDA_TRY(dg.set(g->device));
     ensure_pool(g->device);
+    auto quad = std::make_unique<QuadRule>();
+    rc = quad_setup(g, method, phi, *params, *quad);
+    if (rc) return rc;
     Common c{g, phi, *params, s_int, static_cast<cudaStream_t>(stream), 0, nullptr, true};
+    if (quad->n > 0) c.quad = quad.get();
     // exact restriction of the per-step kernels to rows reached from W (hop distances are
     // kept in 8 bits)
     c.frontier = !params->no_frontier && m <= FRONTIER_MAX_HOPS;
@@ -923,10 +963,15 @@ extern "C" int kb_workspace_bytes(kb_graph *g, kb_method method, kb_phi phi, con
         int rc = validate(g, method, phi, params, dummy.data(), M, m, &probe, &s_int);
         if (rc) return rc;
         const int64_t n = g->dev.n;
+        auto quad = std::make_unique<QuadRule>();
+        rc = quad_setup(g, method, phi, *params, *quad);
+        if (rc) return rc;
+        const QuadRule *q = quad->n > 0 ? quad.get() : nullptr;
+        const bool two = params->two_pass != 0;
         switch (params->basis) {
-            case KB_F64: *bytes = workspace_bytes_t<double>(n, method, M, m, params->two_pass != 0); break;
-            case KB_BF16: *bytes = workspace_bytes_t<__nv_bfloat16>(n, method, M, m, params->two_pass != 0); break;
-            default: *bytes = workspace_bytes_t<float>(n, method, M, m, params->two_pass != 0); break;
+            case KB_F64: *bytes = workspace_bytes_t<double>(n, method, M, m, two, q); break;
+            case KB_BF16: *bytes = workspace_bytes_t<__nv_bfloat16>(n, method, M, m, two, q); break;
+            default: *bytes = workspace_bytes_t<float>(n, method, M, m, two, q); break;
         }
         return KB_OK;
     } catch (...) {

@@ -9,7 +9,11 @@
 //             functions), by the three-term recurrence on the block vectors V_j.  V_j is
 //             supported on block rows 0..j, so iteration j touches only j+2 block rows.
 //   * spline: for integer s, s solves with the SPD block tridiagonal eps I + H_m through
-//             its block Cholesky factorisation (block Thomas algorithm).
+//             its block Cholesky factorisation (block Thomas algorithm).  For non-integer s
+//             the fractional factor (eps I + H_m)^{-alpha} F_1 is the quadrature sum
+//             sum_k W_k (sigma_k I + H_m)^{-1} F_1 over real shifts sigma_k > eps
+//             (quadrature.cu), one block Cholesky factorisation and solve per node, the nodes
+//             in parallel (one CTA each), followed by floor(s) solves with eps I + H_m.
 // Both give the same U as the spectral evaluation assumed in Section 7, up to FP64
 // rounding (the Chebyshev series is truncated below 1e-17 relative).
 #include "kb_internal.cuh"
@@ -95,9 +99,10 @@ __device__ void chol_lower_inplace(double *A, int M) {
     }
 }
 
+// rhs_in_u: U already holds the right-hand side (steps blocks); else U starts as F_1.
 __global__ void __launch_bounds__(1024)
 k_bt_spline(const double *Hd, const double *Hs, int M, double eps, int s_int, double *Ld,
-            double *Ls, double *Yw, double *U, const Ctrl *ctrl) {
+            double *Ls, double *Yw, double *U, const Ctrl *ctrl, int rhs_in_u) {
     const int steps = ctrl->steps;
     const int64_t MM = int64_t(M) * M;
     // factor eps I + H = L L^T, L block lower bidiagonal (Ld diagonal, Ls sub-diagonal blocks)
@@ -128,11 +133,13 @@ k_bt_spline(const double *Hd, const double *Hs, int M, double eps, int s_int, do
         }
         __syncthreads();
     }
-    // U = F_1, then s_int times U <- (eps I + H)^{-1} U
-    for (int idx = threadIdx.x; idx < steps * M * M; idx += blockDim.x) {
-        const int64_t blk = idx / MM;
-        const int i = int((idx / M) % M), j = int(idx % M);
-        U[idx] = (blk == 0 && i == j) ? 1.0 : 0.0;
+    // U = F_1 (unless it holds the right-hand side), then s_int times U <- (eps I + H)^{-1} U
+    if (!rhs_in_u) {
+        for (int idx = threadIdx.x; idx < steps * M * M; idx += blockDim.x) {
+            const int64_t blk = idx / MM;
+            const int i = int((idx / M) % M), j = int(idx % M);
+            U[idx] = (blk == 0 && i == j) ? 1.0 : 0.0;
+        }
     }
     __syncthreads();
     for (int rep = 0; rep < s_int; ++rep) {
@@ -174,6 +181,108 @@ k_bt_spline(const double *Hd, const double *Hs, int M, double eps, int s_int, do
     }
 }
 
+// ---------------------------------------------------------------- quadrature nodes (spline)
+// One CTA per quadrature node: Y = (sigma I + H)^{-1} F_1 through the block Cholesky
+// factorisation sigma I + H = L L^T (L block lower bidiagonal: diagonal blocks Ld_r lower
+// triangular, sub-diagonal blocks Ls_r = L_{r+1,r}), forward and backward block substitution.
+// The triangular solves give each thread one row (Ls) or one right-hand-side column (Y), so
+// they need no barrier inside a block.  Per-node scratch (bt_quad_node_doubles): Ld, Ls, Y
+// (mcap blocks of M x M each) and the reciprocal diagonals of the Ld blocks (mcap x M).
+constexpr int QN_THREADS = 128;
+
+__global__ void __launch_bounds__(QN_THREADS)
+k_bt_shift_solve(const double *__restrict__ Hd, const double *__restrict__ Hs, int M, int mcap,
+                 QuadRule q, int node0, double *scratch, const Ctrl *ctrl) {
+    const int node = node0 + int(blockIdx.x);
+    if (node >= q.n) return;
+    const int steps = ctrl->steps;
+    const double sigma = q.shift[node];
+    const int64_t MM = int64_t(M) * M;
+    double *Ld = scratch + int64_t(blockIdx.x) * int64_t(bt_quad_node_doubles(M, mcap));
+    double *Ls = Ld + int64_t(mcap) * MM;
+    double *Y = Ls + int64_t(mcap) * MM;
+    double *rd = Y + int64_t(mcap) * MM;
+    const int tid = threadIdx.x;
+    for (int r = 0; r < steps; ++r) {
+        // D_r = sigma I + H_rr - Ls_{r-1} Ls_{r-1}^T (lower triangle), then D_r = Ld_r Ld_r^T
+        double *D = Ld + r * MM;
+        const double *P = r > 0 ? Ls + (r - 1) * MM : nullptr;
+        for (int idx = tid; idx < M * M; idx += blockDim.x) {
+            const int i = idx / M, j = idx % M;
+            double v = 0.0;
+            if (j <= i) {
+                v = Hd[r * MM + idx] + (i == j ? sigma : 0.0);
+                if (P)
+                    for (int k = 0; k < M; ++k) v = fma(-P[i * M + k], P[j * M + k], v);
+            }
+            D[idx] = v;
+        }
+        __syncthreads();
+        chol_lower_inplace(D, M);
+        for (int i = tid; i < M; i += blockDim.x) rd[r * M + i] = 1.0 / D[i * M + i];
+        __syncthreads();
+        if (r + 1 < steps) {
+            // Ls_r = H_{r+1,r} D_r^{-T}: row i solves D_r x = (row i of H_{r+1,r})^T
+            const double *Hsub = Hs + r * MM;
+            double *Pn = Ls + r * MM;
+            for (int i = tid; i < M; i += blockDim.x)
+                for (int j = 0; j < M; ++j) {
+                    double v = Hsub[i * M + j];
+                    for (int k = 0; k < j; ++k) v = fma(-D[j * M + k], Pn[i * M + k], v);
+                    Pn[i * M + j] = v * rd[r * M + j];
+                }
+            __syncthreads();
+        }
+    }
+    // forward: Y_0 = D_0^{-1} I, Y_r = D_r^{-1} (-Ls_{r-1} Y_{r-1}); one column per thread
+    for (int r = 0; r < steps; ++r) {
+        const double *D = Ld + r * MM;
+        const double *P = r > 0 ? Ls + (r - 1) * MM : nullptr;
+        const double *Yp = r > 0 ? Y + (r - 1) * MM : nullptr;
+        double *Yr = Y + r * MM;
+        for (int c = tid; c < M; c += blockDim.x)
+            for (int i = 0; i < M; ++i) {
+                double v = (r == 0 && i == c) ? 1.0 : 0.0;
+                if (P)
+                    for (int k = 0; k < M; ++k) v = fma(-P[i * M + k], Yp[k * M + c], v);
+                for (int k = 0; k < i; ++k) v = fma(-D[i * M + k], Yr[k * M + c], v);
+                Yr[i * M + c] = v * rd[r * M + i];
+            }
+        __syncthreads();
+    }
+    // backward: U_r = D_r^{-T} (Y_r - Ls_r^T U_{r+1}), in place in Y
+    for (int r = steps - 1; r >= 0; --r) {
+        const double *D = Ld + r * MM;
+        const double *P = r + 1 < steps ? Ls + r * MM : nullptr;
+        const double *Un = r + 1 < steps ? Y + (r + 1) * MM : nullptr;
+        double *Yr = Y + r * MM;
+        for (int c = tid; c < M; c += blockDim.x)
+            for (int i = M - 1; i >= 0; --i) {
+                double v = Yr[i * M + c];
+                if (P)
+                    for (int k = 0; k < M; ++k) v = fma(-P[k * M + i], Un[k * M + c], v);
+                for (int k = i + 1; k < M; ++k) v = fma(-D[k * M + i], Yr[k * M + c], v);
+                Yr[i * M + c] = v * rd[r * M + i];
+            }
+        __syncthreads();
+    }
+}
+
+// U += sum_{j < nb} W_{node0+j} Y_j over the steps blocks, in a fixed order (deterministic).
+__global__ void __launch_bounds__(256)
+k_quad_accumulate(const double *__restrict__ scratch, int M, int mcap, int nb, QuadRule q, int node0,
+                  double *U, const Ctrl *ctrl) {
+    const int64_t cnt = int64_t(ctrl->steps) * M * M;
+    const int64_t per = int64_t(bt_quad_node_doubles(M, mcap));
+    const int64_t yoff = 2 * int64_t(mcap) * M * M;
+    for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < cnt;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        double acc = U[idx];
+        for (int j = 0; j < nb; ++j) acc = fma(q.weight[node0 + j], scratch[j * per + yoff + idx], acc);
+        U[idx] = acc;
+    }
+}
+
 }  // namespace
 
 int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
@@ -207,12 +316,26 @@ int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
 
 int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double eps, int s_int,
                      double *Ld, double *Ls, double *Yw, double *U, const Ctrl *ctrl,
-                     cudaStream_t s) {
-    (void)m;
+                     cudaStream_t s, const QuadRule *q, double *qscr, int qbatch) {
     prof_begin(KernelClass::PROJECTED, s);
-    k_bt_spline<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, s_int, Ld, Ls, Yw, U, ctrl);
+    int launches = 1;
+    if (q && q->n > 0) {
+        if (!qscr || qbatch < 1) return fail(KB_ERR_ARG, "spline quadrature without scratch");
+        KB_CUDA_TRY(cudaMemsetAsync(U, 0, sizeof(double) * size_t(m) * M * M, s));
+        const int acc_grid = int(std::min<int64_t>((int64_t(m) * M * M + 255) / 256, 4 * int64_t(num_sms())));
+        for (int j0 = 0; j0 < q->n; j0 += qbatch) {
+            const int nb = std::min(qbatch, q->n - j0);
+            k_bt_shift_solve<<<nb, QN_THREADS, 0, s>>>(Hd, Hs, M, m, *q, j0, qscr, ctrl);
+            k_quad_accumulate<<<std::max(acc_grid, 1), 256, 0, s>>>(qscr, M, m, nb, *q, j0, U, ctrl);
+            launches += 2;
+        }
+        if (s_int > 0) k_bt_spline<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, s_int, Ld, Ls, Yw, U, ctrl, 1);
+        else --launches;
+    } else {
+        k_bt_spline<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, s_int, Ld, Ls, Yw, U, ctrl, 0);
+    }
     KB_CUDA_TRY(cudaGetLastError());
-    prof_end(KernelClass::PROJECTED, s, 0, 0);
+    prof_end(KernelClass::PROJECTED, s, 0, 0, launches);
     return 0;
 }
 

@@ -641,9 +641,10 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m
                                                              const double *beta,
                                                              const double *sigma, int phi_kind,
                                                              double eps, int s_int, double lam,
-                                                             ChebCoef cc, double *omega,
-                                                             double *work, Ctrl *ctrl,
-                                                             double bound) {
+                                                             TriCoef tc, double *omega,
+                                                             double *work, double *qwork,
+                                                             Ctrl *ctrl, double bound) {
+    const ChebCoef &cc = tc.cc;
     const int c = blockIdx.x;
     const int ncol = gbl ? 1 : M;
     if (c >= ncol) {
@@ -698,23 +699,52 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m
             __syncthreads();
             double *t = pp; pp = pc; pc = pn; pn = t;
         }
-    } else if (threadIdx.x == 0) {
-        // (eps I + T) = L U: v0 = modified super-diagonal, v2 = reciprocal pivots (once);
-        // then s_int forward / backward sweeps from rhs = e_1
-        double den = eps + a_of(0);
-        v2[0] = 1.0 / den;
-        v0[0] = (s > 1) ? b_of(1) * v2[0] : 0.0;
-        for (int k = 1; k < s; ++k) {
-            den = eps + a_of(k) - b_of(k) * v0[k - 1];
-            v2[k] = 1.0 / den;
-            v0[k] = (k + 1 < s) ? b_of(k + 1) * v2[k] : 0.0;
+    } else {
+        const QuadRule &q = tc.q;
+        if (q.n > 0) {
+            // fractional factor: u = sum_j W_j (sigma_j I + T)^{-1} e_1, one node per thread
+            // (Thomas algorithm: modified super-diagonal in cq, solution in xq), then the
+            // weighted sum per row in a fixed order
+            double *qw = qwork + int64_t(c) * 2 * m * q.n;
+            for (int j = threadIdx.x; j < q.n; j += blockDim.x) {
+                double *cq = qw + int64_t(j) * 2 * m, *xq = cq + m;
+                const double sg = q.shift[j];
+                double piv = 1.0 / (sg + a_of(0));
+                cq[0] = (s > 1) ? b_of(1) * piv : 0.0;
+                xq[0] = piv;
+                for (int k = 1; k < s; ++k) {
+                    piv = 1.0 / (sg + a_of(k) - b_of(k) * cq[k - 1]);
+                    cq[k] = (k + 1 < s) ? b_of(k + 1) * piv : 0.0;
+                    xq[k] = -b_of(k) * xq[k - 1] * piv;
+                }
+                for (int k = s - 2; k >= 0; --k) xq[k] -= cq[k] * xq[k + 1];
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < s; k += blockDim.x) {
+                double acc = 0.0;
+                for (int j = 0; j < q.n; ++j) acc = fma(q.weight[j], qw[int64_t(j) * 2 * m + m + k], acc);
+                u[k] = acc;
+            }
+            __syncthreads();
         }
-        u[0] = 1.0;
-        for (int rep = 0; rep < s_int; ++rep) {
-            v1[0] = u[0] * v2[0];
-            for (int k = 1; k < s; ++k) v1[k] = (u[k] - b_of(k) * v1[k - 1]) * v2[k];
-            u[s - 1] = v1[s - 1];
-            for (int k = s - 2; k >= 0; --k) u[k] = v1[k] - v0[k] * u[k + 1];
+        if (threadIdx.x == 0) {
+            // (eps I + T) = L U: v0 = modified super-diagonal, v2 = reciprocal pivots (once);
+            // then s_int forward / backward sweeps from rhs = e_1 (or from the fractional factor)
+            double den = eps + a_of(0);
+            v2[0] = 1.0 / den;
+            v0[0] = (s > 1) ? b_of(1) * v2[0] : 0.0;
+            for (int k = 1; k < s; ++k) {
+                den = eps + a_of(k) - b_of(k) * v0[k - 1];
+                v2[k] = 1.0 / den;
+                v0[k] = (k + 1 < s) ? b_of(k + 1) * v2[k] : 0.0;
+            }
+            if (q.n == 0) u[0] = 1.0;
+            for (int rep = 0; rep < s_int; ++rep) {
+                v1[0] = u[0] * v2[0];
+                for (int k = 1; k < s; ++k) v1[k] = (u[k] - b_of(k) * v1[k - 1]) * v2[k];
+                u[s - 1] = v1[s - 1];
+                for (int k = s - 2; k >= 0; --k) u[k] = v1[k] - v0[k] * u[k + 1];
+            }
         }
     }
     __syncthreads();
@@ -1118,7 +1148,7 @@ int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, 
 
 int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const double *beta,
                        const double *sigma, int phi_kind, double eps, int s_int, double lam,
-                       const ChebCoef &cc, double *omega, double *work, Ctrl *ctrl,
+                       const TriCoef &tc, double *omega, double *work, double *qwork, Ctrl *ctrl,
                        double bound, cudaStream_t s) {
     prof_begin(KernelClass::PROJECTED, s);
     const size_t smem = m <= TRI_SMEM_M ? sizeof(double) * 6 * size_t(m) : 0;
@@ -1126,8 +1156,8 @@ int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const 
         k_tridiag_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(double) * 6 * TRI_SMEM_M));
     (void)attr;
     k_tridiag_phi<<<gbl ? 1 : W, TRI_THREADS, smem, s>>>(W, M, m, gbl, alpha, beta, sigma,
-                                                         phi_kind, eps, s_int, lam, cc, omega,
-                                                         work, ctrl, bound);
+                                                         phi_kind, eps, s_int, lam, tc, omega,
+                                                         work, qwork, ctrl, bound);
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::PROJECTED, s, 0, 0);
     return 0;

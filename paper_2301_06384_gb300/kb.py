@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
     L.kb_cheb_lobatto_coeffs.restype = ctypes.c_int
     L.kb_exp_series_coeffs.argtypes = [dbl, dbl, dbl, vp, i32, P(i32)]
     L.kb_exp_series_coeffs.restype = ctypes.c_int
+    L.kb_spline_quadrature.argtypes = [dbl, dbl, dbl, dbl, vp, vp, i32, P(i32), P(i32)]
+    L.kb_spline_quadrature.restype = ctypes.c_int
     L.kb_profile_enable.argtypes = [i32]
     L.kb_profile_enable.restype = ctypes.c_int
     L.kb_profile_read.argtypes = [P(kb_kernel_stats), i32, P(i32)]
@@ -257,6 +259,17 @@ def kb_exp_series_coeffs(t: float, lam: float, tol: float = 1e-17, cap: int = 10
     _check(lib().kb_exp_series_coeffs(float(t), float(lam), float(tol), d.ctypes.data, int(cap),
                                       ctypes.byref(cnt)))
     return d[:cnt.value].copy()
+
+
+def kb_spline_quadrature(eps: float, s: float, lam: float, tol: float = 1e-14, cap: int = 4096):
+    """(shift, weight, s_int) of the quadrature form of (eps + lambda)^{-s} on [0, lam]."""
+    sh = np.zeros(cap, dtype=np.float64)
+    w = np.zeros(cap, dtype=np.float64)
+    cnt = ctypes.c_int32()
+    si = ctypes.c_int32()
+    _check(lib().kb_spline_quadrature(float(eps), float(s), float(lam), float(tol), sh.ctypes.data,
+                                      w.ctypes.data, int(cap), ctypes.byref(cnt), ctypes.byref(si)))
+    return sh[:cnt.value].copy(), w[:cnt.value].copy(), si.value
 
 
 def kb_profile_enable(on: bool = True):

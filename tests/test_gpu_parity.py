@@ -100,17 +100,37 @@ def test_rgg_exp_parity(kb, rgg, method, t):
     assert info["spmm_launches"] == 30
 
 
+@pytest.mark.parametrize("s", [2.0, 0.5, 1.5])
 @pytest.mark.parametrize("method", METHODS)
-def test_rgg_spline_parity(kb, rgg, method):
+def test_rgg_spline_parity(kb, rgg, method, s):
+    # (eps I + L)^{-s} for every s > 0 (Section 2.4): integer s by floor(s) block solves of
+    # the projected problem, the fractional rest of non-integer s by the quadrature over
+    # real shifts; the oracle evaluates phi(H_m) by its eigendecomposition
     nodes = synth.sample_nodes(rgg.n, 32, seed=3)
     with kb.Graph.from_csr(rgg) as G:
-        Y = _gpu(kb, G, method, "spline", nodes, 20, eps=0.1, s=2.0)
-        Y64 = _gpu(kb, G, method, "spline", nodes, 20, eps=0.1, s=2.0, basis="f64")
+        Y = _gpu(kb, G, method, "spline", nodes, 20, eps=0.1, s=s)
+        Y64 = _gpu(kb, G, method, "spline", nodes, 20, eps=0.1, s=s, basis="f64")
         lam = G.lambda_max
-    ref = _oracle(rgg, method, nodes, 20, "spline", eps=0.1, s=2.0)
+    ref = _oracle(rgg, method, nodes, 20, "spline", eps=0.1, s=s)
     err, err64 = _rel(Y, ref), _rel(Y64, ref)
-    check_err(f"rgg2e4 {method} spline eps=0.1 s=2 m=20 FP32", err, tol32("spline", lam, eps=0.1, s=2.0))
-    assert err64 < 1e-7
+    check_err(f"rgg2e4 {method} spline eps=0.1 s={s:g} m=20 FP32", err, tol32("spline", lam, eps=0.1, s=s))
+    check_err(f"rgg2e4 {method} spline eps=0.1 s={s:g} m=20 FP64", err64, 1e-7)
+
+
+@pytest.mark.parametrize("method", ["cbl", "gbl", "sbl"])
+@pytest.mark.parametrize("s", [0.3, 2.75])
+def test_noninteger_spline_small_eps_weighted(kb, method, s):
+    # a weighted hub-heavy graph with a small shift: (eps + Lambda) / eps ~ 1e5, where the
+    # quadrature needs its most nodes; FP64 mode against the oracle
+    g = synth.barabasi_albert_graph(3000, 5, seed=13, weighted=True)
+    nodes = synth.sample_nodes(g.n, 12, seed=14)
+    with kb.Graph.from_csr(g) as G:
+        Y64 = _gpu(kb, G, method, "spline", nodes, 14, eps=0.005, s=s, basis="f64")
+        Y = _gpu(kb, G, method, "spline", nodes, 14, eps=0.005, s=s, reorth=2 if method == "cbl" else 0)
+        lam = G.lambda_max
+    ref = _oracle(g, method, nodes, 14, "spline", eps=0.005, s=s)
+    check_err(f"ba3e3w {method} spline eps=0.005 s={s:g} m=14 FP64", _rel(Y64, ref), 1e-7)
+    check_err(f"ba3e3w {method} spline eps=0.005 s={s:g} m=14 FP32", _rel(Y, ref), tol32("spline", lam, eps=0.005, s=s))
 
 
 @pytest.mark.parametrize("method", ["cheb", "cheb2"])

@@ -32,7 +32,7 @@ def rgg():
 
 
 @pytest.mark.parametrize("phi,kw", [("exp", dict(t=0.5)), ("exp", dict(t=3.0)),
-                                    ("spline", dict(eps=0.5, s=2.0))])
+                                    ("spline", dict(eps=0.5, s=2.0)), ("spline", dict(eps=0.5, s=1.5))])
 def test_stopping_rule_matches_fixed_m(kb, rgg, phi, kw):
     import torch
     nodes = synth.sample_nodes(rgg.n, 32, seed=21)

@@ -106,6 +106,53 @@ def test_exp_series_reproduces_exponential(kb, t, lam):
     assert np.max(np.abs(T @ d - ref) / np.maximum(ref, 1e-300 + np.abs(ref).max())) < 1e-14
 
 
+@pytest.mark.parametrize("s", [0.5, 0.25, 0.9, 1.5, 2.3])
+@pytest.mark.parametrize("eps,lam", [(0.1, 20.0), (0.01, 60.0), (1e-3, 3000.0)])
+def test_spline_quadrature_reproduces_the_fractional_power(kb, eps, s, lam):
+    # (eps + lambda)^{-s} = (eps + lambda)^{-floor(s)} sum_k W_k / (sigma_k + lambda) on
+    # [0, Lambda], checked against pow at points the rule's own grid does not use
+    sh, w, s_int = kb.kb_spline_quadrature(eps, s, lam)
+    assert s_int == int(np.floor(s)) and np.all(sh > eps) and np.all(w > 0)
+    rng = np.random.default_rng(5)
+    lmb = np.concatenate([lam * rng.random(500), eps * np.expm1(np.log1p(lam / eps) * rng.random(500))])
+    approx = (eps + lmb) ** (-s_int) * (w[None, :] / (sh[None, :] + lmb[:, None])).sum(axis=1)
+    ref = (eps + lmb) ** (-s)
+    assert np.max(np.abs(approx - ref) / ref) < 1e-13
+    assert sh.size <= 240
+
+
+@pytest.mark.parametrize("alpha", [0.5, 0.2, 0.85])
+def test_spline_quadrature_nodes_are_gauss_jacobi(kb, alpha):
+    # the rule's nodes and weights, mapped back to [-1, 1] (t = c u^3, u = (1-x)/(1+x)), are
+    # the Gauss-Jacobi rule of the weight (1-x)^{3(1-alpha)-1} (1+x)^{3 alpha-1} (library
+    # reference: scipy.special.roots_jacobi)
+    from scipy.special import roots_jacobi
+    eps, lam = 0.02, 50.0
+    sh, w, _ = kb.kb_spline_quadrature(eps, 1.0 + alpha, lam)
+    c = np.sqrt(eps * (eps + lam))
+    u = np.cbrt((sh - eps) / c)
+    x = (1 - u) / (1 + u)
+    pre = c ** (1 - alpha) * 6 * np.sin(np.pi * alpha) / np.pi
+    wj = w * (1 + x) ** 3 / pre
+    order = np.argsort(x)
+    xr, wr = roots_jacobi(sh.size, 3 * (1 - alpha) - 1, 3 * alpha - 1)
+    # mapping a shift back to x loses digits where sigma - eps << eps (x near 1): compare
+    # the nodes where the map is well conditioned, the weights everywhere
+    ok = ((sh - eps) / eps > 1e-4)[order]
+    assert ok.sum() >= 0.9 * sh.size
+    assert np.max(np.abs(x[order] - xr)[ok]) < 1e-12
+    assert np.max(np.abs(wj[order] - wr) / wr.max()) < 1e-10
+
+
+def test_spline_quadrature_integer_s_and_errors(kb):
+    sh, w, s_int = kb.kb_spline_quadrature(0.1, 3.0, 10.0)
+    assert sh.size == 0 and s_int == 3
+    for args in [(0.0, 1.5, 10.0), (0.1, -1.0, 10.0), (0.1, 1.5, 0.0), (float("inf"), 1.5, 1.0)]:
+        with pytest.raises(kb.KbError) as ei:
+            kb.kb_spline_quadrature(*args)
+        assert ei.value.code == -1
+
+
 def test_binding_struct_layouts_match_the_header(kb, tmp_path):
     # the ctypes mirrors of the ABI structs have the C sizes and field offsets (a plain C
     # program compiled against include/kb.h prints them; gcc, no CUDA)
