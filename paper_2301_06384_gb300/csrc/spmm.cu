@@ -66,15 +66,28 @@ template <> struct V4<double> {
     }
 };
 
+// Schedule parameters (compile-time; the defaults are the measured best on the RGG bench).
+#ifndef KB_SPMM_CAP
+#define KB_SPMM_CAP 4096
+#endif
+#ifndef KB_SPMM_VPL
+#define KB_SPMM_VPL 2
+#endif
+#ifndef KB_SPMM_U
+#define KB_SPMM_U 2
+#endif
+#ifndef KB_SPMM_IDX32
+#define KB_SPMM_IDX32 0
+#endif
 constexpr int SPMM_THREADS = 256;
 constexpr int WARPS = SPMM_THREADS / 32;
-constexpr int CAP = 4096;       // staged column indices per tile
-constexpr int VPL = 2;          // 16-byte vectors per lane (8 elements of a row)
-constexpr int U = 2;            // neighbour rows gathered per lane before use
+constexpr int CAP = KB_SPMM_CAP;   // staged column indices per tile
+constexpr int VPL = KB_SPMM_VPL;   // 16-byte vectors per lane (4 VPL elements of a row)
+constexpr int U = KB_SPMM_U;       // neighbour rows gathered per lane before use
 
 template <int W>
 struct SpmmGeo {
-    static constexpr int LPR = W / (4 * VPL);            // lanes per row
+    static constexpr int LPR = W / (4 * VPL) < 1 ? 1 : W / (4 * VPL);   // lanes per row
     static constexpr int RPW = 32 / LPR;                 // rows per warp
     static constexpr int NG = WARPS * RPW;               // lane groups per CTA
     static constexpr int RPG = W >= 64 ? 4 : (W == 32 ? 2 : 1);   // rows per group per tile
@@ -119,12 +132,14 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
     using C = typename Cmp<T>::type;   // arithmetic type
     constexpr int LPR = G::LPR, RPW = G::RPW, NG = G::NG, TR = G::TR, RPG = G::RPG;
     if (e.ctrl && e.ctrl->stop) return;
+    // (arrays a variant does not use take one element: shared memory left to L1 caches the
+    // gathered rows)
     __shared__ int s_rp[TR + 1];
     __shared__ int s_col[CAP];
-    __shared__ float s_w[CAP];
+    __shared__ float s_w[WGT ? CAP : 1];
     __shared__ __align__(16) C s_coef[5][W];       // c1 hi, c1 lo, c0, c2 hi, c2 lo
     __shared__ C s_sc[2];                          // s3, wE in the arithmetic type
-    __shared__ double s_dot[WARPS][W];
+    __shared__ double s_dot[DOT ? WARPS : 1][W];
     __shared__ unsigned long long s_cnt[2];       // rows, stored nonzeros processed
     if (threadIdx.x == 0) {
         s_sc[0] = C(e.s3);
@@ -265,26 +280,31 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                 for (int q = 0; q < 4; ++q) acc[v][q] = C(0);
             }
             for (int p = beg; p < end; p += U) {
+                // slots past the row's end gather the row itself (weight 0): x_i - x_i adds
+                // an exact zero, so the unrolled body needs no per-slot branch
                 V4<T> xj[U][VPL];
                 C wv[U];
+                int jj[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    if (p + u < end) {
-                        const int j = staged ? s_col[p + u] : __ldg(g.col + base + p + u);
-                        wv[u] = WGT ? C(staged ? s_w[p + u] : __ldg(g.w + base + p + u)) : C(1);
-#pragma unroll
-                        for (int v = 0; v < VPL; ++v) xj[u][v] = V4<T>::load(x + int64_t(j) * W + KB_COL(v));
-                    }
+                    const bool in = p + u < end;
+                    jj[u] = in ? (staged ? s_col[p + u] : __ldg(g.col + base + p + u)) : int(row);
+                    wv[u] = WGT ? (in ? C(staged ? s_w[p + u] : __ldg(g.w + base + p + u)) : C(0)) : C(1);
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    if (p + u < end)
 #pragma unroll
-                        for (int v = 0; v < VPL; ++v)
+                    for (int v = 0; v < VPL; ++v)
+                        xj[u][v] = V4<T>::load(KB_SPMM_IDX32 ? x + (unsigned(jj[u]) * unsigned(W) + unsigned(KB_COL(v)))
+                                                             : x + int64_t(jj[u]) * W + KB_COL(v));
 #pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                acc[v][q] = WGT ? fma(wv[u], xi[v].v[q] - xj[u][v].v[q], acc[v][q])
-                                                : acc[v][q] + (xi[v].v[q] - xj[u][v].v[q]);
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            acc[v][q] = WGT ? fma(wv[u], xi[v].v[q] - xj[u][v].v[q], acc[v][q])
+                                            : acc[v][q] + (xi[v].v[q] - xj[u][v].v[q]);
             }
             const C r = g.rdiag ? C(__ldg(g.rdiag + row)) : C(0);
             const int mk = e.marker ? __ldg(e.marker + row) : -1;

@@ -143,6 +143,32 @@ def test_ba_4m_spline_cbl_full_reorth(kb):
     assert w.min() > 0
 
 
+def test_ba_c3_shape_against_the_oracle(kb):
+    """The full-size BA case above cannot hold an FP64 oracle; this is the same kernel and
+    method at a size the host oracle finishes in about a minute: weighted Barabasi-Albert
+    (5 edges per node, weights U[0.5, 1.5]) with n = 2e4, M = 128, (0.01 I + L)^{-2},
+    cbl m = 60 with full reorthogonalisation (mM = 7680), element by element against the
+    FP64 oracle with full reorthogonalisation.  Bars: the FP32 path's conditioning-aware
+    bound kappa Lambda u32 (kappa = s / eps = 200), printed beside the 1e-6 gate (the plain
+    FP64 mode takes blocks of at most 64 columns, so it has no M = 128 counterpart)."""
+    import torch
+    U32 = 2.0 ** -24
+    g = synth.barabasi_albert_graph(20_000, 5, seed=15, weighted=True)
+    nodes = synth.sample_nodes(g.n, 128, seed=16)
+    L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
+    ref = krylov.apply("cbl", L, nodes, 60, "spline", eps=0.01, s=2.0, reorth=True).Y
+    kw = dict(eps=0.01, s=2.0, reorth=1)
+    with kb.Graph.from_csr(g) as G:
+        lam = G.lambda_max
+        Y = kb.kernel_columns(G, "cbl", "spline", nodes, 60, **kw)
+        torch.cuda.synchronize()
+        Y = Y.cpu().numpy().astype(np.float64)
+    err = _rel(Y, ref)
+    bar = 200.0 * lam * U32
+    print(f"ERRLOG ba2e4w cbl spline eps=0.01 s=2 M=128 m=60 reorth=1 FP32: {err:.3e} (bar {bar:.2e})")
+    assert err < bar
+
+
 # ---------------------------------------------------------------- precision sweep, 128^3 grid
 @pytest.mark.parametrize("method,M,ms", [("cbl", 32, (20, 40, 80)), ("sbl", 128, (20, 40))])
 def test_grid_128cubed_precision_sweep(kb, grid128, method, M, ms):

@@ -234,12 +234,12 @@ def test_breakdown_at_a_middle_pivot(kb, M):
     # block X is exactly zero while the others are not; the Cholesky factorisation of X^T X
     # meets a zero pivot at index 1 <= M - 2, found by the look-ahead warp while the other
     # warps still update the trailing rows
-    b = synth.barabasi_albert_graph(3000, 5, seed=12)   # connected: no small components
+    b = synth.random_geometric_graph(3001, 9, seed=5)   # the graph of test_ragged_widths
     rows = np.repeat(np.arange(b.n), np.diff(b.rowptr))
     up = rows < b.col
-    n = b.n + 1                                            # node n - 1 has no edges
+    n = b.n + 1                                          # node n - 1 has no edges
     g = synth.from_edges(n, rows[up], b.col[up])
-    nodes = [int(x) for x in synth.sample_nodes(b.n, M, seed=11)]
+    nodes = [int(x) for x in synth.sample_nodes(b.n, M, seed=M)]
     nodes[1] = n - 1
     with kb.Graph.from_csr(g) as G:
         for _ in range(2):   # the same status twice: the context survives the breakdown
