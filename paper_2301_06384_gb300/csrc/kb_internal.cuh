@@ -183,6 +183,10 @@ struct LinEpi {
                                       // all lie beyond the limit skips them
     int limit = 0;                    // process tiles with tgen <= limit
     int zero_inactive = 0;            // write zeros for skipped tiles (final output)
+    const int32_t *alist = nullptr;   // with tgen: the 32-row frontier tiles with tgen <= limit in
+    const int32_t *acount = nullptr;  // increasing order and their number (device); the kernel
+                                      // then visits only the row tiles they cover (ignored when
+                                      // zero_inactive is set: every tile is written then)
     ProfCount prof;
 };
 
@@ -226,6 +230,8 @@ struct RowArgs {
     const Ctrl *ctrl = nullptr;
     const int32_t *tgen = nullptr;    // frontier tiles (nullptr: all rows)
     int limit = 0;                    // process tiles with tgen <= limit (ASM: all tiles)
+    const int32_t *alist = nullptr;   // as LinEpi::alist (not used by ASM, which writes every
+    const int32_t *acount = nullptr;  // row of its output)
     int kbase = 0;                    // ASM: index of the first block (frontier reach)
     int accumulate = 0;               // ASM: y += product (the accumulator starts from y)
     ProfCount prof;

@@ -91,7 +91,8 @@ int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const 
 template <typename T>
 int launch_axpy_colnorm(int W, T *X, const T *P, const double *a, int64_t n, double *parts,
                         int *grid_out, const Ctrl *ctrl, const int32_t *tgen, int limit,
-                        int64_t M_alg, cudaStream_t s);
+                        int64_t M_alg, cudaStream_t s, const int32_t *alist = nullptr,
+                        const int32_t *acount = nullptr);
 int axpy_max_grid();
 template <typename T>
 int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const double *omega,
@@ -103,6 +104,10 @@ int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const 
 int launch_frontier_init(uint8_t *gen, int32_t *tgen, int64_t n, const int32_t *nodes, int M,
                          cudaStream_t s);
 int launch_frontier_expand(const GraphDev &g, uint8_t *gen, int32_t *tgen, int k, cudaStream_t s);
+// Compacts the 32-row frontier tiles with tgen <= limit into list (increasing tile order,
+// capacity ceil(n / 32)) and their number into *count; one CTA, deterministic.
+int launch_frontier_list(const int32_t *tgen, int64_t n, int limit, int32_t *list, int32_t *count,
+                         cudaStream_t s);
 template <typename T>
 int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ctrl, cudaStream_t s);
 

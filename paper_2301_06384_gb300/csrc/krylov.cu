@@ -204,6 +204,7 @@ struct CblBufs {
     Ctrl *ctrl, *ctrl2, *ctrl_chk;
     uint8_t *gen;
     int32_t *tgen;
+    int32_t *alist, *acount;   // active 32-row tiles of the current step (frontier)
 };
 
 template <typename T>
@@ -236,6 +237,8 @@ void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_g
     b.ctrl_chk = ar.take<Ctrl>(1);
     b.gen = ar.take<uint8_t>(size_t(n));
     b.tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
+    b.alist = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
+    b.acount = ar.take<int32_t>(1);
 }
 
 template <typename T>
@@ -289,7 +292,10 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             C *S1 = b.Rs1 + (k - 1) * WW, *S2 = b.Rs2 + (k - 1) * WW;
             C *Cl = b.Cloc + 2 * (k - 1) * WW;
             // Q_k is supported on rows within k-1 hops of W; L Q_k within k hops
-            if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+            if (c.frontier) {
+                KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                KB_TRY(launch_frontier_list(b.tgen, n, k, b.alist, b.acount, c.s));
+            }
             // block SpMM: W = L Q_k
             LinEpi<T> e;
             e.s1 = 1.0;
@@ -298,13 +304,15 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             e.tgen = tg;
             e.gen = tg ? b.gen : nullptr;
             e.limit = k;
+            e.alist = tg ? b.alist : nullptr;
+            e.acount = b.acount;
             KB_TRY(launch_spmm<T>(c.g->dev, W, Qk, e, c.s, nullptr, M, 0));
             ++c.spmm;
             // diagonal block: H_kk = Q_k^T L Q_k
             int grid = 0;
             RowArgs<T> pa;
             pa.n = n; pa.x = b.wbuf; pa.qa = Qk; pa.partials = b.parts; pa.ctrl = b.ctrl;
-            pa.tgen = tg; pa.limit = k;
+            pa.tgen = tg; pa.limit = k; pa.alist = tg ? b.alist : nullptr; pa.acount = b.acount;
             KB_TRY(launch_rowblock<T>(RB_PROJ, W, pa, c.s, &grid, M));
             KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
             KB_TRY(launch_hkk<C>(b.Gsum, M, W, b.Hd + size_t(k - 1) * M * M, Cb, b.ctrl, c.s));
@@ -314,7 +322,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             RowArgs<T> ua;
             ua.n = n; ua.x = b.wbuf; ua.qa = Qp; ua.ca = Bp; ua.qb = Qk; ua.cb = Cb;
             ua.out = X; ua.partials = b.parts; ua.ctrl = b.ctrl;
-            ua.tgen = tg; ua.limit = k;
+            ua.tgen = tg; ua.limit = k; ua.alist = tg ? b.alist : nullptr; ua.acount = b.acount;
             KB_TRY(launch_rowblock<T>(RB_UPD, W, ua, c.s, &grid, M));
             KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
             if (c.p.reorth == 2) {
@@ -327,14 +335,14 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                     if (!loc[j]) continue;
                     RowArgs<T> ra;
                     ra.n = n; ra.x = X; ra.qa = loc[j]; ra.partials = b.parts; ra.ctrl = b.ctrl;
-                    ra.tgen = tg; ra.limit = k;
+                    ra.tgen = tg; ra.limit = k; ra.alist = tg ? b.alist : nullptr; ra.acount = b.acount;
                     KB_TRY(launch_rowblock<T>(RB_PROJ, W, ra, c.s, &grid, M));
                     KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl, Cl + j * WW));
                 }
                 RowArgs<T> la;
                 la.n = n; la.x = X; la.qa = Qp; la.ca = Cl + WW; la.qb = Qk;
                 la.cb = Cl; la.out = X; la.partials = b.parts; la.ctrl = b.ctrl;
-                la.tgen = tg; la.limit = k;
+                la.tgen = tg; la.limit = k; la.alist = tg ? b.alist : nullptr; la.acount = b.acount;
                 KB_TRY(launch_rowblock<T>(RB_UPD, W, la, c.s, &grid, M));
                 KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
             }
@@ -347,7 +355,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                         RowArgs<T> ra;
                         ra.n = n; ra.x = X; ra.qa = b.basis + j * bs; ra.partials = b.parts;
                         ra.ctrl = b.ctrl;
-                        ra.tgen = tg; ra.limit = k;
+                        ra.tgen = tg; ra.limit = k; ra.alist = tg ? b.alist : nullptr; ra.acount = b.acount;
                         KB_TRY(launch_rowblock<T>(RB_PROJ, W, ra, c.s, &grid, M));
                         KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl,
                                                 b.Cstk + size_t(j) * W * W));
@@ -355,7 +363,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                     RowArgs<T> sa;
                     sa.n = n; sa.x = X; sa.basis = b.basis; sa.block_stride = bs; sa.nblk = k;
                     sa.ca = b.Cstk; sa.out = X; sa.partials = b.parts; sa.ctrl = b.ctrl;
-                    sa.tgen = tg; sa.limit = k;
+                    sa.tgen = tg; sa.limit = k; sa.alist = tg ? b.alist : nullptr; sa.acount = b.acount;
                     KB_TRY(launch_rowblock<T>(RB_ASMSUB, W, sa, c.s, &grid, M));
                     KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
                 }
@@ -365,14 +373,14 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                                   nullptr, b.ctrl, c.s));
             RowArgs<T> ma;
             ma.n = n; ma.x = X; ma.ca = S1; ma.out = X; ma.partials = b.parts; ma.ctrl = b.ctrl;
-            ma.tgen = tg; ma.limit = k;
+            ma.tgen = tg; ma.limit = k; ma.alist = tg ? b.alist : nullptr; ma.acount = b.acount;
             KB_TRY(launch_rowblock<T>(RB_MULGRAM, W, ma, c.s, &grid, M));
             KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
             KB_TRY(launch_chol<C>(b.Gsum, M, W, 2, k, inv_thresh2, piv2, b.R1, S2,
                                   b.Hs + size_t(k - 1) * M * M, Bk, b.ctrl, c.s));
             RowArgs<T> qa;
             qa.n = n; qa.x = X; qa.ca = S2; qa.out = X; qa.ctrl = b.ctrl;
-            qa.tgen = tg; qa.limit = k;
+            qa.tgen = tg; qa.limit = k; qa.alist = tg ? b.alist : nullptr; qa.acount = b.acount;
             KB_TRY(launch_rowblock<T>(RB_MUL, W, qa, c.s, &grid, M));
             // stopping rule: U_k at the check steps, compared with the previous check's
             if (c.p.tol > 0.0 && k < m && (k == 8 || k == 12 || k == 16 || k == 24 || k == 32 ||
@@ -428,7 +436,10 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                 int grid = 0;
                 KB_TRY(launch_rowblock<T>(RB_ASM, W, aa, c.s, &grid, M));
                 if (k == m) break;
-                if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                if (c.frontier) {
+                    KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                    KB_TRY(launch_frontier_list(b.tgen, n, k, b.alist, b.acount, c.s));
+                }
                 LinEpi<T> e;
                 e.s1 = 1.0;
                 e.out = b.wbuf;
@@ -436,13 +447,15 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                 e.tgen = tg;
                 e.gen = tg ? b.gen : nullptr;
                 e.limit = k;
+                e.alist = tg ? b.alist : nullptr;
+                e.acount = b.acount;
                 KB_TRY(launch_spmm<T>(c.g->dev, W, Qk, e, c.s, nullptr, M, 0));
                 ++c.spmm;
                 T *X = blk(k);
                 RowArgs<T> ua;
                 ua.n = n; ua.x = b.wbuf; ua.qa = Qp; ua.ca = k >= 2 ? b.Bs + (k - 2) * WW : nullptr;
                 ua.qb = Qk; ua.cb = b.Cbs + (k - 1) * WW;
-                ua.out = X; ua.partials = b.parts; ua.ctrl = b.ctrl2; ua.tgen = tg; ua.limit = k;
+                ua.out = X; ua.partials = b.parts; ua.ctrl = b.ctrl2; ua.tgen = tg; ua.limit = k; ua.alist = tg ? b.alist : nullptr; ua.acount = b.acount;
                 KB_TRY(launch_rowblock<T>(RB_UPD, W, ua, c.s, &grid, M));
                 if (c.p.reorth == 2) {
                     RowArgs<T> la = ua;
@@ -452,7 +465,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                 for (int pass = 0; pass < 2; ++pass) {
                     RowArgs<T> qa;
                     qa.n = n; qa.x = X; qa.ca = (pass == 0 ? b.Rs1 : b.Rs2) + (k - 1) * WW;
-                    qa.out = X; qa.ctrl = b.ctrl2; qa.tgen = tg; qa.limit = k;
+                    qa.out = X; qa.ctrl = b.ctrl2; qa.tgen = tg; qa.limit = k; qa.alist = tg ? b.alist : nullptr; qa.acount = b.acount;
                     KB_TRY(launch_rowblock<T>(RB_MUL, W, qa, c.s, &grid, M));
                 }
             }
@@ -480,6 +493,7 @@ struct LzBufs {
     Ctrl *ctrl, *ctrl2;
     uint8_t *gen;
     int32_t *tgen;
+    int32_t *alist, *acount;   // active 32-row tiles of the current step (frontier)
 };
 
 template <typename T>
@@ -501,6 +515,8 @@ void plan_lz(Arena &ar, LzBufs<T> &b, int64_t n, int W, int m, int pgrid, bool t
     b.ctrl2 = ar.take<Ctrl>(1);
     b.gen = ar.take<uint8_t>(size_t(n));
     b.tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
+    b.alist = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
+    b.acount = ar.take<int32_t>(1);
 }
 
 template <typename T>
@@ -555,12 +571,17 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
             T *Pk = blk(k - 1);
             T *Pp = k >= 2 ? blk(k - 2) : nullptr;
             T *X = blk(k);
-            if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+            if (c.frontier) {
+                KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                KB_TRY(launch_frontier_list(b.tgen, n, k, b.alist, b.acount, c.s));
+            }
             // X = L Q_k - h_{k,k-1} Q_{k-1}, with Q_k = sigma_k P_k; dots <P_k, X> per column
             LinEpi<T> e;
             e.tgen = tg;
             e.gen = tg ? b.gen : nullptr;
             e.limit = k;
+            e.alist = tg ? b.alist : nullptr;
+            e.acount = b.acount;
             e.a1 = b.c1 + int64_t(k - 1) * W;
             e.a2 = b.c2 + int64_t(k - 1) * W;
             e.s0 = 0.0;
@@ -576,7 +597,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
             if (k == m) break;
             int grid2 = 0;
             KB_TRY(launch_axpy_colnorm<T>(W, X, Pk, b.aupd + int64_t(k - 1) * W, n, b.parts, &grid2,
-                                          b.ctrl, tg, k, M, c.s));
+                                          b.ctrl, tg, k, M, c.s, tg ? b.alist : nullptr, b.acount));
             KB_TRY(launch_lanczos_beta(b.parts, grid2, W, M, gbl ? 1 : 0, k - 1, f64 ? 0 : 1, thresh, b.beta,
                                        b.sigma, b.alive, b.c1 + int64_t(k) * W, b.c2 + int64_t(k) * W,
                                        b.ctrl, c.s));
@@ -598,11 +619,16 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
                 T *Pk = blk(k - 1);
                 T *Pp = k >= 2 ? blk(k - 2) : nullptr;
                 T *X = blk(k);
-                if (c.frontier) KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                if (c.frontier) {
+                    KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                    KB_TRY(launch_frontier_list(b.tgen, n, k, b.alist, b.acount, c.s));
+                }
                 LinEpi<T> e;
                 e.tgen = tg;
                 e.gen = tg ? b.gen : nullptr;
                 e.limit = k;
+                e.alist = tg ? b.alist : nullptr;
+                e.acount = b.acount;
                 e.a1 = b.c1 + int64_t(k - 1) * W;
                 e.a2 = b.c2 + int64_t(k - 1) * W;
                 e.s0 = 0.0;
@@ -615,7 +641,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
                 ++c.spmm;
                 int grid2 = 0;
                 KB_TRY(launch_axpy_colnorm<T>(W, X, Pk, b.aupd + int64_t(k - 1) * W, n, b.parts, &grid2,
-                                              b.ctrl2, tg, k, M, c.s));
+                                              b.ctrl2, tg, k, M, c.s, tg ? b.alist : nullptr, b.acount));
                 KB_TRY(launch_assemble_diag<T>(W, X, bs, 1, b.omega + int64_t(k) * W, n, Y, ldy, M, M,
                                                tg, c.s, k, 1));
             }
@@ -637,7 +663,7 @@ template <typename T>
 int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int64_t n,
               const int32_t *marker, const int32_t *nodes, int Mc, const T *Zsrc, T *bufs[3],
               T *out, float *yout, int64_t ldo, int mo, int64_t M_alg, uint8_t *gen,
-              int32_t *tgen, int hop0) {
+              int32_t *tgen, int hop0, int32_t *alist, int32_t *acount) {
     // weights of sum_k'' c_k T_k (reading A3)
     const int h = int(coef.size()) - 1;
     std::vector<double> w(coef);
@@ -659,11 +685,17 @@ int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int
         while (dst_i == cur_i || dst_i == prev_i) ++dst_i;
         // b_k is supported on rows within hop0 + (h - k) hops of W
         const int hop = hop0 + (h - k);
-        if (tgen) KB_TRY(launch_frontier_expand(c.g->dev, gen, tgen, hop, c.s));
+        if (tgen) {
+            KB_TRY(launch_frontier_expand(c.g->dev, gen, tgen, hop, c.s));
+            // (the last step writes zeros on inactive tiles and walks every tile)
+            if (!last) KB_TRY(launch_frontier_list(tgen, n, hop, alist, acount, c.s));
+        }
         LinEpi<T> e;
         e.tgen = tgen;
         e.gen = tgen ? gen : nullptr;
         e.limit = hop;
+        e.alist = (tgen && !last) ? alist : nullptr;
+        e.acount = acount;
         e.zero_inactive = last ? 1 : 0;
         e.s1 = (last ? -2.0 : -4.0) / lam;
         e.s0 = last ? 1.0 : 2.0;
@@ -689,13 +721,15 @@ int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int
 
 template <typename T>
 void plan_cheb(Arena &ar, int64_t n, int Mmax, bool squared, T **bufs, T **Z, int32_t **marker,
-               uint8_t **gen, int32_t **tgen) {
+               uint8_t **gen, int32_t **tgen, int32_t **alist, int32_t **acount) {
     const int Wmax = width_for(Mmax);
     for (int i = 0; i < 3; ++i) bufs[i] = ar.take<T>(size_t(n) * Wmax);
     *Z = squared ? ar.take<T>(size_t(n) * Wmax) : nullptr;
     *marker = ar.take<int32_t>(size_t(n));
     *gen = ar.take<uint8_t>(size_t(n));
     *tgen = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
+    *alist = ar.take<int32_t>(size_t((n + ACT_ROWS - 1) / ACT_ROWS));
+    *acount = ar.take<int32_t>(1);
 }
 
 template <typename T>
@@ -707,12 +741,12 @@ int run_cheb(Common &c, bool squared, const int32_t *nodes, int M, int m, float 
     const int Mmax = std::min(M, sizeof(T) == 8 ? 64 : 128);
     Arena dry;
     T *bufs[3], *Z;
-    int32_t *marker, *tgen;
+    int32_t *marker, *tgen, *alist, *acount;
     uint8_t *gen;
-    plan_cheb<T>(dry, n, Mmax, squared, bufs, &Z, &marker, &gen, &tgen);
+    plan_cheb<T>(dry, n, Mmax, squared, bufs, &Z, &marker, &gen, &tgen, &alist, &acount);
     Arena ar;
     KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
-    plan_cheb<T>(ar, n, Mmax, squared, bufs, &Z, &marker, &gen, &tgen);
+    plan_cheb<T>(ar, n, Mmax, squared, bufs, &Z, &marker, &gen, &tgen, &alist, &acount);
     auto body = [&]() -> int {
         for (int col0 = 0; col0 < M; col0 += Mmax) {
             const int Mc = std::min(Mmax, M - col0);
@@ -730,12 +764,12 @@ int run_cheb(Common &c, bool squared, const int32_t *nodes, int M, int m, float 
             }
             if (!squared) {
                 KB_TRY(cheb_pass<T>(c, coef, lam, W, n, marker, nodes + col0, Mc, nullptr, bufs,
-                                    nullptr, Y + col0, ldy, Mc, Mc, gen, tg, 0));
+                                    nullptr, Y + col0, ldy, Mc, Mc, gen, tg, 0, alist, acount));
             } else {
                 KB_TRY(cheb_pass<T>(c, coef, lam, W, n, marker, nodes + col0, Mc, nullptr, bufs, Z,
-                                    nullptr, 0, 0, Mc, gen, tg, 0));
+                                    nullptr, 0, 0, Mc, gen, tg, 0, alist, acount));
                 KB_TRY(cheb_pass<T>(c, coef, lam, W, n, marker, nodes + col0, Mc, Z, bufs,
-                                    nullptr, Y + col0, ldy, Mc, Mc, gen, tg, h));
+                                    nullptr, Y + col0, ldy, Mc, Mc, gen, tg, h, alist, acount));
             }
         }
         return 0;
@@ -769,10 +803,10 @@ size_t workspace_bytes_t(int64_t n, kb_method method, int M, int m, bool two, co
         case KB_CHEB:
         case KB_CHEB2: {
             T *bufs[3], *Z;
-            int32_t *marker, *tgen;
+            int32_t *marker, *tgen, *alist, *acount;
             uint8_t *gen;
             plan_cheb<T>(dry, n, std::min(M, sizeof(T) == 8 ? 64 : 128), method == KB_CHEB2, bufs, &Z,
-                         &marker, &gen, &tgen);
+                         &marker, &gen, &tgen, &alist, &acount);
             break;
         }
     }

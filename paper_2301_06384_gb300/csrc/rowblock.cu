@@ -125,7 +125,17 @@ k_rowblock(RowArgs<T> a) {
 
     const int64_t ntiles = (a.n + TR - 1) / TR;
     unsigned long long my_rows = 0, my_units = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // active-tile list (not for ASM, which writes every row): only row tiles holding a listed
+    // 32-row frontier tile are visited, the first listed entry of a tile taking it
+    constexpr int APT = TR / ACT_ROWS > 0 ? TR / ACT_ROWS : 1;
+    const bool listed = MODE != RB_ASM && a.alist && a.tgen;
+    const int64_t nloop = listed ? int64_t(*a.acount) : ntiles;
+    for (int64_t it = blockIdx.x; it < nloop; it += gridDim.x) {
+        int64_t tile = it;
+        if (listed) {
+            tile = __ldg(a.alist + it) / APT;
+            if (it > 0 && __ldg(a.alist + it - 1) / APT == tile) continue;
+        }
         const int64_t r0 = tile * TR;
         const int rows_t = (a.n - r0 < TR) ? int(a.n - r0) : TR;
         // frontier restriction: a tile beyond the limit is zero in every operand; in the

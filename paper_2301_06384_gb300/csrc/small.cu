@@ -775,7 +775,9 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m
 template <typename T, int W>
 __global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const double *a, int64_t n,
                                                        double *parts, const Ctrl *ctrl,
-                                                       const int32_t *tgen, int limit, ProfCount pc) {
+                                                       const int32_t *tgen, int limit,
+                                                       const int32_t *alist, const int32_t *acount,
+                                                       ProfCount pc) {
     if (ctrl->stop) return;
     using C = typename Cmp<T>::type;
     constexpr int CG = W / 4;
@@ -791,9 +793,31 @@ __global__ void __launch_bounds__(256) k_axpy_colnorm(T *X, const T *P, const do
     }
     C acc[4] = {0, 0, 0, 0};
     unsigned long long my_rows = 0;
+    if (alist && tgen) {
+        // active 32-row tiles only (listed in increasing order): RPP rows per pass
+        const int cnt = *acount;
+        for (int it = blockIdx.x; it < cnt; it += gridDim.x) {
+            const int64_t t0 = int64_t(__ldg(alist + it)) * ACT_ROWS;
+            for (int sub = rr; sub < ACT_ROWS; sub += RPP) {
+                const int64_t row = t0 + sub;
+                if (row >= n) break;
+                C xv[4], pv[4];
+                ldv4(X + row * W + c4, xv);
+                ldv4(P + row * W + c4, pv);
+                if (cg == 0) ++my_rows;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    xv[q] = xv[q] - fma(ah[q], pv[q], al[q] * pv[q]);
+                    if constexpr (!std::is_same<T, C>::value) xv[q] = C(T(xv[q]));
+                    acc[q] = fma(xv[q], xv[q], acc[q]);
+                }
+                stv4(X + row * W + c4, xv);
+            }
+        }
+    }
     // two rows per iteration, 16-byte vector accesses: four loads in flight per thread
     const int64_t stride = int64_t(gridDim.x) * RPP;
-    for (int64_t row = int64_t(blockIdx.x) * RPP + rr; row < n; row += 2 * stride) {
+    for (int64_t row = int64_t(blockIdx.x) * RPP + rr; !(alist && tgen) && row < n; row += 2 * stride) {
         const int64_t row2 = row + stride;
         const bool act0 = !tgen || __ldg(tgen + row / ACT_ROWS) <= limit;
         const bool act1 = row2 < n && (!tgen || __ldg(tgen + row2 / ACT_ROWS) <= limit);
@@ -1068,6 +1092,49 @@ int launch_frontier_init(uint8_t *gen, int32_t *tgen, int64_t n, const int32_t *
     return 0;
 }
 
+// Stream compaction of the active 32-row tiles in tile order: each thread counts a contiguous
+// range, a block-wide exclusive scan gives its output offset, then it writes its range.
+__global__ void __launch_bounds__(1024) k_frontier_list(const int32_t *__restrict__ tgen, int64_t nact,
+                                                        int limit, int32_t *__restrict__ list,
+                                                        int32_t *__restrict__ count) {
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t per = (nact + blockDim.x - 1) / blockDim.x;
+    const int64_t a0 = int64_t(tid) * per;
+    const int64_t a1 = a0 + per < nact ? a0 + per : nact;
+    int c = 0;
+    for (int64_t a = a0; a < a1; ++a) c += __ldg(tgen + a) <= limit ? 1 : 0;
+    int incl = c;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < int(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += u;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int pos = (warp > 0 ? wsum[warp - 1] : 0) + incl - c;
+    for (int64_t a = a0; a < a1; ++a)
+        if (__ldg(tgen + a) <= limit) list[pos++] = int32_t(a);
+    if (tid == int(blockDim.x) - 1) *count = pos;
+}
+
+int launch_frontier_list(const int32_t *tgen, int64_t n, int limit, int32_t *list, int32_t *count,
+                         cudaStream_t s) {
+    prof_begin(KernelClass::OTHER, s);
+    k_frontier_list<<<1, 1024, 0, s>>>(tgen, (n + ACT_ROWS - 1) / ACT_ROWS, limit, list, count);
+    KB_CUDA_TRY(cudaGetLastError());
+    prof_end(KernelClass::OTHER, s, double(n) / ACT_ROWS * 4, 0);
+    return 0;
+}
+
 int launch_frontier_expand(const GraphDev &g, uint8_t *gen, int32_t *tgen, int k, cudaStream_t s) {
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, int64_t(num_sms()) * 8)));
     prof_begin(KernelClass::OTHER, s);
@@ -1166,16 +1233,16 @@ int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const 
 template <typename T>
 int launch_axpy_colnorm(int W, T *X, const T *P, const double *a, int64_t n, double *parts,
                         int *grid_out, const Ctrl *ctrl, const int32_t *tgen, int limit,
-                        int64_t M_alg, cudaStream_t s) {
+                        int64_t M_alg, cudaStream_t s, const int32_t *alist, const int32_t *acount) {
     const int rpp = 256 / (W / 4);
     const int grid = int(std::min<int64_t>((n + rpp - 1) / rpp, int64_t(num_sms()) * 4));
     *grid_out = std::max(grid, 1);
     const ProfCount pc = prof_begin(KernelClass::ROWBLOCK, s);
     switch (W) {
-        case 16: k_axpy_colnorm<T, 16><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, pc); break;
-        case 32: k_axpy_colnorm<T, 32><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, pc); break;
-        case 64: k_axpy_colnorm<T, 64><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, pc); break;
-        case 128: k_axpy_colnorm<T, 128><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, pc); break;
+        case 16: k_axpy_colnorm<T, 16><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, alist, acount, pc); break;
+        case 32: k_axpy_colnorm<T, 32><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, alist, acount, pc); break;
+        case 64: k_axpy_colnorm<T, 64><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, alist, acount, pc); break;
+        case 128: k_axpy_colnorm<T, 128><<<*grid_out, 256, 0, s>>>(X, P, a, n, parts, ctrl, tgen, limit, alist, acount, pc); break;
         default: return fail(KB_ERR_ARG, "bad width");
     }
     KB_CUDA_TRY(cudaGetLastError());
@@ -1236,7 +1303,7 @@ int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ct
                                 T *, double *, T *, Ctrl *, cudaStream_t);                      \
     template int launch_axpy_colnorm<T>(int, T *, const T *, const double *, int64_t, double *,  \
                                         int *, const Ctrl *, const int32_t *, int, int64_t,     \
-                                        cudaStream_t);                                          \
+                                        cudaStream_t, const int32_t *, const int32_t *);        \
     template int launch_assemble_diag<T>(int, const T *, int64_t, int, const double *, int64_t, \
                                          float *, int64_t, int, int64_t, const int32_t *,       \
                                          cudaStream_t, int, int);                               \
@@ -1252,7 +1319,7 @@ template int launch_scale_copy<__nv_bfloat16>(__nv_bfloat16 *, const __nv_bfloat
 template int launch_axpy_colnorm<__nv_bfloat16>(int, __nv_bfloat16 *, const __nv_bfloat16 *,
                                                 const double *, int64_t, double *, int *,
                                                 const Ctrl *, const int32_t *, int, int64_t,
-                                                cudaStream_t);
+                                                cudaStream_t, const int32_t *, const int32_t *);
 template int launch_assemble_diag<__nv_bfloat16>(int, const __nv_bfloat16 *, int64_t, int,
                                                  const double *, int64_t, float *, int64_t, int,
                                                  int64_t, const int32_t *, cudaStream_t, int, int);

@@ -74,7 +74,10 @@ template <> struct V4<double> {
 #define KB_SPMM_VPL 2
 #endif
 #ifndef KB_SPMM_U
-#define KB_SPMM_U 2
+#define KB_SPMM_U 4
+#endif
+#ifndef KB_SPMM_PACKED
+#define KB_SPMM_PACKED 1   // FP32 neighbour loop on packed f32x2 pairs
 #endif
 #ifndef KB_SPMM_IDX32
 #define KB_SPMM_IDX32 0
@@ -102,6 +105,38 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Packed FP32 pairs (Blackwell add/sub/fma.rn.f32x2): each lane of the pair is rounded as
+// the scalar instruction would round it, so the packed neighbour loop gives bit-identical
+// sums with half the floating-point instructions.
+using f2 = unsigned long long;
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// 16 bytes of a read-only FP32 row as two packed pairs
+__device__ __forceinline__ void ldg_f2x2(const float *p, f2 &a, f2 &b) {
+    asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+}
+
 // Four consecutive coefficients from shared memory in one 16-byte (FP32) or two 16-byte
 // (FP64) loads; c is a multiple of 4 and the arrays are 16-byte aligned.
 template <typename C>
@@ -117,11 +152,14 @@ __device__ __forceinline__ void lds4(const C *p, C (&v)[4]) {
 }
 
 #ifndef KB_SPMM_OCC
-#define KB_SPMM_OCC 5   // FP32 / BF16 kernel without column dots
+#define KB_SPMM_OCC 4   // FP32 / BF16 kernel without column dots
+#endif
+#ifndef KB_SPMM_OCC_DOT
+#define KB_SPMM_OCC_DOT 4   // FP32 / BF16 kernel with column dots
 #endif
 template <typename T, bool DOT>
 struct SpmmOcc {
-    static constexpr int value = sizeof(typename Cmp<T>::type) == 8 ? 3 : (DOT ? 4 : KB_SPMM_OCC);
+    static constexpr int value = sizeof(typename Cmp<T>::type) == 8 ? 3 : (DOT ? KB_SPMM_OCC_DOT : KB_SPMM_OCC);
 };
 
 // WGT: the graph stores edge weights (false: unit weights, w_ij = 1)
@@ -131,6 +169,9 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
     using G = SpmmGeo<W>;
     using C = typename Cmp<T>::type;   // arithmetic type
     constexpr int LPR = G::LPR, RPW = G::RPW, NG = G::NG, TR = G::TR, RPG = G::RPG;
+    // gathers in flight per lane group: fewer in the variant that also accumulates column
+    // dots (its registers hold the dot partials)
+    constexpr int UU = DOT ? (U < 2 ? U : 2) : U;
     if (e.ctrl && e.ctrl->stop) return;
     // (arrays a variant does not use take one element: shared memory left to L1 caches the
     // gathered rows)
@@ -172,8 +213,18 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) dot[v][q] = C(0);
     const int64_t ntiles = (g.n + TR - 1) / TR;
+    // with the active-tile list, visit only the row tiles holding an active 32-row tile (a
+    // tile covering several listed entries is taken by the CTA that meets its first one)
+    constexpr int APT = TR / ACT_ROWS > 0 ? TR / ACT_ROWS : 1;   // list entries per row tile
+    const bool listed = e.alist && e.tgen && !e.zero_inactive;
+    const int64_t nloop = listed ? int64_t(*e.acount) : ntiles;
 
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int64_t it = blockIdx.x; it < nloop; it += gridDim.x) {
+        int64_t tile = it;
+        if (listed) {
+            tile = __ldg(e.alist + it) / APT;
+            if (it > 0 && __ldg(e.alist + it - 1) / APT == tile) continue;
+        }
         const int64_t r0 = tile * TR;
         const int rows = (g.n - r0 < TR) ? int(g.n - r0) : TR;
         if (e.tgen && tile_min_gen(e.tgen, r0, rows) > e.limit) {
@@ -279,32 +330,85 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[v][q] = C(0);
             }
-            for (int p = beg; p < end; p += U) {
+            if constexpr (std::is_same<T, float>::value && KB_SPMM_PACKED) {
+                // the same sums on packed pairs: acc += w (x_i - x_j), two columns per
+                // instruction
+                f2 xi2[VPL][2], acc2[VPL][2];
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    xi2[v][0] = f2_pack(xi[v].v[0], xi[v].v[1]);
+                    xi2[v][1] = f2_pack(xi[v].v[2], xi[v].v[3]);
+                    acc2[v][0] = 0ull;
+                    acc2[v][1] = 0ull;
+                }
+                for (int p = beg; p < end; p += UU) {
+                    // slots past the row's end gather the row itself (weight 0): x_i - x_i
+                    // adds an exact zero, so the unrolled body needs no per-slot branch
+                    f2 xj2[UU][VPL][2];
+                    f2 wv2[UU];
+                    int jj[UU];
+#pragma unroll
+                    for (int u = 0; u < UU; ++u) {
+                        const bool in = p + u < end;
+                        jj[u] = in ? (staged ? s_col[p + u] : __ldg(g.col + base + p + u)) : int(row);
+                        if (WGT) {
+                            const float w = in ? (staged ? s_w[p + u] : __ldg(g.w + base + p + u)) : 0.f;
+                            wv2[u] = f2_pack(w, w);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < UU; ++u)
+#pragma unroll
+                        for (int v = 0; v < VPL; ++v)
+                            ldg_f2x2(reinterpret_cast<const float *>(x) + int64_t(jj[u]) * W + KB_COL(v),
+                                     xj2[u][v][0], xj2[u][v][1]);
+#pragma unroll
+                    for (int u = 0; u < UU; ++u)
+#pragma unroll
+                        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const f2 d = f2_sub(xi2[v][h], xj2[u][v][h]);
+                                acc2[v][h] = WGT ? f2_fma(wv2[u], d, acc2[v][h]) : f2_add(acc2[v][h], d);
+                            }
+                }
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    f2_unpack(acc2[v][0], acc[v][0], acc[v][1]);
+                    f2_unpack(acc2[v][1], acc[v][2], acc[v][3]);
+                    // x_i again from its packed copy (the scalar copy need not live across
+                    // the loop)
+                    f2_unpack(xi2[v][0], xi[v].v[0], xi[v].v[1]);
+                    f2_unpack(xi2[v][1], xi[v].v[2], xi[v].v[3]);
+                }
+            } else {
+            for (int p = beg; p < end; p += UU) {
                 // slots past the row's end gather the row itself (weight 0): x_i - x_i adds
                 // an exact zero, so the unrolled body needs no per-slot branch
-                V4<T> xj[U][VPL];
-                C wv[U];
-                int jj[U];
+                V4<T> xj[UU][VPL];
+                C wv[UU];
+                int jj[UU];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
+                for (int u = 0; u < UU; ++u) {
                     const bool in = p + u < end;
                     jj[u] = in ? (staged ? s_col[p + u] : __ldg(g.col + base + p + u)) : int(row);
                     wv[u] = WGT ? (in ? C(staged ? s_w[p + u] : __ldg(g.w + base + p + u)) : C(0)) : C(1);
                 }
 #pragma unroll
-                for (int u = 0; u < U; ++u)
+                for (int u = 0; u < UU; ++u)
 #pragma unroll
                     for (int v = 0; v < VPL; ++v)
                         xj[u][v] = V4<T>::load(KB_SPMM_IDX32 ? x + (unsigned(jj[u]) * unsigned(W) + unsigned(KB_COL(v)))
                                                              : x + int64_t(jj[u]) * W + KB_COL(v));
 #pragma unroll
-                for (int u = 0; u < U; ++u)
+                for (int u = 0; u < UU; ++u)
 #pragma unroll
                     for (int v = 0; v < VPL; ++v)
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
                             acc[v][q] = WGT ? fma(wv[u], xi[v].v[q] - xj[u][v].v[q], acc[v][q])
                                             : acc[v][q] + (xi[v].v[q] - xj[u][v].v[q]);
+            }
             }
             const C r = g.rdiag ? C(__ldg(g.rdiag + row)) : C(0);
             const int mk = e.marker ? __ldg(e.marker + row) : -1;
