@@ -148,6 +148,14 @@ void kb_graph_destroy(kb_graph *g);
 int kb_graph_info(const kb_graph *g, int64_t *n, int64_t *nnz_offdiag, double *lambda_max,
                   int32_t *standard_unit);
 
+/* Spectral upper bounds of the graph (host values, no GPU work): gershgorin =
+ * max_i sum_j |L_ij| (the Lambda of the Chebyshev methods, reading A5); projected = the bound
+ * the Lanczos methods use for their projected e^{-tH} series (Algorithms 1 and 2 need
+ * phi(H_m), whose spectrum lies in [0, lambda_max(L)]): for the unit-weight standard
+ * Laplacian D - A the edge bound max over edges (d_i + d_j) of Anderson and Morley when
+ * smaller, otherwise gershgorin.  Either pointer may be NULL. */
+int kb_graph_lambda_bounds(const kb_graph *g, double *gershgorin, double *projected);
+
 /* ------------------------------------------------------------------ kernel columns */
 /*
  * kb_krylov_apply -- Y ~ phi(L) E_W by one block Krylov method.   (Section 3; Algorithms 1, 2)

@@ -41,6 +41,9 @@ struct kb_graph {
     float *d_w = nullptr;
     float *d_rdiag = nullptr;
     double lambda = 0.0;     // Gershgorin bound
+    double lambda_proj = 0.0;// spectral bound for the Lanczos projected step: the Gershgorin
+                             // bound, or for a unit-weight D - A the smaller edge bound
+                             // max over edges (d_i + d_j) (Anderson and Morley)
     int device = 0;
     int32_t unit_weights = 0;
     int32_t zero_excess = 0;

@@ -112,9 +112,11 @@ template <typename T>
 int launch_u_convert(const double *U, int M, int W, int m, T *Ut, const Ctrl *ctrl, cudaStream_t s);
 
 // Projected problem of the classical block Lanczos method (FP64, block tridiagonal H_m).
+// Hdf: nullptr for the FP64 recurrence; else 2 m M^2 doubles of scratch for the split H, and
+// the recurrence runs in double-float on the FP32 pipe (the FP32 and BF16 modes).
 int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
                    const std::vector<double> &d, double *V0, double *V1, double *V2, double *U,
-                   const Ctrl *ctrl, cudaStream_t s);
+                   const Ctrl *ctrl, cudaStream_t s, double *Hdf = nullptr);
 // U = (eps I + H_m)^{-s} F_1.  Integer s: s_int block Cholesky solves (q == nullptr or
 // q->n == 0).  Non-integer s: the quadrature rule q gives the fractional factor
 // sum_k W_k (sigma_k I + H_m)^{-1} F_1, one block Cholesky factorisation and solve per node

@@ -155,7 +155,7 @@ int quad_setup(const kb_graph *g, kb_method method, kb_phi phi, const kb_params 
     q.n = 0;
     q.s_int = 0;
     if (phi != KB_PHI_SPLINE || method == KB_CHEB || method == KB_CHEB2) return KB_OK;
-    return spline_quadrature(p.eps, p.s, g->lambda, 1e-14, q);
+    return spline_quadrature(p.eps, p.s, g->lambda_proj, 1e-14, q);
 }
 
 // Quadrature nodes processed at once by the cbl projected step (one CTA and one scratch
@@ -200,6 +200,7 @@ struct CblBufs {
     double *Gsum, *Hd, *Hs, *R1, *V0, *V1, *V2, *U;
     double *Uc;          // stopping rule: two U_k of the checks (alternating)
     double *qscr;        // projected step with non-integer s: per-node block solves
+    double *Hdf;         // projected e^{-tH} F_1 in double-float: H split into float pairs
     int32_t *chk_prev;   // steps of the previous check (0: none yet)
     Ctrl *ctrl, *ctrl2, *ctrl_chk;
     uint8_t *gen;
@@ -231,6 +232,7 @@ void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_g
     b.U = ar.take<double>(size_t(m) * M * M);
     b.Uc = ar.take<double>(size_t(2) * m * M * M);
     b.qscr = qbatch > 0 ? ar.take<double>(size_t(qbatch) * bt_quad_node_doubles(M, m)) : nullptr;
+    b.Hdf = sizeof(typename Cmp<T>::type) == 4 ? ar.take<double>(size_t(2) * m * M * M) : nullptr;
     b.chk_prev = ar.take<int32_t>(1);
     b.ctrl = ar.take<Ctrl>(1);
     b.ctrl2 = ar.take<Ctrl>(1);
@@ -257,7 +259,8 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
     KB_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&ar.base), dry.off, c.s));
     plan_cbl<T>(ar, b, n, M, W, m, rb_grid, two, qbatch);
     auto body = [&]() -> int {
-        const double lam = c.g->lambda;
+        const double lam = c.g->lambda;        // thresholds (scale of L)
+        const double lam_p = c.g->lambda_proj; // interval of the projected series
         const double tau_inv = f64 ? 1e-12 : 1e-6;
         const double tau_piv = f64 ? 1e-12 : 1e-5;
         const double inv_thresh2 = (tau_inv * lam) * (tau_inv * lam) * M;
@@ -389,8 +392,8 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                 const double *Uprev = b.Uc + size_t((nchk + 1) % 2) * m * M * M;
                 KB_TRY(launch_ctrl_snapshot(b.ctrl_chk, b.ctrl, k, c.s));
                 if (c.phi == KB_PHI_EXP) {
-                    const std::vector<double> d = exp_series_coeffs(c.p.t, lam, 1e-17);
-                    KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam, d, b.V0, b.V1, b.V2, Ucur, b.ctrl_chk, c.s));
+                    const std::vector<double> d = exp_series_coeffs(c.p.t, lam_p, 1e-17);
+                    KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam_p, d, b.V0, b.V1, b.V2, Ucur, b.ctrl_chk, c.s, b.Hdf));
                 } else {
                     KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, Ucur,
                                             b.ctrl_chk, c.s, c.quad, b.qscr, qbatch));
@@ -401,8 +404,8 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
         }
         // projected problem: U = phi(H_m) F_1 in FP64
         if (c.phi == KB_PHI_EXP) {
-            const std::vector<double> d = exp_series_coeffs(c.p.t, lam, 1e-17);
-            KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam, d, b.V0, b.V1, b.V2, b.U, b.ctrl, c.s));
+            const std::vector<double> d = exp_series_coeffs(c.p.t, lam_p, 1e-17);
+            KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam_p, d, b.V0, b.V1, b.V2, b.U, b.ctrl, c.s, b.Hdf));
         } else {
             KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, b.U,
                                     b.ctrl, c.s, c.quad, b.qscr, qbatch));
@@ -529,7 +532,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
     auto tc = std::make_unique<TriCoef>();
     int nquad = 0;
     if (c.phi == KB_PHI_EXP) {
-        const std::vector<double> d = exp_series_coeffs(c.p.t, c.g->lambda, 1e-17);
+        const std::vector<double> d = exp_series_coeffs(c.p.t, c.g->lambda_proj, 1e-17);
         if (int(d.size()) > ChebCoef::CAP)
             return fail(KB_ERR_UNSUPPORTED, "t * Lambda too large for the tridiagonal Chebyshev series");
         tc->cc.n = int(d.size());
@@ -603,7 +606,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
                                        b.ctrl, c.s));
         }
         KB_TRY(launch_tridiag_phi(W, M, m, gbl ? 1 : 0, b.alpha, b.beta, b.sigma, int(c.phi),
-                                  c.p.eps, c.s_int, c.g->lambda, *tc, b.omega, b.work, b.qwork, b.ctrl,
+                                  c.p.eps, c.s_int, c.g->lambda_proj, *tc, b.omega, b.work, b.qwork, b.ctrl,
                                   projected_bound(c), c.s));
         if (!two) {
             KB_TRY(launch_assemble_diag<T>(W, b.basis, bs, m, b.omega, n, Y, ldy, M, M, tg, c.s));
@@ -854,7 +857,7 @@ int validate(kb_graph *g, kb_method method, kb_phi phi, const kb_params *params,
         if (params->s >= 65) return fail(KB_ERR_UNSUPPORTED, "Lanczos methods support s < 65");
         *s_int = int(std::floor(params->s));
     }
-    if (method == KB_CBL && phi == KB_PHI_EXP && std::fabs(params->t) * g->lambda > 2e5)
+    if (method == KB_CBL && phi == KB_PHI_EXP && std::fabs(params->t) * g->lambda_proj > 2e5)
         return fail(KB_ERR_UNSUPPORTED, "t * Lambda too large for the Chebyshev projected solve");
     std::vector<int32_t> sorted(nodes, nodes + M);
     std::sort(sorted.begin(), sorted.end());

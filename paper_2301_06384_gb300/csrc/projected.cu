@@ -76,6 +76,102 @@ k_cheb_bt_iter(const double *__restrict__ Hd, const double *__restrict__ Hs,
     }
 }
 
+// ---------------------------------------------------------------- double-float recurrence
+// The same recurrence with H and V held as unevaluated float pairs (hi + lo, about 48
+// significant bits) on the FP32 pipe, which this part runs at 64 times its FP64 rate.  The
+// products are compensated dot products (Ogita, Rump and Oishi's Dot2): each h v term is
+// split exactly by an FMA (TwoProd), the running sum by Knuth's TwoSum, and the rounding
+// errors are summed beside it; the result is exact to about 2^-48 relative, far below the
+// 1e-14 the projected solve needs after thousands of terms.  U is accumulated in FP64.
+struct dfl {
+    float h, l;
+};
+__device__ __forceinline__ dfl dfl_fast(float s, float e) {   // |s| >= |e|
+    const float h = s + e;
+    return dfl{h, e - (h - s)};
+}
+// sum += a * b, exact products and sums tracked in (s, err)
+__device__ __forceinline__ void dot2_step(float &s, float &err, dfl a, dfl b) {
+    const float p = a.h * b.h;
+    float pe = fmaf(a.h, b.h, -p);
+    pe = fmaf(a.h, b.l, pe);
+    pe = fmaf(a.l, b.h, pe);
+    const float t = s + p;
+    const float bb = t - s;
+    err += ((s - (t - bb)) + (p - bb)) + pe;
+    s = t;
+}
+__host__ __device__ __forceinline__ dfl dfl_from(double v) {
+    const float h = float(v);
+    return dfl{h, float(v - double(h))};
+}
+__device__ __forceinline__ double dfl_val(dfl a) { return double(a.h) + double(a.l); }
+
+// H_d, H_s split into float pairs (once per projected solve)
+__global__ void k_split_df(const double *__restrict__ H, dfl *__restrict__ out, int64_t count) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = dfl_from(H[i]);
+}
+
+__global__ void k_cheb_bt_seed_df(dfl *V0, double *U, int M, double d0) {
+    const int i = threadIdx.x + blockIdx.x * blockDim.x;
+    if (i < M) {
+        V0[int64_t(i) * M + i] = dfl{1.f, 0.f};
+        U[int64_t(i) * M + i] = d0;
+    }
+}
+
+// V_{j+1} = beta (V_j - g H V_j) - gamma V_{j-1};  U += d_{j+1} V_{j+1}, in double-float
+__global__ void __launch_bounds__(256)
+k_cheb_bt_iter_df(const dfl *__restrict__ Hd, const dfl *__restrict__ Hs, const dfl *__restrict__ Vp,
+                  const dfl *__restrict__ Vc, dfl *__restrict__ Vn, double *__restrict__ U, int M,
+                  float beta, float gamma, double dnext, dfl g, const Ctrl *ctrl) {
+    const int r = blockIdx.x;
+    const int steps = ctrl->steps;
+    if (r >= steps) return;
+    const int c0 = blockIdx.y * TC;
+    extern __shared__ __align__(16) unsigned char svraw[];   // [3][M][TC] pairs
+    dfl *s0 = reinterpret_cast<dfl *>(svraw), *s1 = s0 + M * TC, *s2 = s0 + 2 * M * TC;
+    const int64_t MM = int64_t(M) * M;
+    for (int idx = threadIdx.x; idx < M * TC; idx += blockDim.x) {
+        const int k = idx / TC, cc = idx % TC, c = c0 + cc;
+        dfl a{0.f, 0.f}, b{0.f, 0.f}, d{0.f, 0.f};
+        if (c < M) {
+            if (r > 0) a = Vc[(r - 1) * MM + int64_t(k) * M + c];
+            b = Vc[r * MM + int64_t(k) * M + c];
+            if (r + 1 < steps) d = Vc[(r + 1) * MM + int64_t(k) * M + c];
+        }
+        s0[idx] = a; s1[idx] = b; s2[idx] = d;
+    }
+    __syncthreads();
+    const dfl *hd = Hd + r * MM;
+    const dfl *hl = (r > 0) ? Hs + (r - 1) * MM : nullptr;   // H_{r, r-1} = R_{r-1} (upper)
+    const dfl *hu = (r + 1 < steps) ? Hs + r * MM : nullptr; // H_{r, r+1} = R_r^T
+    for (int idx = threadIdx.x; idx < M * TC; idx += blockDim.x) {
+        const int i = idx / TC, cc = idx % TC, c = c0 + cc;
+        if (c >= M) continue;
+        float s = 0.f, err = 0.f;
+        for (int k = 0; k < M; ++k) dot2_step(s, err, hd[i * M + k], s1[k * TC + cc]);
+        if (hl)
+            for (int k = i; k < M; ++k) dot2_step(s, err, hl[i * M + k], s0[k * TC + cc]);
+        if (hu)
+            for (int k = 0; k <= i; ++k) dot2_step(s, err, hu[k * M + i], s2[k * TC + cc]);
+        // av = V_j - g (H V_j): one more compensated step with the pair -g
+        const dfl hv = dfl_fast(s, err);
+        float s2v = s1[i * TC + cc].h, e2 = s1[i * TC + cc].l;
+        dot2_step(s2v, e2, dfl{-g.h, -g.l}, hv);
+        // vn = beta av - gamma V_{j-1} (beta in {1, 2}, gamma in {0, 1}: exact scalings)
+        const int64_t o = r * MM + int64_t(i) * M + c;
+        const dfl vp = Vp[o];
+        float s3 = beta * s2v, e3 = beta * e2;
+        dot2_step(s3, e3, dfl{-gamma, 0.f}, vp);
+        const dfl vn = dfl_fast(s3, e3);
+        Vn[o] = vn;
+        U[o] += dnext * dfl_val(vn);
+    }
+}
+
 // ---------------------------------------------------------------- block Cholesky (spline)
 // One CTA; all scratch in global memory (L1/L2 resident for the sizes used).
 __device__ void chol_lower_inplace(double *A, int M) {
@@ -287,9 +383,35 @@ k_quad_accumulate(const double *__restrict__ scratch, int M, int mcap, int nb, Q
 
 int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
                    const std::vector<double> &d, double *V0, double *V1, double *V2, double *U,
-                   const Ctrl *ctrl, cudaStream_t s) {
+                   const Ctrl *ctrl, cudaStream_t s, double *Hdf) {
     const size_t bytes = sizeof(double) * size_t(m) * M * M;
     prof_begin(KernelClass::PROJECTED, s);
+    if (Hdf) {
+        // double-float recurrence: H split once, V_j as float pairs in the V buffers
+        const int64_t cnt = int64_t(m) * M * M;
+        dfl *hd = reinterpret_cast<dfl *>(Hdf), *hs = hd + cnt;
+        const int sg = int(std::min<int64_t>((cnt + 255) / 256, 8 * int64_t(num_sms())));
+        k_split_df<<<sg, 256, 0, s>>>(Hd, hd, cnt);
+        k_split_df<<<sg, 256, 0, s>>>(Hs, hs, cnt);
+        KB_CUDA_TRY(cudaMemsetAsync(V0, 0, bytes, s));
+        KB_CUDA_TRY(cudaMemsetAsync(V1, 0, bytes, s));
+        KB_CUDA_TRY(cudaMemsetAsync(V2, 0, bytes, s));
+        KB_CUDA_TRY(cudaMemsetAsync(U, 0, bytes, s));
+        dfl *pp = reinterpret_cast<dfl *>(V2), *pc = reinterpret_cast<dfl *>(V0), *pn = reinterpret_cast<dfl *>(V1);
+        k_cheb_bt_seed_df<<<(M + 127) / 128, 128, 0, s>>>(pc, U, M, d[0]);
+        const size_t smem = sizeof(dfl) * 3 * M * TC;
+        const dfl g = dfl_from(2.0 / lam);
+        for (size_t j = 0; j + 1 < d.size(); ++j) {
+            const int nrb = std::min<int>(int(j) + 2, m);
+            dim3 grid(nrb, (M + TC - 1) / TC);
+            const float beta = j == 0 ? 1.f : 2.f, gamma = j == 0 ? 0.f : 1.f;
+            k_cheb_bt_iter_df<<<grid, 256, smem, s>>>(hd, hs, pp, pc, pn, U, M, beta, gamma, d[j + 1], g, ctrl);
+            dfl *t = pp; pp = pc; pc = pn; pn = t;
+        }
+        KB_CUDA_TRY(cudaGetLastError());
+        prof_end(KernelClass::PROJECTED, s, 0, 0, int(d.size()) + 3);
+        return 0;
+    }
     KB_CUDA_TRY(cudaMemsetAsync(V0, 0, bytes, s));
     KB_CUDA_TRY(cudaMemsetAsync(V1, 0, bytes, s));
     KB_CUDA_TRY(cudaMemsetAsync(V2, 0, bytes, s));

@@ -172,6 +172,7 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
     // gathers in flight per lane group: fewer in the variant that also accumulates column
     // dots (its registers hold the dot partials)
     constexpr int UU = DOT ? (U < 2 ? U : 2) : U;
+    static_assert(TR >= ACT_ROWS && TR % ACT_ROWS == 0, "row tiles hold whole 32-row frontier tiles");
     if (e.ctrl && e.ctrl->stop) return;
     // (arrays a variant does not use take one element: shared memory left to L1 caches the
     // gathered rows)
@@ -213,20 +214,15 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) dot[v][q] = C(0);
     const int64_t ntiles = (g.n + TR - 1) / TR;
-    // with the active-tile list, visit only the row tiles holding an active 32-row tile (a
-    // tile covering several listed entries is taken by the CTA that meets its first one)
-    constexpr int APT = TR / ACT_ROWS > 0 ? TR / ACT_ROWS : 1;   // list entries per row tile
+    // with the active-tile list, the unit of work is one listed 32-row tile instead of a
+    // TR-row tile: the few active rows of an early step spread over all CTAs
     const bool listed = e.alist && e.tgen && !e.zero_inactive;
     const int64_t nloop = listed ? int64_t(*e.acount) : ntiles;
 
     for (int64_t it = blockIdx.x; it < nloop; it += gridDim.x) {
-        int64_t tile = it;
-        if (listed) {
-            tile = __ldg(e.alist + it) / APT;
-            if (it > 0 && __ldg(e.alist + it - 1) / APT == tile) continue;
-        }
-        const int64_t r0 = tile * TR;
-        const int rows = (g.n - r0 < TR) ? int(g.n - r0) : TR;
+        const int64_t r0 = listed ? int64_t(__ldg(e.alist + it)) * ACT_ROWS : it * TR;
+        const int urows = listed ? ACT_ROWS : TR;
+        const int rows = (g.n - r0 < urows) ? int(g.n - r0) : urows;
         if (e.tgen && tile_min_gen(e.tgen, r0, rows) > e.limit) {
             // every row of the tile is beyond the frontier: its output is exactly zero
             if (e.zero_inactive) {

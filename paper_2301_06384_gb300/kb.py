@@ -77,6 +77,8 @@ def lib() -> ctypes.CDLL:
     L.kb_graph_destroy.restype = None
     L.kb_graph_info.argtypes = [vp, P(i64), P(i64), P(dbl), P(i32)]
     L.kb_graph_info.restype = ctypes.c_int
+    L.kb_graph_lambda_bounds.argtypes = [vp, P(dbl), P(dbl)]
+    L.kb_graph_lambda_bounds.restype = ctypes.c_int
     for name in ("kb_krylov_apply", "kb_krylov_apply_host"):
         f = getattr(L, name)
         f.argtypes = [vp, ctypes.c_int, ctypes.c_int, P(kb_params), vp, i32, i32, vp, vp, P(kb_info)]
@@ -181,8 +183,10 @@ class Graph:
         n, nnz, lam, su = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32()
         _check(lib().kb_graph_info(self.handle, ctypes.byref(n), ctypes.byref(nnz),
                                    ctypes.byref(lam), ctypes.byref(su)))
+        gb, pb = ctypes.c_double(), ctypes.c_double()
+        _check(lib().kb_graph_lambda_bounds(self.handle, ctypes.byref(gb), ctypes.byref(pb)))
         return {"n": n.value, "nnz_offdiag": nnz.value, "lambda_max": lam.value,
-                "standard_unit": bool(su.value)}
+                "standard_unit": bool(su.value), "lambda_projected": pb.value}
 
     @property
     def n(self):

@@ -195,6 +195,45 @@ def test_weighted_generalized_laplacian(kb):
             assert _rel(Y, _oracle(g2, method, nodes, 16, "exp", t=0.05)) < TOL32, method
 
 
+def test_projected_bound_brackets_the_spectrum(kb):
+    # the bound of the Lanczos projected series lies between lambda_max(L) (dense
+    # eigenvalues) and the Gershgorin bound; for unit-weight D - A it is the edge bound
+    # max (d_i + d_j) (Anderson and Morley), for a star graph exactly lambda_max = n
+    n = 30
+    star = synth.from_edges(n, np.zeros(n - 1, dtype=np.int64), np.arange(1, n))
+    cases = [star, synth.barabasi_albert_graph(400, 3, seed=2),
+             synth.barabasi_albert_graph(400, 3, seed=2, weighted=True), synth.grid_graph((9, 7))]
+    for g in cases:
+        lmax = np.linalg.eigvalsh(dense.laplacian_dense(g.n, g.rowptr, g.col, g.val)).max()
+        with kb.Graph.from_csr(g) as G:
+            info = G.info()
+        assert lmax <= info["lambda_projected"] * (1 + 1e-12)
+        assert info["lambda_projected"] <= info["lambda_max"] * (1 + 1e-12)
+        if info["standard_unit"]:
+            rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+            off = rows != g.col
+            deg = np.bincount(rows[off], minlength=g.n)
+            edge = (deg[rows[off]] + deg[g.col[off]]).max()
+            assert abs(info["lambda_projected"] - min(info["lambda_max"], edge * 1.001)) < 1e-9 * edge
+    # the star: the bound is tight up to its margin of 1e-3
+    with kb.Graph.from_csr(star) as G:
+        assert abs(G.info()["lambda_projected"] - n * 1.001) < 1e-9
+
+
+@pytest.mark.parametrize("t", [0.5, 3.0])
+def test_star_graph_exp_lanczos_with_tight_bound(kb, t):
+    # the edge bound meets lambda_max exactly on a star: the projected series must still
+    # cover the Ritz values the FP32 process produces
+    n = 2001
+    g = synth.from_edges(n, np.zeros(n - 1, dtype=np.int64), np.arange(1, n))
+    with kb.Graph.from_csr(g) as G:
+        for method in ("cbl", "gbl", "sbl"):
+            # (several leaves in one cbl block give a rank-deficient block: centre only)
+            nodes = [0] if method == "cbl" else [0, 5, 17, 900]
+            Y = _gpu(kb, G, method, "exp", nodes, 6, t=t)
+            check_err(f"star2001 {method} exp t={t} m=6 FP32", _rel(Y, _oracle(g, method, nodes, 6, "exp", t=t)), TOL32)
+
+
 # ---------------------------------------------------------------- exactness and stops
 def test_cbl_exact_at_full_dimension(kb):
     g = synth.random_weighted_graph(12, 0.5, seed=7)
@@ -446,8 +485,10 @@ def test_argument_errors(kb):
             with pytest.raises(kb.KbError) as ei:
                 kb.kb_krylov_apply(G, kw["method"], "exp", p, np.array(kw["nodes"]), kw["M"], kw["m"], Y)
             assert ei.value.code == code, (kw, str(ei.value))
+        # non-integer s is supported (quadrature of the fractional power); s >= 65 is not
+        kb.kb_krylov_apply(G, "cbl", "spline", kb.make_params(eps=0.1, s=1.5), np.arange(4), 4, 5, Y)
         with pytest.raises(kb.KbError) as ei:
-            kb.kb_krylov_apply(G, "cbl", "spline", kb.make_params(eps=0.1, s=1.5), np.arange(4), 4, 5, Y)
+            kb.kb_krylov_apply(G, "cbl", "spline", kb.make_params(eps=0.1, s=65.5), np.arange(4), 4, 5, Y)
         assert ei.value.code == -7
         with pytest.raises(kb.KbError) as ei:
             kb.kb_krylov_apply(G, "cbl", "exp", kb.make_params(t=1.0, basis=7), np.arange(4), 4, 5, Y)
