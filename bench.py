@@ -173,6 +173,8 @@ def serving_sample(a, kb, torch):
             phi = "spline"
         nodes = synth.sample_nodes(ns[k], M, seed=1000 + i)
         reqs.append((k, phi, p, nodes))
+    # latency per request class (graph family x kernel), from the Poisson run
+    cls = [("rgg" if k % 2 == 0 else "ba") + "-" + phi for (k, phi, _, _) in reqs]
     window = 64
     slots = [torch.empty(max(ns) * 128, dtype=torch.float32, device="cuda") for _ in range(window)]
 
@@ -180,23 +182,27 @@ def serving_sample(a, kb, torch):
     retried = [0]
     steps = []
 
-    def finish(sv, tk, lat):
+    def finish(sv, tk, lat, idx=None, bycls=None):
         # a request whose block Lanczos process meets a rank-deficient block (a node set
         # spanning a small connected component) is rerun by the server as sbl (counted);
         # a request that still fails is counted, not timed
         try:
             info, ms = sv.poll(tk, wait_ms=-1)
             lat.append(ms)
+            if bycls is not None:
+                bycls.setdefault(cls[idx], []).append(ms)
             steps.append(info["steps_done"])
             if info["breakdown_step"] >= 0:
                 retried[0] += 1
         except kb.KbError:
             failed[0] += 1
 
-    def run(arrival_times):
+    bycls = {}
+
+    def run(arrival_times, record=None):
         lat = []
         with kb.Server(streams=a.serve_streams, queue_capacity=R + 1, fallback_sbl=True) as sv:
-            outstanding = []   # (ticket, slot)
+            outstanding = []   # (ticket, slot, request index)
             free = list(range(window))
             t0 = time.perf_counter()
             for i, (k, phi, p, nodes) in enumerate(reqs):
@@ -205,14 +211,14 @@ def serving_sample(a, kb, torch):
                     if dt > 0:
                         time.sleep(dt)
                 while not free:
-                    tk, sl = outstanding.pop(0)
-                    finish(sv, tk, lat)
+                    tk, sl, ii = outstanding.pop(0)
+                    finish(sv, tk, lat, ii, record)
                     free.append(sl)
                 sl = free.pop()
                 Y = slots[sl][: ns[k] * nodes.size].view(ns[k], nodes.size)
-                outstanding.append((sv.submit(Gs[k], "cbl", phi, p, nodes, M_MAX, Y), sl))
-            for tk, sl in outstanding:
-                finish(sv, tk, lat)
+                outstanding.append((sv.submit(Gs[k], "cbl", phi, p, nodes, M_MAX, Y), sl, i))
+            for tk, sl, ii in outstanding:
+                finish(sv, tk, lat, ii, record)
             wall = time.perf_counter() - t0
         return lat, wall
 
@@ -228,7 +234,7 @@ def serving_sample(a, kb, torch):
     sat = R / wall
     rate = 0.8 * sat
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=R))
-    lat, _ = run(arrivals)
+    lat, _ = run(arrivals, bycls)
     kmid = K // 2
     ref_nodes = synth.sample_nodes(ns[kmid], 64, seed=5)
     Yref = torch.empty((ns[kmid], 64), dtype=torch.float32, device="cuda")
@@ -250,6 +256,9 @@ def serving_sample(a, kb, torch):
             "failed_breakdown": failed[0], "failed_breakdown_saturated_run": failed_sat,
             "retried_as_sbl": retried[0],
             "reference_alone_ms": round(float(np.median(alone)), 3),
+            "p50_p99_ms_by_class": {c: [round(float(np.percentile(v, 50)), 1), round(float(np.percentile(v, 99)), 1), len(v)]
+                                    for c, v in sorted(bycls.items())},
+            "columns_per_s_saturated": round(sum(int(r[3].size) for r in reqs) / wall, 1),
             "reference": f"n={ns[kmid]} M=64 exp t=1 cbl tol=1e-6 on an idle server"}
 
 
