@@ -70,6 +70,8 @@ struct Ctrl {
     int32_t steps;           // blocks entering the result
     int32_t breakdown_step;  // -1 or step index
     double est_change;       // stopping rule: relative change at the last check, -1 if none
+    int32_t from_check;      // stopping rule: buffer of the check whose U_k is the result, or -1
+    int32_t reserved;
 };
 
 // Makes a device current for the lifetime of the object and restores the caller's current

@@ -57,8 +57,15 @@ int launch_ctrl_snapshot(Ctrl *dst, const Ctrl *src, int k, cudaStream_t s);
 // Stopping rule of the serving workload: with steps = chk->steps and p = *prev_steps,
 // stops ctrl (stop = 1, steps) when p > 0 and ||U - [Up; 0]||_F <= tol ||U||_F (U, Up:
 // (steps M) x M and (p M) x M row-major); then *prev_steps = steps.  No-op once ctrl stopped.
+// buf: index of U among the alternating check buffers; recorded in ctrl->from_check when the
+// check stops the process.
 int launch_conv_check(const double *U, const double *Up, int M, const Ctrl *chk, int32_t *prev_steps,
-                      double tol, Ctrl *ctrl, cudaStream_t s);
+                      double tol, Ctrl *ctrl, cudaStream_t s, int buf);
+// dst = src, with steps = 0 when src->from_check >= 0 (the final projected solve is then
+// skipped); launch_copy_check_u copies that check's U (buffers of per doubles) into U.
+int launch_ctrl_final(Ctrl *dst, const Ctrl *src, cudaStream_t s);
+int launch_copy_check_u(const double *Uc, int64_t per, double *U, int M, int m, const Ctrl *ctrl,
+                        cudaStream_t s);
 template <typename T>
 int launch_scatter(T *block, int64_t ld, const int32_t *nodes, int M, int col0, T val, cudaStream_t s);
 int launch_marker(int32_t *marker, const int32_t *nodes, int M, cudaStream_t s);

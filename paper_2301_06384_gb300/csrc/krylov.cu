@@ -398,18 +398,25 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                     KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, Ucur,
                                             b.ctrl_chk, c.s, c.quad, b.qscr, qbatch));
                 }
-                KB_TRY(launch_conv_check(Ucur, Uprev, M, b.ctrl_chk, b.chk_prev, c.p.tol, b.ctrl, c.s));
+                KB_TRY(launch_conv_check(Ucur, Uprev, M, b.ctrl_chk, b.chk_prev, c.p.tol, b.ctrl, c.s, nchk % 2));
                 ++nchk;
             }
         }
-        // projected problem: U = phi(H_m) F_1 in FP64
+        // projected problem: U = phi(H_m) F_1 in FP64 (skipped when the stopping rule's last
+        // check formed it: the check's U is copied instead)
+        const Ctrl *cfin = b.ctrl;
+        if (c.p.tol > 0.0) {
+            KB_TRY(launch_ctrl_final(b.ctrl_chk, b.ctrl, c.s));
+            cfin = b.ctrl_chk;
+        }
         if (c.phi == KB_PHI_EXP) {
             const std::vector<double> d = exp_series_coeffs(c.p.t, lam_p, 1e-17);
-            KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam_p, d, b.V0, b.V1, b.V2, b.U, b.ctrl, c.s, b.Hdf));
+            KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam_p, d, b.V0, b.V1, b.V2, b.U, cfin, c.s, b.Hdf));
         } else {
             KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, b.U,
-                                    b.ctrl, c.s, c.quad, b.qscr, qbatch));
+                                    cfin, c.s, c.quad, b.qscr, qbatch));
         }
+        if (c.p.tol > 0.0) KB_TRY(launch_copy_check_u(b.Uc, int64_t(m) * M * M, b.U, M, m, b.ctrl, c.s));
         KB_TRY(launch_check_projected(b.U, int64_t(m) * M * M, projected_bound(c), b.ctrl, c.s));
         KB_TRY(launch_u_convert<C>(b.U, M, W, m, b.Ut, b.ctrl, c.s));
         // assembly: Y = [Q_1 .. Q_m] U
@@ -889,7 +896,7 @@ int apply_device(kb_graph *g, kb_method method, kb_phi phi, const kb_params *par
     // one host control block per column group (sbl may run several groups)
     std::vector<Ctrl> hc;
     const int ngroups = method == KB_SBL ? (M + chunk - 1) / chunk : 1;
-    if (info) hc.assign(ngroups, Ctrl{KB_OK, 0, m, -1, -1.0});
+    if (info) hc.assign(ngroups, Ctrl{KB_OK, 0, m, -1, -1.0, -1, 0});
     switch (method) {
         case KB_CBL:
             c.hctrl = info ? &hc[0] : nullptr;

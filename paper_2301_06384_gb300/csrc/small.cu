@@ -62,6 +62,7 @@ __global__ void k_ctrl_init(Ctrl *c, int steps) {
     c->steps = steps;
     c->breakdown_step = -1;
     c->est_change = -1.0;
+    c->from_check = -1;
 }
 
 template <typename T>
@@ -983,7 +984,7 @@ __global__ void k_ctrl_snapshot(Ctrl *dst, const Ctrl *src, int k) {
 
 __global__ void __launch_bounds__(1024) k_conv_check(const double *U, const double *Up, int M,
                                                      const Ctrl *chk, int32_t *prev_steps,
-                                                     double tol, Ctrl *ctrl) {
+                                                     double tol, Ctrl *ctrl, int buf) {
     if (ctrl->stop) return;   // already stopped (invariant space, breakdown or converged)
     __shared__ double sd[32], sn[32];
     const int steps = chk->steps, ps = *prev_steps;
@@ -1011,6 +1012,7 @@ __global__ void __launch_bounds__(1024) k_conv_check(const double *U, const doub
             if (change <= tol) {
                 ctrl->stop = 1;
                 ctrl->steps = steps;
+                ctrl->from_check = buf;   // U of this check is the result: no second solve
             }
         }
         *prev_steps = steps;
@@ -1025,10 +1027,39 @@ int launch_ctrl_snapshot(Ctrl *dst, const Ctrl *src, int k, cudaStream_t s) {
     return 0;
 }
 
+// The control block the final projected solve runs on: a copy of ctrl with no steps when
+// the stopping rule already formed U at its last check (then k_copy_check_u supplies it).
+__global__ void k_ctrl_final(Ctrl *dst, const Ctrl *src) {
+    Ctrl c = *src;
+    if (c.from_check >= 0) c.steps = 0;
+    *dst = c;
+}
+__global__ void k_copy_check_u(const double *Uc, int64_t per, double *U, int M, const Ctrl *ctrl) {
+    const int b = ctrl->from_check;
+    if (b < 0) return;
+    const int64_t cnt = int64_t(ctrl->steps) * M * M;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < cnt; i += int64_t(gridDim.x) * blockDim.x)
+        U[i] = Uc[b * per + i];
+}
+int launch_ctrl_final(Ctrl *dst, const Ctrl *src, cudaStream_t s) {
+    k_ctrl_final<<<1, 1, 0, s>>>(dst, src);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+int launch_copy_check_u(const double *Uc, int64_t per, double *U, int M, int m, const Ctrl *ctrl,
+                        cudaStream_t s) {
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>((int64_t(m) * M * M + 255) / 256, 4 * int64_t(num_sms()))));
+    k_copy_check_u<<<grid, 256, 0, s>>>(Uc, per, U, M, ctrl);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
 int launch_conv_check(const double *U, const double *Up, int M, const Ctrl *chk, int32_t *prev_steps,
-                      double tol, Ctrl *ctrl, cudaStream_t s) {
+                      double tol, Ctrl *ctrl, cudaStream_t s, int buf) {
     prof_begin(KernelClass::SMALL, s);
-    k_conv_check<<<1, 1024, 0, s>>>(U, Up, M, chk, prev_steps, tol, ctrl);
+    k_conv_check<<<1, 1024, 0, s>>>(U, Up, M, chk, prev_steps, tol, ctrl, buf);
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::SMALL, s, 0, 0);
     return 0;
