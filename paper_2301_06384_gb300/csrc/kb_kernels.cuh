@@ -110,7 +110,10 @@ int launch_assemble_diag(int W, const T *basis, int64_t stride, int nblk, const 
 // per-32-row tile minima; expand(k) marks the rows at distance k.
 int launch_frontier_init(uint8_t *gen, int32_t *tgen, int64_t n, const int32_t *nodes, int M,
                          cudaStream_t s);
-int launch_frontier_expand(const GraphDev &g, uint8_t *gen, int32_t *tgen, int k, cudaStream_t s);
+// alist / acount (optional): the active-tile list of step k - 1 (launch_frontier_list with
+// limit k - 1), which holds every row at distance k - 1; only those tiles are visited.
+int launch_frontier_expand(const GraphDev &g, uint8_t *gen, int32_t *tgen, int k, cudaStream_t s,
+                           const int32_t *alist = nullptr, const int32_t *acount = nullptr);
 // Compacts the 32-row frontier tiles with tgen <= limit into list (increasing tile order,
 // capacity ceil(n / 32)) and their number into *count; one CTA, deterministic.
 int launch_frontier_list(const int32_t *tgen, int64_t n, int limit, int32_t *list, int32_t *count,

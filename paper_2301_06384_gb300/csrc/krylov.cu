@@ -276,6 +276,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
         const int32_t *tg = c.frontier ? b.tgen : nullptr;
         if (c.frontier) {
             KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
+            KB_TRY(launch_frontier_list(b.tgen, n, 0, b.alist, b.acount, c.s));
             // the SpMM and the row-block kernels tile rows differently; rows of L Q_k that
             // the SpMM skips must read as zero in the row-block kernels (the reached set
             // only grows, so zeroing once suffices)
@@ -296,7 +297,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             C *Cl = b.Cloc + 2 * (k - 1) * WW;
             // Q_k is supported on rows within k-1 hops of W; L Q_k within k hops
             if (c.frontier) {
-                KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s, b.alist, b.acount));
                 KB_TRY(launch_frontier_list(b.tgen, n, k, b.alist, b.acount, c.s));
             }
             // block SpMM: W = L Q_k
@@ -434,6 +435,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
             if (c.frontier) {
                 KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
+                KB_TRY(launch_frontier_list(b.tgen, n, 0, b.alist, b.acount, c.s));
                 KB_CUDA_TRY(cudaMemsetAsync(b.wbuf, 0, sizeof(T) * size_t(n) * W, c.s));
             }
             for (int k = 1; k <= m; ++k) {
@@ -447,7 +449,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                 KB_TRY(launch_rowblock<T>(RB_ASM, W, aa, c.s, &grid, M));
                 if (k == m) break;
                 if (c.frontier) {
-                    KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                    KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s, b.alist, b.acount));
                     KB_TRY(launch_frontier_list(b.tgen, n, k, b.alist, b.acount, c.s));
                 }
                 LinEpi<T> e;
@@ -566,7 +568,10 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
         KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W * (c.frontier ? nbuf : 1), c.s));
         KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
         const int32_t *tg = c.frontier ? b.tgen : nullptr;
-        if (c.frontier) KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
+        if (c.frontier) {
+            KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
+            KB_TRY(launch_frontier_list(b.tgen, n, 0, b.alist, b.acount, c.s));
+        }
         // coefficients of steps after an invariant stop are never written: keep them zero
         KB_CUDA_TRY(cudaMemsetAsync(b.c1, 0, sizeof(double) * size_t(m + 1) * W, c.s));
         KB_CUDA_TRY(cudaMemsetAsync(b.c2, 0, sizeof(double) * size_t(m + 1) * W, c.s));
@@ -582,7 +587,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
             T *Pp = k >= 2 ? blk(k - 2) : nullptr;
             T *X = blk(k);
             if (c.frontier) {
-                KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s, b.alist, b.acount));
                 KB_TRY(launch_frontier_list(b.tgen, n, k, b.alist, b.acount, c.s));
             }
             // X = L Q_k - h_{k,k-1} Q_{k-1}, with Q_k = sigma_k P_k; dots <P_k, X> per column
@@ -623,14 +628,17 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
             KB_TRY(launch_ctrl_init(b.ctrl2, m, c.s));
             KB_CUDA_TRY(cudaMemsetAsync(b.basis, 0, sizeof(T) * size_t(n) * W * (c.frontier ? 3 : 1), c.s));
             KB_TRY(launch_scatter<T>(b.basis, W, nodes, M, 0, T(1), c.s));
-            if (c.frontier) KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
+            if (c.frontier) {
+                KB_TRY(launch_frontier_init(b.gen, b.tgen, n, nodes, M, c.s));
+                KB_TRY(launch_frontier_list(b.tgen, n, 0, b.alist, b.acount, c.s));
+            }
             KB_TRY(launch_assemble_diag<T>(W, blk(0), bs, 1, b.omega, n, Y, ldy, M, M, nullptr, c.s, 0, 0));
             for (int k = 1; k < m; ++k) {
                 T *Pk = blk(k - 1);
                 T *Pp = k >= 2 ? blk(k - 2) : nullptr;
                 T *X = blk(k);
                 if (c.frontier) {
-                    KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s));
+                    KB_TRY(launch_frontier_expand(c.g->dev, b.gen, b.tgen, k, c.s, b.alist, b.acount));
                     KB_TRY(launch_frontier_list(b.tgen, n, k, b.alist, b.acount, c.s));
                 }
                 LinEpi<T> e;
@@ -696,9 +704,11 @@ int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int
         // b_k is supported on rows within hop0 + (h - k) hops of W
         const int hop = hop0 + (h - k);
         if (tgen) {
-            KB_TRY(launch_frontier_expand(c.g->dev, gen, tgen, hop, c.s));
-            // (the last step writes zeros on inactive tiles and walks every tile)
-            if (!last) KB_TRY(launch_frontier_list(tgen, n, hop, alist, acount, c.s));
+            // the list of the previous hop holds every row at distance hop - 1; the list of
+            // this hop serves this step's SpMM (the last step writes zeros on inactive tiles
+            // and walks every tile) and the next expansion (the second cheb2 pass)
+            KB_TRY(launch_frontier_expand(c.g->dev, gen, tgen, hop, c.s, alist, acount));
+            KB_TRY(launch_frontier_list(tgen, n, hop, alist, acount, c.s));
         }
         LinEpi<T> e;
         e.tgen = tgen;
@@ -770,6 +780,7 @@ int run_cheb(Common &c, bool squared, const int32_t *nodes, int M, int m, float 
                     KB_CUDA_TRY(cudaMemsetAsync(bufs[i], 0, sizeof(T) * size_t(n) * W, c.s));
                 if (Z) KB_CUDA_TRY(cudaMemsetAsync(Z, 0, sizeof(T) * size_t(n) * W, c.s));
                 KB_TRY(launch_frontier_init(gen, tgen, n, nodes + col0, Mc, c.s));
+                KB_TRY(launch_frontier_list(tgen, n, 0, alist, acount, c.s));
                 tg = tgen;
             }
             if (!squared) {

@@ -1123,6 +1123,27 @@ int launch_frontier_init(uint8_t *gen, int32_t *tgen, int64_t n, const int32_t *
     return 0;
 }
 
+// Same as k_frontier_expand, visiting only the rows of the 32-row tiles active at step k-1
+// (the list made after the previous expansion): the rows at distance k-1 lie there.
+__global__ void __launch_bounds__(256) k_frontier_expand_listed(GraphDev g, uint8_t *gen, int32_t *tgen, int k,
+                                                                const int32_t *__restrict__ alist,
+                                                                const int32_t *__restrict__ acount) {
+    const int64_t total = int64_t(*acount) * ACT_ROWS;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t i = int64_t(__ldg(alist + idx / ACT_ROWS)) * ACT_ROWS + idx % ACT_ROWS;
+        if (i >= g.n || gen[i] != uint8_t(k - 1)) continue;
+        const int beg = __ldg(g.rowptr + i), end = __ldg(g.rowptr + i + 1);
+        for (int p = beg; p < end; ++p) {
+            const int j = __ldg(g.col + p);
+            if (gen[j] == 255) {
+                gen[j] = uint8_t(k);
+                atomicMin(tgen + j / ACT_ROWS, k);
+            }
+        }
+    }
+}
+
 // Stream compaction of the active 32-row tiles in tile order: each thread counts a contiguous
 // range, a block-wide exclusive scan gives its output offset, then it writes its range.
 __global__ void __launch_bounds__(1024) k_frontier_list(const int32_t *__restrict__ tgen, int64_t nact,
@@ -1134,6 +1155,7 @@ __global__ void __launch_bounds__(1024) k_frontier_list(const int32_t *__restric
     const int64_t a0 = int64_t(tid) * per;
     const int64_t a1 = a0 + per < nact ? a0 + per : nact;
     int c = 0;
+#pragma unroll 8
     for (int64_t a = a0; a < a1; ++a) c += __ldg(tgen + a) <= limit ? 1 : 0;
     int incl = c;
     for (int off = 1; off < 32; off <<= 1) {
@@ -1152,6 +1174,7 @@ __global__ void __launch_bounds__(1024) k_frontier_list(const int32_t *__restric
     }
     __syncthreads();
     int pos = (warp > 0 ? wsum[warp - 1] : 0) + incl - c;
+#pragma unroll 8
     for (int64_t a = a0; a < a1; ++a)
         if (__ldg(tgen + a) <= limit) list[pos++] = int32_t(a);
     if (tid == int(blockDim.x) - 1) *count = pos;
@@ -1166,10 +1189,12 @@ int launch_frontier_list(const int32_t *tgen, int64_t n, int limit, int32_t *lis
     return 0;
 }
 
-int launch_frontier_expand(const GraphDev &g, uint8_t *gen, int32_t *tgen, int k, cudaStream_t s) {
+int launch_frontier_expand(const GraphDev &g, uint8_t *gen, int32_t *tgen, int k, cudaStream_t s,
+                           const int32_t *alist, const int32_t *acount) {
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>((g.n + 255) / 256, int64_t(num_sms()) * 8)));
     prof_begin(KernelClass::OTHER, s);
-    k_frontier_expand<<<grid, 256, 0, s>>>(g, gen, tgen, k);
+    if (alist) k_frontier_expand_listed<<<grid, 256, 0, s>>>(g, gen, tgen, k, alist, acount);
+    else k_frontier_expand<<<grid, 256, 0, s>>>(g, gen, tgen, k);
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::OTHER, s, double(g.n) / ACT_ROWS * 4, 0);
     return 0;
