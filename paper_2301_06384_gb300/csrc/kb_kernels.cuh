@@ -91,10 +91,13 @@ int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, 
 // phi(T) e_1 per tridiagonal T (one for gbl, one per column for sbl).  Spline kernel:
 // (eps I + T)^{-s_int} applied after the fractional factor sum_k W_k (sigma_k I + T)^{-1}
 // when tc.q.n > 0; qwork: 2 m tc.q.n doubles per column (nullptr when tc.q.n == 0).
+// series: the full Chebyshev series of e^{-t lambda} (diffusion kernel); when it is longer
+// than one ChebCoef it is applied in chunks (state in work, 4 m doubles per column) and tc.cc
+// is not used.
 int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const double *beta,
                        const double *sigma, int phi_kind, double eps, int s_int, double lam,
                        const TriCoef &tc, double *omega, double *work, double *qwork, Ctrl *ctrl,
-                       double bound, cudaStream_t s);
+                       double bound, cudaStream_t s, const std::vector<double> *series = nullptr);
 template <typename T>
 int launch_axpy_colnorm(int W, T *X, const T *P, const double *a, int64_t n, double *parts,
                         int *grid_out, const Ctrl *ctrl, const int32_t *tgen, int limit,

@@ -540,12 +540,12 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
     const int pgrid = std::max(spmm_max_grid<T>(W), axpy_max_grid());
     auto tc = std::make_unique<TriCoef>();
     int nquad = 0;
+    std::vector<double> series;
     if (c.phi == KB_PHI_EXP) {
-        const std::vector<double> d = exp_series_coeffs(c.p.t, c.g->lambda_proj, 1e-17);
-        if (int(d.size()) > ChebCoef::CAP)
-            return fail(KB_ERR_UNSUPPORTED, "t * Lambda too large for the tridiagonal Chebyshev series");
-        tc->cc.n = int(d.size());
-        for (int j = 0; j < tc->cc.n; ++j) tc->cc.d[j] = d[j];
+        series = exp_series_coeffs(c.p.t, c.g->lambda_proj, 1e-17);
+        // longer series are applied in chunks by launch_tridiag_phi
+        tc->cc.n = int(std::min<size_t>(series.size(), ChebCoef::CAP));
+        for (int j = 0; j < tc->cc.n; ++j) tc->cc.d[j] = series[j];
     } else {
         tc->q.n = 0;
         tc->q.s_int = c.s_int;
@@ -619,7 +619,7 @@ int run_lanczos_scalar(Common &c, bool gbl, const int32_t *nodes, int M, int m, 
         }
         KB_TRY(launch_tridiag_phi(W, M, m, gbl ? 1 : 0, b.alpha, b.beta, b.sigma, int(c.phi),
                                   c.p.eps, c.s_int, c.g->lambda_proj, *tc, b.omega, b.work, b.qwork, b.ctrl,
-                                  projected_bound(c), c.s));
+                                  projected_bound(c), c.s, c.phi == KB_PHI_EXP ? &series : nullptr));
         if (!two) {
             KB_TRY(launch_assemble_diag<T>(W, b.basis, bs, m, b.omega, n, Y, ldy, M, M, tg, c.s));
         } else {

@@ -142,6 +142,20 @@ __device__ void tri_inv_upper_inplace(S *A, int lda, int M, S *t) {
     }
 }
 
+// 1/d for a positive double d by Newton's iteration for the reciprocal, r <- r + r (1 - d r),
+// from the single-precision reciprocal: two steps take its 2^-23 relative error to the
+// FP64 rounding level (the error squares at each step).  The FP64 division it replaces is
+// a long dependent sequence on this part's FP64 unit; this is four FMAs.  Outside the
+// normal single-precision range the division is used.
+__device__ __forceinline__ double recip_newton(double d) {
+    if (!(d > 1e-36 && d < 1e36)) return 1.0 / d;
+    double r = double(__frcp_rn(float(d)));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
 // Cholesky G = R^T R of an M x M symmetric matrix in shared memory, upper R overwriting A
 // and the lower part zeroed.  Square-root-free form: step j needs the pivot d_j (the
 // diagonal of the current Schur complement) and one reciprocal; the Schur complement update
@@ -169,7 +183,7 @@ __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, d
         if (!(d > thr)) {
             if (lane == 0) bad[0] = 1;
         } else {
-            const double dinv = 1.0 / d;
+            const double dinv = recip_newton(d);
             for (int c = 1 + lane; c < M; c += 32) srow[0][c] = A[c] * dinv;
             if (lane == 0) piv[0] = d;
         }
@@ -188,7 +202,7 @@ __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, d
                 if (!(d > thr)) {
                     if (lane == 0) bad[(j + 1) & 1] = 1;
                 } else {
-                    const double dinv = 1.0 / d;
+                    const double dinv = recip_newton(d);
                     double *sn = srow[(j + 1) & 1];
                     for (int c = j + 2 + lane; c < M; c += 32) sn[c] = A[(j + 1) * lda + c] * dinv;
                     if (lane == 0) piv[j + 1] = d;
@@ -637,6 +651,53 @@ __global__ void k_lanczos_beta(const double *parts, int nparts, int W, int M, in
 // when 6 m doubles fit (m <= TRI_SMEM_M), else in the global scratch work (4 m per column).
 constexpr int TRI_SMEM_M = 1024;
 constexpr int TRI_THREADS = 128;
+
+// Chebyshev series of e^{-t lambda} applied to e_1, terms [j0, j0 + cc.n) of it, for series
+// longer than one ChebCoef: V_j (term j) lives in slot j % 3 of the column's global state
+// (3 m doubles), the partial sum u in the fourth m doubles (the layout k_tridiag_phi reads
+// with u_ready).  A = I - (2/lam) T; V_0 = e_1, V_1 = A e_1, V_j = 2 A V_{j-1} - V_{j-2}.
+__global__ void __launch_bounds__(TRI_THREADS) k_tridiag_exp_chunk(int W, int M, int m, int gbl,
+                                                                   const double *alpha,
+                                                                   const double *beta, double lam,
+                                                                   ChebCoef cc, int j0,
+                                                                   double *work, const Ctrl *ctrl) {
+    const int c = blockIdx.x;
+    if (c >= (gbl ? 1 : M)) return;
+    const int s = gbl ? ctrl->steps : m;
+    double *slot[3] = {work + int64_t(c) * 4 * m, work + int64_t(c) * 4 * m + m, work + int64_t(c) * 4 * m + 2 * m};
+    double *u = work + int64_t(c) * 4 * m + 3 * m;
+    auto a_of = [&](int k) { return alpha[int64_t(k) * W + c]; };
+    auto b_of = [&](int k) { return beta[int64_t(k) * W + c]; };
+    const double g = 2.0 / lam;
+    for (int q = 0; q < cc.n; ++q) {
+        const int j = j0 + q;
+        double *vn = slot[j % 3];
+        if (j == 0) {
+            for (int k = threadIdx.x; k < m; k += blockDim.x) {
+                vn[k] = k == 0 ? 1.0 : 0.0;
+                u[k] = k == 0 ? cc.d[q] : 0.0;
+                slot[1][k] = 0.0;
+                slot[2][k] = 0.0;
+            }
+        } else {
+            const double *pc = slot[(j - 1) % 3];
+            const double *pp = slot[(j + 1) % 3];   // V_{j-2} (slot (j - 2) % 3)
+            for (int k = threadIdx.x; k < s; k += blockDim.x) {
+                double tv = a_of(k) * pc[k];
+                if (k > 0) tv += b_of(k) * pc[k - 1];
+                if (k + 1 < s) tv += b_of(k + 1) * pc[k + 1];
+                const double av = pc[k] - g * tv;
+                const double v = j == 1 ? av : 2.0 * av - pp[k];
+                vn[k] = v;
+                u[k] += cc.d[q] * v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// u_ready: the series part of e^{-t T} e_1 was formed by k_tridiag_exp_chunk in work; only
+// the bound check and the scaling into omega run here.
 __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m, int gbl,
                                                              const double *alpha,
                                                              const double *beta,
@@ -644,7 +705,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m
                                                              double eps, int s_int, double lam,
                                                              TriCoef tc, double *omega,
                                                              double *work, double *qwork,
-                                                             Ctrl *ctrl, double bound) {
+                                                             Ctrl *ctrl, double bound, int u_ready) {
     const ChebCoef &cc = tc.cc;
     const int c = blockIdx.x;
     const int ncol = gbl ? 1 : M;
@@ -654,7 +715,7 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m
     }
     const int s = gbl ? ctrl->steps : m;
     extern __shared__ __align__(16) double tsm[];
-    const bool in_smem = m <= TRI_SMEM_M;
+    const bool in_smem = m <= TRI_SMEM_M && !u_ready;
     double *v0, *v1, *v2, *u;
     const double *av, *bv;
     int64_t st;   // stride of av / bv
@@ -673,9 +734,12 @@ __global__ void __launch_bounds__(TRI_THREADS) k_tridiag_phi(int W, int M, int m
     // b_of(k) couples rows k-1 and k
     auto a_of = [&](int k) { return av[int64_t(k) * st]; };
     auto b_of = [&](int k) { return bv[int64_t(k) * st]; };
-    for (int k = threadIdx.x; k < m; k += blockDim.x) { v0[k] = 0.0; v1[k] = 0.0; v2[k] = 0.0; u[k] = 0.0; }
+    if (!u_ready)
+        for (int k = threadIdx.x; k < m; k += blockDim.x) { v0[k] = 0.0; v1[k] = 0.0; v2[k] = 0.0; u[k] = 0.0; }
     __syncthreads();
-    if (phi_kind == KB_PHI_EXP) {
+    if (u_ready) {
+        // (series formed in chunks)
+    } else if (phi_kind == KB_PHI_EXP) {
         // v0 = e_1, v1 = A e_1, v_{j+1} = 2 A v_j - v_{j-1}, A = I - (2/lam) T
         const double g = 2.0 / lam;
         if (threadIdx.x == 0) { v0[0] = 1.0; u[0] = cc.d[0]; }
@@ -1272,17 +1336,30 @@ int launch_lanczos_beta(const double *parts, int nparts, int W, int M, int gbl, 
 int launch_tridiag_phi(int W, int M, int m, int gbl, const double *alpha, const double *beta,
                        const double *sigma, int phi_kind, double eps, int s_int, double lam,
                        const TriCoef &tc, double *omega, double *work, double *qwork, Ctrl *ctrl,
-                       double bound, cudaStream_t s) {
+                       double bound, cudaStream_t s, const std::vector<double> *series) {
     prof_begin(KernelClass::PROJECTED, s);
-    const size_t smem = m <= TRI_SMEM_M ? sizeof(double) * 6 * size_t(m) : 0;
+    int launches = 1, u_ready = 0;
+    if (phi_kind == KB_PHI_EXP && series && int(series->size()) > ChebCoef::CAP) {
+        // a series longer than one parameter block: chunks of CAP terms, state in work
+        for (size_t j0 = 0; j0 < series->size(); j0 += ChebCoef::CAP) {
+            ChebCoef cc{};
+            cc.n = int(std::min<size_t>(ChebCoef::CAP, series->size() - j0));
+            for (int q = 0; q < cc.n; ++q) cc.d[q] = (*series)[j0 + q];
+            k_tridiag_exp_chunk<<<gbl ? 1 : W, TRI_THREADS, 0, s>>>(W, M, m, gbl, alpha, beta, lam, cc,
+                                                                    int(j0), work, ctrl);
+            ++launches;
+        }
+        u_ready = 1;
+    }
+    const size_t smem = (m <= TRI_SMEM_M && !u_ready) ? sizeof(double) * 6 * size_t(m) : 0;
     static const cudaError_t attr = cudaFuncSetAttribute(
         k_tridiag_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(double) * 6 * TRI_SMEM_M));
     (void)attr;
     k_tridiag_phi<<<gbl ? 1 : W, TRI_THREADS, smem, s>>>(W, M, m, gbl, alpha, beta, sigma,
                                                          phi_kind, eps, s_int, lam, tc, omega,
-                                                         work, qwork, ctrl, bound);
+                                                         work, qwork, ctrl, bound, u_ready);
     KB_CUDA_TRY(cudaGetLastError());
-    prof_end(KernelClass::PROJECTED, s, 0, 0);
+    prof_end(KernelClass::PROJECTED, s, 0, 0, launches);
     return 0;
 }
 

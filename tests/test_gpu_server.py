@@ -136,8 +136,13 @@ def test_workspace_bytes_matches_layout(kb, graphs):
     c10 = kb.kb_workspace_bytes(G, "gbl", "exp", p32, 64, 10)
     c20 = kb.kb_workspace_bytes(G, "gbl", "exp", p32, 64, 20)
     assert abs((c20 - c10) - 10 * g.n * 64 * 4) < 0.05 * (c20 - c10)
+    # non-integer s adds the per-node scratch of the quadrature (one block factorisation per
+    # node, at most 2 x SMs nodes at a time); s >= 65 is not supported
+    w_int = kb.kb_workspace_bytes(G, "cbl", "spline", kb.make_params(eps=0.1, s=2.0), 4, 5)
+    w_frac = kb.kb_workspace_bytes(G, "cbl", "spline", kb.make_params(eps=0.1, s=1.5), 4, 5)
+    assert w_frac > w_int
     with pytest.raises(kb.KbError):
-        kb.kb_workspace_bytes(G, "cbl", "spline", kb.make_params(eps=0.1, s=1.5), 4, 5)
+        kb.kb_workspace_bytes(G, "cbl", "spline", kb.make_params(eps=0.1, s=65.5), 4, 5)
 
 
 def test_server_falls_back_to_sbl_on_block_breakdown(kb):
