@@ -175,7 +175,9 @@ def serving_sample(a, kb, torch):
         reqs.append((k, phi, p, nodes))
     # latency per request class (graph family x kernel), from the Poisson run
     cls = [("rgg" if k % 2 == 0 else "ba") + "-" + phi for (k, phi, _, _) in reqs]
-    window = 64
+    # output slots for the requests in flight: at most 16 GB of them (with the 2e6-node graphs
+    # of the full serving stream that is 15 slots), the rest of the memory for the solves
+    window = int(max(8, min(64, 16e9 // (max(ns) * 128 * 4))))
     slots = [torch.empty(max(ns) * 128, dtype=torch.float32, device="cuda") for _ in range(window)]
 
     failed = [0]

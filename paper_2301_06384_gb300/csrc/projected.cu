@@ -195,36 +195,62 @@ __device__ void chol_lower_inplace(double *A, int M) {
     }
 }
 
+// Lane groups for the triangular solves of k_bt_spline: a group of TPC consecutive lanes
+// (a power of two dividing 32) works on one row or column, each lane taking every TPC-th term
+// of the dot product; the group's partial sums meet by shuffles.  All threads run the same
+// loop bounds (idle groups on zeros), so the full-warp shuffles are uniform.
+__device__ __forceinline__ int tpc_for(int M) {
+    int t = 1;
+    while (t < 32 && 2 * t * M <= 1024) t *= 2;
+    return t;
+}
+__device__ __forceinline__ double group_sum(double v, int tpc) {
+    for (int off = 1; off < tpc; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
 // rhs_in_u: U already holds the right-hand side (steps blocks); else U starts as F_1.
+// One CTA of 1024 threads.  The dense block products (the Schur complement update of each
+// diagonal block, and the coupling terms of the substitutions) run over all threads, one
+// output each; the triangular solves (the sub-diagonal factor rows, and forward / backward
+// substitution per right-hand-side column) give each row or column a lane group, so their
+// dependent chains are TPC times shorter than with one thread per column.
 __global__ void __launch_bounds__(1024)
 k_bt_spline(const double *Hd, const double *Hs, int M, double eps, int s_int, double *Ld,
             double *Ls, double *Yw, double *U, const Ctrl *ctrl, int rhs_in_u) {
     const int steps = ctrl->steps;
     const int64_t MM = int64_t(M) * M;
+    const int tpc = tpc_for(M);
+    const int grp = threadIdx.x / tpc, sub = threadIdx.x % tpc;
+    const bool gact = grp < M;                 // this lane group has a row / column
+    __shared__ double rd[128];                 // reciprocal diagonal of the current D block
     // factor eps I + H = L L^T, L block lower bidiagonal (Ld diagonal, Ls sub-diagonal blocks)
     for (int r = 0; r < steps; ++r) {
         double *D = Ld + r * MM;
         for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
             const int i = idx / M, j = idx % M;
             double v = Hd[r * MM + idx] + (i == j ? eps : 0.0);
-            if (r > 0) {
+            if (r > 0 && j <= i) {
                 const double *P = Ls + (r - 1) * MM;
-                for (int k = 0; k < M; ++k) v -= P[i * M + k] * P[j * M + k];
+                for (int k = 0; k < M; ++k) v = fma(-P[i * M + k], P[j * M + k], v);
             }
             D[idx] = v;
         }
         __syncthreads();
         chol_lower_inplace(D, M);
         if (r + 1 < steps) {
-            // Ls_r = H_{r+1,r} D^{-T}: row i solves D x = H_{r+1,r}[i,:]^T
+            // Ls_r = H_{r+1,r} D^{-T}: row i solves D x = H_{r+1,r}[i,:]^T (lane group per row)
+            for (int i = threadIdx.x; i < M; i += blockDim.x) rd[i] = 1.0 / D[i * M + i];
+            __syncthreads();
             const double *Hsub = Hs + r * MM;
             double *P = Ls + r * MM;
-            for (int i = threadIdx.x; i < M; i += blockDim.x) {
-                for (int j = 0; j < M; ++j) {
-                    double v = Hsub[i * M + j];
-                    for (int k = 0; k < j; ++k) v -= D[j * M + k] * P[i * M + k];
-                    P[i * M + j] = v / D[j * M + j];
-                }
+            for (int j = 0; j < M; ++j) {
+                double part = 0.0;
+                if (gact)
+                    for (int k = sub; k < j; k += tpc) part = fma(D[j * M + k], P[grp * M + k], part);
+                part = group_sum(part, tpc);
+                if (gact && sub == 0) P[grp * M + j] = (Hsub[grp * M + j] - part) * rd[j];
+                __syncwarp();
             }
         }
         __syncthreads();
@@ -243,34 +269,51 @@ k_bt_spline(const double *Hd, const double *Hs, int M, double eps, int s_int, do
         for (int r = 0; r < steps; ++r) {
             const double *D = Ld + r * MM;
             double *Y = Yw + r * MM;
-            for (int c = threadIdx.x; c < M; c += blockDim.x) {
-                for (int i = 0; i < M; ++i) {
-                    double v = U[r * MM + int64_t(i) * M + c];
-                    if (r > 0) {
-                        const double *P = Ls + (r - 1) * MM;
-                        const double *Yp = Yw + (r - 1) * MM;
-                        for (int k = 0; k < M; ++k) v -= P[i * M + k] * Yp[k * M + c];
-                    }
-                    for (int k = 0; k < i; ++k) v -= D[i * M + k] * Y[k * M + c];
-                    Y[i * M + c] = v / D[i * M + i];
+            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+                const int i = idx / M, c = idx % M;
+                double v = U[r * MM + idx];
+                if (r > 0) {
+                    const double *P = Ls + (r - 1) * MM;
+                    const double *Yp = Yw + (r - 1) * MM;
+                    for (int k = 0; k < M; ++k) v = fma(-P[i * M + k], Yp[k * M + c], v);
                 }
+                Y[idx] = v;
+            }
+            for (int i = threadIdx.x; i < M; i += blockDim.x) rd[i] = 1.0 / D[i * M + i];
+            __syncthreads();
+            for (int i = 0; i < M; ++i) {
+                double part = 0.0;
+                if (gact)
+                    for (int k = sub; k < i; k += tpc) part = fma(D[i * M + k], Y[k * M + grp], part);
+                part = group_sum(part, tpc);
+                if (gact && sub == 0) Y[i * M + grp] = (Y[i * M + grp] - part) * rd[i];
+                __syncwarp();
             }
             __syncthreads();
         }
         // backward: U_r = D_r^{-T} (Y_r - Ls_r^T U_{r+1})
         for (int r = steps - 1; r >= 0; --r) {
             const double *D = Ld + r * MM;
-            for (int c = threadIdx.x; c < M; c += blockDim.x) {
-                for (int i = M - 1; i >= 0; --i) {
-                    double v = Yw[r * MM + int64_t(i) * M + c];
-                    if (r + 1 < steps) {
-                        const double *P = Ls + r * MM;
-                        const double *Un = U + (r + 1) * MM;
-                        for (int k = 0; k < M; ++k) v -= P[k * M + i] * Un[k * M + c];
-                    }
-                    for (int k = i + 1; k < M; ++k) v -= D[k * M + i] * U[r * MM + int64_t(k) * M + c];
-                    U[r * MM + int64_t(i) * M + c] = v / D[i * M + i];
+            double *Ur = U + r * MM;
+            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+                const int i = idx / M, c = idx % M;
+                double v = Yw[r * MM + idx];
+                if (r + 1 < steps) {
+                    const double *P = Ls + r * MM;
+                    const double *Un = U + (r + 1) * MM;
+                    for (int k = 0; k < M; ++k) v = fma(-P[k * M + i], Un[k * M + c], v);
                 }
+                Ur[idx] = v;
+            }
+            for (int i = threadIdx.x; i < M; i += blockDim.x) rd[i] = 1.0 / D[i * M + i];
+            __syncthreads();
+            for (int i = M - 1; i >= 0; --i) {
+                double part = 0.0;
+                if (gact)
+                    for (int k = i + 1 + sub; k < M; k += tpc) part = fma(D[k * M + i], Ur[k * M + grp], part);
+                part = group_sum(part, tpc);
+                if (gact && sub == 0) Ur[i * M + grp] = (Ur[i * M + grp] - part) * rd[i];
+                __syncwarp();
             }
             __syncthreads();
         }
