@@ -156,6 +156,9 @@ __device__ __forceinline__ double recip_newton(double d) {
     return fma(r, e, r);
 }
 
+__device__ __forceinline__ double chol_recip(double d) { return recip_newton(d); }
+__device__ __forceinline__ float chol_recip(float d) { return 1.0f / d; }
+
 // Cholesky G = R^T R of an M x M symmetric matrix in shared memory, upper R overwriting A
 // and the lower part zeroed.  Square-root-free form: step j needs the pivot d_j (the
 // diagonal of the current Schur complement) and one reciprocal; the Schur complement update
@@ -171,19 +174,19 @@ __device__ __forceinline__ double recip_newton(double d) {
 // barrier that ends step j-1; the flag warp 0 writes during step j is the other one, so no
 // thread can read a flag in the same barrier interval in which it is written (all threads
 // leave at the same step).
-__device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, double maxdiag,
-                                   double *t, int *bad) {
-    double *srow[2] = {t, t + M};   // u_j / d_j, double-buffered by the parity of j
-    double *piv = t + 2 * M;        // d_j
+template <typename S>
+__device__ bool chol_upper_inplace(S *A, int lda, int M, S piv_rel2, S maxdiag, S *t, int *bad) {
+    S *srow[2] = {t, t + M};   // u_j / d_j, double-buffered by the parity of j
+    S *piv = t + 2 * M;        // d_j
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const double thr = piv_rel2 * maxdiag;
+    const S thr = piv_rel2 * maxdiag;
     // pivot row 0
     if (warp == 0) {
-        const double d = A[0];
+        const S d = A[0];
         if (!(d > thr)) {
             if (lane == 0) bad[0] = 1;
         } else {
-            const double dinv = recip_newton(d);
+            const S dinv = chol_recip(d);
             for (int c = 1 + lane; c < M; c += 32) srow[0][c] = A[c] * dinv;
             if (lane == 0) piv[0] = d;
         }
@@ -191,19 +194,19 @@ __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, d
     __syncthreads();
     for (int j = 0; j < M; ++j) {
         if (bad[j & 1]) return false;
-        const double *sr = srow[j & 1];
+        const S *sr = srow[j & 1];
         if (warp == 0) {
             if (j + 1 < M) {
                 // the next pivot row: A[j+1][c] -= u_{j,j+1} u_{j,c} / d_j, c >= j+1
-                const double ujn = A[j * lda + j + 1];
+                const S ujn = A[j * lda + j + 1];
                 for (int c = j + 1 + lane; c < M; c += 32) A[(j + 1) * lda + c] -= ujn * sr[c];
                 __syncwarp();
-                const double d = A[(j + 1) * lda + j + 1];
+                const S d = A[(j + 1) * lda + j + 1];
                 if (!(d > thr)) {
                     if (lane == 0) bad[(j + 1) & 1] = 1;
                 } else {
-                    const double dinv = recip_newton(d);
-                    double *sn = srow[(j + 1) & 1];
+                    const S dinv = chol_recip(d);
+                    S *sn = srow[(j + 1) & 1];
                     for (int c = j + 2 + lane; c < M; c += 32) sn[c] = A[(j + 1) * lda + c] * dinv;
                     if (lane == 0) piv[j + 1] = d;
                 }
@@ -227,16 +230,16 @@ __device__ bool chol_upper_inplace(double *A, int lda, int M, double piv_rel2, d
     // (no pivot is examined during the last step: the flags are final here)
     if (bad[0] | bad[1]) return false;
     // R_jj = sqrt(d_j), R_jc = u_jc / sqrt(d_j)
-    double *rinv = srow[0];
+    S *rinv = srow[0];
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        const double r = sqrt(piv[j]);
+        const S r = sqrt(piv[j]);
         piv[j] = r;
-        rinv[j] = 1.0 / r;
+        rinv[j] = S(1) / r;
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
         const int i = idx / M, j = idx % M;
-        if (j < i) A[i * lda + j] = 0.0;
+        if (j < i) A[i * lda + j] = S(0);
         else if (j == i) A[i * lda + j] = piv[i];
         else A[i * lda + j] *= rinv[i];
     }
@@ -378,7 +381,37 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
         return;
     }
     // ---- general CholeskyQR pass
-    if (!chol_upper_inplace(A, lda, M, piv_rel2, maxdiag, t, pivot_bad)) {
+    // Pass 1 of the FP32 path first factors G in FP32 (the FP32 pipe runs 64 times the FP64
+    // rate): the first pass only has to bring X close to orthonormal, the second pass
+    // corrects what is left (its first-order form when max |G2 - I| < 1e-4, a full
+    // factorisation otherwise), and R1 below is the FP64 inverse of the applied inverse
+    // whatever R it came from.  A pivot below 1e-5 of the largest diagonal entry is not
+    // trusted in FP32: the factorisation is then redone in FP64 (which alone decides a
+    // breakdown).
+    bool factored = false;
+    if (sizeof(T) == 4 && pass == 1) {
+        float *Af = reinterpret_cast<float *>(Sf);   // Sf is free until the inverse below
+        float *tf = reinterpret_cast<float *>(t);
+        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+            const int i = idx / M, j = idx % M;
+            Af[i * lda + j] = float(A[i * lda + j]);
+        }
+        __syncthreads();
+        if (chol_upper_inplace<float>(Af, lda, M, 1e-5f, float(maxdiag), tf, pivot_bad)) {
+            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
+                const int i = idx / M, j = idx % M;
+                A[i * lda + j] = (j >= i) ? double(Af[i * lda + j]) : 0.0;
+            }
+            factored = true;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            pivot_bad[0] = 0;
+            pivot_bad[1] = 0;
+        }
+        __syncthreads();
+    }
+    if (!factored && !chol_upper_inplace<double>(A, lda, M, piv_rel2, maxdiag, t, pivot_bad)) {
         if (threadIdx.x == 0) {
             ctrl->status = KB_ERR_BREAKDOWN;
             ctrl->stop = 1;
