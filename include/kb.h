@@ -333,7 +333,8 @@ int kb_workspace_bytes(kb_graph *g, kb_method method, kb_phi phi, const kb_param
  * kb_server_create starts `streams` host worker threads on `device`, each owning one CUDA
  * stream.  Requests start in submission order; a worker starts the oldest pending request
  * once its scratch (kb_workspace_bytes) fits in `memory_budget` next to the requests in
- * flight (memory_budget <= 0: three quarters of the free device memory at creation), runs
+ * flight (memory_budget <= 0: three quarters of the device memory available at creation,
+ * free memory plus what the stream-ordered pool holds unused), runs
  * it on its stream and waits for it, so at most `streams` solves run concurrently and
  * requests may complete out of order.
  *

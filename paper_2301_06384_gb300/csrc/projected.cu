@@ -24,9 +24,23 @@ namespace {
 
 constexpr int TC = 4;    // output columns per CTA (many small CTAs: the FP64 work spreads over all SMs)
 
-__global__ void k_cheb_bt_seed(double *V0, double *U, int M, double d0) {
+// U = 0, only when the solve has steps: the stopping rule's later checks run with no steps
+// and must leave the buffer of the check that stopped the process as it is.
+__global__ void k_zero_if_active(double *U, int64_t count, const Ctrl *ctrl) {
+    if (ctrl->steps <= 0) return;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * blockDim.x)
+        U[i] = 0.0;
+}
+int zero_if_active(double *U, int64_t count, const Ctrl *ctrl, cudaStream_t s) {
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, 4 * int64_t(num_sms()))));
+    k_zero_if_active<<<grid, 256, 0, s>>>(U, count, ctrl);
+    return 0;
+}
+
+__global__ void k_cheb_bt_seed(double *V0, double *U, int M, double d0, const Ctrl *ctrl) {
     const int i = threadIdx.x + blockIdx.x * blockDim.x;
-    if (i < M) {
+    if (ctrl->steps > 0 && i < M) {
         V0[int64_t(i) * M + i] = 1.0;
         U[int64_t(i) * M + i] = d0;
     }
@@ -114,9 +128,9 @@ __global__ void k_split_df(const double *__restrict__ H, dfl *__restrict__ out, 
         out[i] = dfl_from(H[i]);
 }
 
-__global__ void k_cheb_bt_seed_df(dfl *V0, double *U, int M, double d0) {
+__global__ void k_cheb_bt_seed_df(dfl *V0, double *U, int M, double d0, const Ctrl *ctrl) {
     const int i = threadIdx.x + blockIdx.x * blockDim.x;
-    if (i < M) {
+    if (ctrl->steps > 0 && i < M) {
         V0[int64_t(i) * M + i] = dfl{1.f, 0.f};
         U[int64_t(i) * M + i] = d0;
     }
@@ -439,9 +453,9 @@ int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
         KB_CUDA_TRY(cudaMemsetAsync(V0, 0, bytes, s));
         KB_CUDA_TRY(cudaMemsetAsync(V1, 0, bytes, s));
         KB_CUDA_TRY(cudaMemsetAsync(V2, 0, bytes, s));
-        KB_CUDA_TRY(cudaMemsetAsync(U, 0, bytes, s));
+        zero_if_active(U, int64_t(m) * M * M, ctrl, s);
         dfl *pp = reinterpret_cast<dfl *>(V2), *pc = reinterpret_cast<dfl *>(V0), *pn = reinterpret_cast<dfl *>(V1);
-        k_cheb_bt_seed_df<<<(M + 127) / 128, 128, 0, s>>>(pc, U, M, d[0]);
+        k_cheb_bt_seed_df<<<(M + 127) / 128, 128, 0, s>>>(pc, U, M, d[0], ctrl);
         const size_t smem = sizeof(dfl) * 3 * M * TC;
         const dfl g = dfl_from(2.0 / lam);
         for (size_t j = 0; j + 1 < d.size(); ++j) {
@@ -458,8 +472,8 @@ int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
     KB_CUDA_TRY(cudaMemsetAsync(V0, 0, bytes, s));
     KB_CUDA_TRY(cudaMemsetAsync(V1, 0, bytes, s));
     KB_CUDA_TRY(cudaMemsetAsync(V2, 0, bytes, s));
-    KB_CUDA_TRY(cudaMemsetAsync(U, 0, bytes, s));
-    k_cheb_bt_seed<<<(M + 127) / 128, 128, 0, s>>>(V0, U, M, d[0]);
+    zero_if_active(U, int64_t(m) * M * M, ctrl, s);
+    k_cheb_bt_seed<<<(M + 127) / 128, 128, 0, s>>>(V0, U, M, d[0], ctrl);
     const size_t smem = sizeof(double) * 3 * M * TC;
     // function-local static: initialised once, thread-safe (several serving workers)
     static const cudaError_t attr = cudaFuncSetAttribute(
@@ -486,7 +500,7 @@ int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double ep
     int launches = 1;
     if (q && q->n > 0) {
         if (!qscr || qbatch < 1) return fail(KB_ERR_ARG, "spline quadrature without scratch");
-        KB_CUDA_TRY(cudaMemsetAsync(U, 0, sizeof(double) * size_t(m) * M * M, s));
+        zero_if_active(U, int64_t(m) * M * M, ctrl, s);
         const int acc_grid = int(std::min<int64_t>((int64_t(m) * M * M + 255) / 256, 4 * int64_t(num_sms())));
         for (int j0 = 0; j0 < q->n; j0 += qbatch) {
             const int nb = std::min(qbatch, q->n - j0);
@@ -497,7 +511,10 @@ int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double ep
         if (s_int > 0) k_bt_spline<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, s_int, Ld, Ls, Yw, U, ctrl, 1);
         else --launches;
     } else {
+        // (blocks past the steps stay zero: the bound check reads all m of them)
+        zero_if_active(U, int64_t(m) * M * M, ctrl, s);
         k_bt_spline<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, s_int, Ld, Ls, Yw, U, ctrl, 0);
+        ++launches;
     }
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::PROJECTED, s, 0, 0, launches);

@@ -132,8 +132,19 @@ extern "C" int kb_server_create(int32_t device, const kb_server_config *cfg, kb_
         if (cfg->memory_budget > 0) {
             budget = size_t(cfg->memory_budget);
         } else {
+            // the solves allocate from the device's stream-ordered pool, which keeps what
+            // earlier solves freed (release threshold raised): memory it holds but does not
+            // use counts as available too
             size_t fr = 0, tot = 0;
             KB_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+                uint64_t reserved = 0, used = 0;
+                if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+                    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess &&
+                    reserved > used)
+                    fr += size_t(reserved - used);
+            }
             budget = fr / 4 * 3;
         }
         auto *sv = new kb_server();

@@ -1134,7 +1134,8 @@ __global__ void k_ctrl_final(Ctrl *dst, const Ctrl *src) {
 __global__ void k_copy_check_u(const double *Uc, int64_t per, double *U, int M, const Ctrl *ctrl) {
     const int b = ctrl->from_check;
     if (b < 0) return;
-    const int64_t cnt = int64_t(ctrl->steps) * M * M;
+    (void)M;
+    const int64_t cnt = per;   // the check zeroed its whole buffer: copy it all
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < cnt; i += int64_t(gridDim.x) * blockDim.x)
         U[i] = Uc[b * per + i];
 }
