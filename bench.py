@@ -44,6 +44,14 @@ def parse():
     ap.add_argument("--M", type=int, default=64)
     ap.add_argument("--m", type=int, default=30)
     ap.add_argument("--ts", default="0.5,2.0")
+    ap.add_argument("--graph", default="rgg", choices=["rgg", "ba"],
+                    help="random geometric graph (mean degree 10) or Barabasi-Albert (5 edges per node)")
+    ap.add_argument("--weighted", action="store_true", help="BA edge weights uniform in [0.5, 1.5]")
+    ap.add_argument("--phi", default="exp", choices=["exp", "spline"],
+                    help="diffusion kernel e^{-tL} (times --ts) or spline (eps I + L)^{-s}")
+    ap.add_argument("--eps", type=float, default=0.01)
+    ap.add_argument("--s", type=float, default=2.0)
+    ap.add_argument("--reorth", type=int, default=0, help="cbl reorthogonalisation: 0, 1 full, 2 local")
     ap.add_argument("--methods", default=",".join(METHODS))
     ap.add_argument("--graph-seed", type=int, default=1)
     ap.add_argument("--node-seed", type=int, default=2)
@@ -71,12 +79,34 @@ def parse():
     return ap.parse_args()
 
 
+def kernel_times(a):
+    """The diffusion times of the step's solves (one placeholder for the spline kernel)."""
+    return [float(x) for x in a.ts.split(",")] if a.phi == "exp" else [0.0]
+
+
+def phi_kwargs(a, t):
+    return dict(t=t) if a.phi == "exp" else dict(eps=a.eps, s=a.s)
+
+
+def bench_graph(a):
+    import synth
+    if a.graph == "ba":
+        return synth.barabasi_albert_graph(a.n, 5, seed=a.graph_seed, weighted=a.weighted)
+    return synth.random_geometric_graph(a.n, 10, seed=a.graph_seed)
+
+
 def workload_config(a):
-    return {"workload": f"rgg n={a.n} mean_degree=10 M={a.M} m={a.m} exp t={a.ts} "
-                        f"methods={a.methods}",
-            "graph": "random geometric graph, unit square, cell-sorted node order",
+    kern = f"exp t={a.ts}" if a.phi == "exp" else f"spline eps={a.eps:g} s={a.s:g}"
+    gname = ("rgg n=%d mean_degree=10" % a.n) if a.graph == "rgg" else \
+            ("ba n=%d edges_per_node=5%s" % (a.n, " weighted" if a.weighted else ""))
+    return {"workload": f"{gname} M={a.M} m={a.m} {kern} methods={a.methods}"
+                        + (f" reorth={a.reorth}" if a.reorth else ""),
+            "graph": ("random geometric graph, unit square, cell-sorted node order" if a.graph == "rgg"
+                      else "Barabasi-Albert, 5 edges per new node"),
             "n": a.n, "mean_degree": 10, "M": a.M, "m": a.m,
-            "t": [float(x) for x in a.ts.split(",")], "methods": a.methods.split(","),
+            "phi": a.phi, "t": kernel_times(a) if a.phi == "exp" else None,
+            "eps": a.eps if a.phi == "spline" else None, "s": a.s if a.phi == "spline" else None,
+            "reorth": a.reorth, "methods": a.methods.split(","),
             "graph_seed": a.graph_seed, "node_seed": a.node_seed, "basis": a.basis,
             "l2": "256 MiB flush write between steps; per-solve working set > L2",
             "streams": a.streams, "schedule": a.schedule,
@@ -347,16 +377,16 @@ def run_reference(a, rank, world):
         return
     import synth
     from oracle import krylov
-    ts = [float(x) for x in a.ts.split(",")]
+    ts = kernel_times(a)
     methods = a.methods.split(",")
-    g = synth.random_geometric_graph(a.n, 10, seed=a.graph_seed)
+    g = bench_graph(a)
     nodes = synth.sample_nodes(a.n, a.M, seed=a.node_seed)[: a.ref_sample_cols]
     L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
 
     def step():
         for mth in methods:
             for t in ts:
-                krylov.apply(mth, L, nodes, a.m, "exp", t=t)
+                krylov.apply(mth, L, nodes, a.m, a.phi, reorth=bool(a.reorth == 1), **phi_kwargs(a, t))
 
     for _ in range(a.warmup):
         step()
@@ -385,9 +415,9 @@ def cpu_baseline(a, budget_s=25.0):
     columns are independent (sbl, cheb, cheb2), which equal the GPU's first columns."""
     import synth
     from oracle import krylov
-    ts = [float(x) for x in a.ts.split(",")]
+    ts = kernel_times(a)
     methods = a.methods.split(",")
-    g = synth.random_geometric_graph(a.n, 10, seed=a.graph_seed)
+    g = bench_graph(a)
     nodes = synth.sample_nodes(a.n, a.M, seed=a.node_seed)[: a.ref_sample_cols]
     L = krylov.laplacian(g.n, g.rowptr, g.col, g.val)
     t0 = time.perf_counter()
@@ -395,7 +425,7 @@ def cpu_baseline(a, budget_s=25.0):
     ref_cols = {}
     for mth in methods:
         for t in ts:
-            Y = krylov.apply(mth, L, nodes, a.m, "exp", t=t).Y
+            Y = krylov.apply(mth, L, nodes, a.m, a.phi, reorth=bool(a.reorth == 1), **phi_kwargs(a, t)).Y
             cols += len(nodes)
             if mth in ("sbl", "cheb", "cheb2"):
                 ref_cols[(mth, t)] = Y
@@ -464,9 +494,9 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.cuda.current_device()
-    ts = [float(x) for x in a.ts.split(",")]
+    ts = kernel_times(a)
     methods = a.methods.split(",")
-    g = synth.random_geometric_graph(a.n, 10, seed=a.graph_seed)
+    g = bench_graph(a)
     nodes = synth.sample_nodes(a.n, a.M, seed=replica_node_seed(a.node_seed, rank))
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
@@ -477,7 +507,8 @@ def main():
     solves = [(mth, t) for mth in methods for t in ts]
     Ys = [torch.empty((a.n, a.M), dtype=torch.float32, device="cuda") for _ in solves]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    params = {t: kb.make_params(t=t, basis=a.basis, no_frontier=int(a.no_frontier)) for t in ts}
+    params = {t: kb.make_params(basis=a.basis, no_frontier=int(a.no_frontier), reorth=a.reorth,
+                                **phi_kwargs(a, t)) for t in ts}
 
     where, order = assign_streams(solves, len(streams), a.schedule)
 
@@ -489,7 +520,7 @@ def main():
             s2.wait_event(ev)
         for i in order:
             mth, t = solves[i]
-            kb.kb_krylov_apply(G, mth, "exp", pr[t], nodes, a.M, a.m, Ys[i], stream=streams[where[i]])
+            kb.kb_krylov_apply(G, mth, a.phi, pr[t], nodes, a.M, a.m, Ys[i], stream=streams[where[i]])
         for s2 in streams[1:]:
             e2 = torch.cuda.Event()
             e2.record(s2)
@@ -536,13 +567,13 @@ def main():
     kb.kb_profile_enable(True)
     evs[0].record(stream)
     for i, ((mth, t), Y) in enumerate(zip(solves, Ys)):
-        kb.kb_krylov_apply(G, mth, "exp", params[t], nodes, a.M, a.m, Y, stream=stream)
+        kb.kb_krylov_apply(G, mth, a.phi, params[t], nodes, a.M, a.m, Y, stream=stream)
         evs[i + 1].record(stream)
     torch.cuda.synchronize()
     kb.kb_profile_enable(False)
     stats1 = kb.kb_profile_read()
     for i, (mth, t) in enumerate(solves):
-        solve_ms[f"{mth} t={t:g}"] = round(evs[i].elapsed_time(evs[i + 1]), 3)
+        solve_ms[f"{mth} t={t:g}" if a.phi == "exp" else f"{mth} {a.phi}"] = round(evs[i].elapsed_time(evs[i + 1]), 3)
     ms1 = evs[0].elapsed_time(evs[-1])
     # the FP32 results' first columns, kept for the accuracy check against the oracle (the
     # FP64 comparator below reuses the output buffers)
@@ -605,7 +636,7 @@ def main():
         def run_share(j):
             for i in (q for q in order if where[q] == j):
                 mth, t = solves[i]
-                kb.kb_krylov_apply_host(G, mth, "exp", params[t], nodes, a.M, a.m, Yh[i],
+                kb.kb_krylov_apply_host(G, mth, a.phi, params[t], nodes, a.M, a.m, Yh[i],
                                         stream=streams[j])
 
         def step_host():
@@ -626,7 +657,8 @@ def main():
     # plain FP64 GPU mode (the comparator of the mixed-precision form), same solves
     fp64 = None
     if a.fp64_steps > 0 and a.basis == "f32":
-        p64 = {t: kb.make_params(t=t, basis="f64", no_frontier=int(a.no_frontier)) for t in ts}
+        p64 = {t: kb.make_params(basis="f64", no_frontier=int(a.no_frontier), reorth=a.reorth,
+                                 **phi_kwargs(a, t)) for t in ts}
         try:
             step(p64)
             torch.cuda.synchronize()
