@@ -159,6 +159,63 @@ __device__ __forceinline__ double recip_newton(double d) {
 __device__ __forceinline__ double chol_recip(double d) { return recip_newton(d); }
 __device__ __forceinline__ float chol_recip(float d) { return 1.0f / d; }
 
+// Scratch of tri_inv_upper_blocked: (P/2)^2 values, P the power of two >= M.
+__host__ __device__ inline int tri_inv_tmp_elems(int M) {
+    int P = 1;
+    while (P < M) P *= 2;
+    return (P / 2) * (P / 2);
+}
+
+// Blocked in-place inverse of an upper triangular M x M matrix in shared memory (ld lda),
+// with few barriers: the 8 x 8 diagonal blocks are inverted one per thread (column by
+// column, rows ascending, so each row still reads the original column above the diagonal),
+// then pairs of inverted diagonal blocks [A B; 0 C] are merged level by level into
+// [A^-1, -A^-1 B C^-1; 0, C^-1] (block edge 8, 16, 32, 64): two barriers per level instead
+// of one per column.  tmp: tri_inv_tmp_elems(M) values of shared scratch (the products
+// A^-1 B of every pair at the widest level).
+template <typename S>
+__device__ void tri_inv_upper_blocked(S *A, int lda, int M, S *tmp) {
+    const int nb = (M + 7) / 8;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const int r0 = b * 8, r1 = min(r0 + 8, M);
+        for (int j = r0; j < r1; ++j) {
+            const S ajj = S(1) / A[j * lda + j];
+            for (int i = r0; i < j; ++i) {
+                S acc = S(0);
+                for (int k = i; k < j; ++k) acc = fma(A[i * lda + k], A[k * lda + j], acc);
+                A[i * lda + j] = -ajj * acc;
+            }
+            A[j * lda + j] = ajj;
+        }
+    }
+    __syncthreads();
+    for (int bs = 8; bs < M; bs *= 2) {
+        // T_p = A_p^-1 B_p for every pair p (rows r0.., columns r0 + bs..)
+        const int npairs = (M + 2 * bs - 1) / (2 * bs);
+        const int per = bs * bs;
+        for (int idx = threadIdx.x; idx < npairs * per; idx += blockDim.x) {
+            const int p = idx / per, i = (idx % per) / bs, c = idx % bs;
+            const int r0 = p * 2 * bs, cb = min(bs, M - r0 - bs);
+            if (cb <= 0 || c >= cb) continue;
+            S acc = S(0);
+            for (int k = i; k < bs; ++k) acc = fma(A[(r0 + i) * lda + r0 + k], A[(r0 + k) * lda + r0 + bs + c], acc);
+            tmp[p * per + i * bs + c] = acc;
+        }
+        __syncthreads();
+        // B_p <- -T_p C_p^-1 (C^-1 upper triangular)
+        for (int idx = threadIdx.x; idx < npairs * per; idx += blockDim.x) {
+            const int p = idx / per, i = (idx % per) / bs, c = idx % bs;
+            const int r0 = p * 2 * bs, cb = min(bs, M - r0 - bs);
+            if (cb <= 0 || c >= cb) continue;
+            const int c0 = r0 + bs;
+            S acc = S(0);
+            for (int k = 0; k <= c; ++k) acc = fma(tmp[p * per + i * bs + k], A[(c0 + k) * lda + c0 + c], acc);
+            A[(r0 + i) * lda + c0 + c] = -acc;
+        }
+        __syncthreads();
+    }
+}
+
 // Cholesky G = R^T R of an M x M symmetric matrix in shared memory, upper R overwriting A
 // and the lower part zeroed.  Square-root-free form: step j needs the pivot d_j (the
 // diagonal of the current Schur complement) and one reciprocal; the Schur complement update
@@ -430,7 +487,11 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
         if (newton) Rf[i * lda + j] = float(Sf[i * lda + j]);
     }
     __syncthreads();
-    tri_inv_upper_inplace<T>(Sf, lda, M, reinterpret_cast<T *>(t));
+    {
+        // scratch after the Newton region (launch_chol sizes it)
+        unsigned char *after = reinterpret_cast<unsigned char *>(t + 3 * M + 2) + (newton ? 16 * size_t(M) * lda : 0);
+        tri_inv_upper_blocked<T>(Sf, lda, M, reinterpret_cast<T *>(after));
+    }
     for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
         const int i = idx / W, j = idx % W;
         Rinv[idx] = (i < M && j < M && j >= i) ? Sf[i * lda + j] : T(0);
@@ -1323,7 +1384,8 @@ int launch_chol(const double *G, int M, int W, int pass, int step, double inv_th
         const bool newton = sizeof(T) == 4 && m <= CHOL_NEWTON_MAX;
         return sizeof(double) * size_t(m) * (m + 1) + sizeof(T) * (size_t(m) * (m + 1) + 2) +
                sizeof(double) * size_t(3 * m + 2) +
-               (newton ? (sizeof(double) + 2 * sizeof(float)) * size_t(m) * (m + 1) : 0);
+               (newton ? (sizeof(double) + 2 * sizeof(float)) * size_t(m) * (m + 1) : 0) +
+               sizeof(T) * size_t(tri_inv_tmp_elems(m));
     };
     const size_t smem = bytes_for(M);
     // FP64 blocks are at most 64 wide; function-local static: set once, thread-safe
