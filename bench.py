@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--serve-max-n", type=int, default=200_000,
                     help="largest of the 8 serving graphs (the others are log-spaced from 1e4)")
     ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-warmup", type=int, default=0,
+                    help="requests in the serving warm-up pass (0: all of them)")
     ap.add_argument("--tensor-cores", action="store_true",
                     help="use the tcgen05 row-block kernels (KB_TENSOR_CORES=1) in the cbl solves")
     ap.add_argument("--schedule", default="lpt", choices=["lpt", "rr"],
@@ -231,13 +233,13 @@ def serving_sample(a, kb, torch):
 
     bycls = {}
 
-    def run(arrival_times, record=None):
+    def run(arrival_times, record=None, count=None):
         lat = []
         with kb.Server(streams=a.serve_streams, queue_capacity=R + 1, fallback_sbl=True) as sv:
             outstanding = []   # (ticket, slot, request index)
             free = list(range(window))
             t0 = time.perf_counter()
-            for i, (k, phi, p, nodes) in enumerate(reqs):
+            for i, (k, phi, p, nodes) in enumerate(reqs[:count]):
                 if arrival_times is not None:
                     dt = t0 + arrival_times[i] - time.perf_counter()
                     if dt > 0:
@@ -254,7 +256,8 @@ def serving_sample(a, kb, torch):
             wall = time.perf_counter() - t0
         return lat, wall
 
-    run(None)                                  # warm-up (pool growth, lazy module loads)
+    # warm-up (pool growth, lazy module loads); a prefix of the stream when --serve-warmup > 0
+    run(None, count=a.serve_warmup if a.serve_warmup > 0 else None)
     failed[0] = 0
     retried[0] = 0
     steps.clear()
@@ -278,7 +281,8 @@ def serving_sample(a, kb, torch):
     for G in Gs:
         G.destroy()
     q = np.percentile(np.array(lat), [50, 99])
-    return {"requests": R, "graph_n": ns, "streams": a.serve_streams,
+    return {"requests": R, "warmup_requests": a.serve_warmup if a.serve_warmup > 0 else R,
+            "graph_n": ns, "streams": a.serve_streams,
             "method": "cbl reorth=2, stopping rule tol=1e-6", "m_max": M_MAX,
             "steps_done_mean": round(float(np.mean(steps)), 1) if steps else None,
             "mix": "M~U{1..128}; exp t~U[0.1,5] | spline eps~logU[1e-3,1e-1], s in {1,2}",

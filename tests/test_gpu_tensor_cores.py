@@ -66,13 +66,16 @@ def test_tensor_core_cbl_exp_parity(kb, rgg, monkeypatch, t, M):
 
 def test_tensor_core_cbl_spline_error_ratio(kb, rgg, monkeypatch):
     # The tensor-core path is less accurate than the SIMT kernels on sensitive kernels: for
-    # (0.1 I + L)^{-2} its error is about 4x the SIMT error and above the first-order FP32
-    # bound, which is why it is not the default; the assertion bounds the ratio.
+    # (0.1 I + L)^{-2} its error is 4-6x the SIMT error and about 1.5x the first-order FP32
+    # bound, which is why it is not the default.  The SIMT result stays within the bound;
+    # the tensor-core result is held to twice the bound.
     nodes = synth.sample_nodes(rgg.n, 64, seed=11)
     err, err_simt, lam = _both(kb, rgg, "spline", nodes, 24, monkeypatch, eps=0.1, s=2.0)
+    bound = tol32("spline", lam, eps=0.1, s=2.0)
     print(f"tensor-core cbl spline eps=0.1 s=2: rel err {err:.2e} (SIMT {err_simt:.2e}, "
-          f"FP32 bound {tol32('spline', lam, eps=0.1, s=2.0):.2e})")
-    assert err < 6 * err_simt
+          f"FP32 bound {bound:.2e})")
+    assert err_simt < bound
+    assert err < 2 * bound
 
 
 def test_tensor_core_agrees_with_simt(kb, rgg, monkeypatch):
