@@ -216,6 +216,129 @@ __device__ void tri_inv_upper_blocked(S *A, int lda, int M, S *tmp) {
     }
 }
 
+// The upper triangle of an M x M matrix in 4 x 4 tiles: tile t (row-major over the tiles
+// (bi, bj), bi <= bj, of the ceil(M/4) x ceil(M/4) grid) -> first row i0, first column j0.
+__device__ __forceinline__ void upper_tile(int t, int nt, int &i0, int &j0) {
+    int bi = 0;
+    while (t >= nt - bi) {
+        t -= nt - bi;
+        ++bi;
+    }
+    i0 = 4 * bi;
+    j0 = 4 * (bi + t);
+}
+
+// C = init + sum_k a(i, k) b(k, j) over the upper triangle i <= j < M of a product of two
+// upper triangular M x M matrices, read through the accessors a and b (which must return
+// exact zeros below the diagonal).  Each thread takes 4 x 4 tiles of C: 16 independent
+// FMA chains over k = i0 .. j0 + 3, the only k where a term of the tile can be non-zero,
+// in ascending order, so every entry is the FMA chain of the plain loop k = i .. j with
+// exact zero terms added.  epi(i, j, c) receives the upper-triangle entries.
+template <typename S, typename FA, typename FB, typename FI, typename FE>
+__device__ void tri_mm_upper(int M, const FA &a, const FB &b, const FI &init, const FE &epi) {
+    const int nt = (M + 3) / 4;
+    const int ntiles = nt * (nt + 1) / 2;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        int i0, j0;
+        upper_tile(t, nt, i0, j0);
+        S acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                acc[r][q] = (i0 + r < M && j0 + q < M) ? init(i0 + r, j0 + q) : S(0);
+        const int kend = min(j0 + 4, M);
+        for (int k = i0; k < kend; ++k) {
+            S av[4], bv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) av[r] = (i0 + r < M) ? a(i0 + r, k) : S(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bv[q] = (j0 + q < M) ? b(k, j0 + q) : S(0);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], bv[q], acc[r][q]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + r, j = j0 + q;
+                if (i < M && j < M && j >= i) epi(i, j, acc[r][q]);
+            }
+    }
+}
+
+// E = I - S R for upper triangular FP32 matrices S and R in shared memory (ld lda, zeros
+// below the diagonal), each entry accumulated as an unevaluated pair of floats: every
+// product s r is split exactly into p + pe (p the rounded product, pe = fma(s, r, -p)) and
+// subtracted with Knuth's two-sum, so the residual, whose size is the FP32 rounding of the
+// inverse, keeps about 48 bits while running on the FP32 pipe.  Returns E rounded to FP32
+// through epi(i, j, e) for the upper triangle.
+template <typename FE>
+__device__ void tri_residual_df(const float *Sm, const float *Rm, int lda, int M, const FE &epi) {
+    const int nt = (M + 3) / 4;
+    const int ntiles = nt * (nt + 1) / 2;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        int i0, j0;
+        upper_tile(t, nt, i0, j0);
+        float hi[4][4], lo[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                hi[r][q] = (i0 + r == j0 + q) ? 1.f : 0.f;
+                lo[r][q] = 0.f;
+            }
+        const int kend = min(j0 + 4, M);
+        for (int k = i0; k < kend; ++k) {
+            float sv[4], rv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sv[r] = (i0 + r < M) ? Sm[(i0 + r) * lda + k] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) rv[q] = (j0 + q < M) ? Rm[k * lda + j0 + q] : 0.f;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float p = __fmul_rn(sv[r], rv[q]);
+                    const float pe = fmaf(sv[r], rv[q], -p);
+                    float s, e;
+                    two_sum(hi[r][q], -p, s, e);
+                    hi[r][q] = s;
+                    lo[r][q] += e - pe;
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + r, j = j0 + q;
+                if (i < M && j < M && j >= i) epi(i, j, hi[r][q] + lo[r][q]);
+            }
+    }
+}
+
+// Copy an M x M row-major matrix (leading dimension ldg) from global memory through
+// store(i, j, v), eight loads in flight per thread before their stores.
+template <typename FS>
+__device__ __forceinline__ void load_square(const double *g, int ldg, int M, const FS &store) {
+    const int MM = M * M;
+    for (int base = threadIdx.x; base < MM; base += 8 * blockDim.x) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * blockDim.x;
+            v[u] = idx < MM ? __ldg(g + (idx / M) * ldg + idx % M) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < MM) store(idx / M, idx % M, v[u]);
+        }
+    }
+}
+
 // Cholesky G = R^T R of an M x M symmetric matrix in shared memory, upper R overwriting A
 // and the lower part zeroed.  Square-root-free form: step j needs the pivot d_j (the
 // diagonal of the current Schur complement) and one reciprocal; the Schur complement update
@@ -269,17 +392,11 @@ __device__ bool chol_upper_inplace(S *A, int lda, int M, S piv_rel2, S maxdiag, 
                 }
             }
         } else {
-            // rows j+2.. of the trailing upper triangle
-            const int L = M - j - 2;
-            const int npairs = L > 0 ? L * (L + 1) / 2 : 0;
-            for (int idx = threadIdx.x - 32; idx < npairs; idx += blockDim.x - 32) {
-                // idx -> (a, b), b <= a (FP32 root estimate, corrected exactly in integers)
-                int a = int((sqrtf(8.f * float(idx) + 1.f) - 1.f) * 0.5f);
-                while ((a + 1) * (a + 2) / 2 <= idx) ++a;
-                while (a * (a + 1) / 2 > idx) --a;
-                const int b = idx - a * (a + 1) / 2;
-                const int ra = j + 2 + b, rb = j + 2 + a;   // ra <= rb
-                A[ra * lda + rb] -= A[j * lda + ra] * sr[rb];
+            // rows j+2.. of the trailing upper triangle: one warp per row, lanes along it
+            const int nw = (blockDim.x >> 5) - 1;
+            for (int ra = j + 1 + warp; ra < M; ra += nw) {
+                const S uja = A[j * lda + ra];
+                for (int rb = ra + lane; rb < M; rb += 32) A[ra * lda + rb] -= uja * sr[rb];
             }
         }
         __syncthreads();
@@ -319,9 +436,13 @@ __device__ bool chol_upper_inplace(S *A, int lda, int M, S piv_rel2, S maxdiag, 
 // the corrections formed in FP32.  When ||E|| is not small (max |E_ij| >= 1e-4), and always
 // in the FP64 mode, pass 2 uses the pass-1 algorithm.
 //
-// FP64 arithmetic is slow on this part: the kernel avoids serial FP64 loops (the statistics
-// of G are reduced in parallel, max |E_ij| through the order-preserving bit patterns of
-// non-negative doubles) and the Cholesky factorisation needs one FP64 division per column.
+// The kernel runs on one SM, so its time is latency: the matrices are loaded with several
+// loads in flight per thread, the triangular products run as 4 x 4 register tiles (16
+// independent FMA chains per thread instead of one serial chain per entry), the residual of
+// the FP32 inverse uses pairs of floats rather than FP64 (whose rate on this part is a small
+// fraction of FP32), the statistics of G are reduced in parallel (max |E_ij| through the
+// order-preserving bit patterns of non-negative doubles) and the Cholesky factorisation needs
+// one division per column.
 constexpr int CHOL_NEWTON_MAX = 64;   // widest block with the corrected-inverse scratch
 template <typename T>
 __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int pass, int step,
@@ -346,9 +467,7 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
     }
     __syncthreads();
     unsigned long long my_e = 0ull;
-    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-        const int i = idx / M, j = idx % M;
-        const double g = G[i * W + j];
+    load_square(G, W, M, [&](int i, int j, double g) {
         A[i * lda + j] = g;
         if (try_small) {
             double e = g;
@@ -356,7 +475,7 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
             const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(fabs(e)));
             my_e = b > my_e ? b : my_e;
         }
-    }
+    });
     if (try_small) {
         for (int off = 16; off > 0; off >>= 1) {
             const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_e, off);
@@ -407,34 +526,34 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
             if (i < M && j < M) Sf[i * lda + j] = (j >= i) ? T((i == j ? 1.0 : 0.0) - double(v)) : T(0);
         }
         __syncthreads();
-        // A is free now: R1 rounded to T, and C = F R1 (both upper triangular)
+        // A is free now: R1 rounded to T, and C = F R1 (both upper triangular, zeros below)
         T *R1t = reinterpret_cast<T *>(A);
         T *Ct = R1t + M * lda;
-        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-            const int i = idx / M, j = idx % M;
-            R1t[i * lda + j] = (j >= i) ? T(__ldg(R1 + idx)) : T(0);
-        }
+        load_square(R1, M, M, [&](int i, int j, double v) {
+            R1t[i * lda + j] = (j >= i) ? T(v) : T(0);
+            Ct[i * lda + j] = T(0);
+        });
         __syncthreads();
-        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-            const int i = idx / M, j = idx % M;
-            T corr = T(0);
-            for (int k = i; k <= j; ++k) corr = fma(Sf[i * lda + k], R1t[k * lda + j], corr);
-            Ct[i * lda + j] = corr;
+        auto sf = [&](int i, int k) { return Sf[i * lda + k]; };
+        auto zero = [](int, int) { return T(0); };
+        tri_mm_upper<T>(M, sf, [&](int k, int j) { return R1t[k * lda + j]; }, zero,
+                        [&](int i, int j, T c) { Ct[i * lda + j] = c; });
+        // entries of Hs and B outside H's upper triangle are zero
+        for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+            const int i = idx / W, j = idx % W;
+            if (i < M && j < M && j >= i) continue;
+            if (i < M && j < M) Hs[i * M + j] = 0.0;
+            Bout[j * W + i] = T(0);
         }
         __syncthreads();
         // H = (I + F + F^2) R1 = R1 + (C + F C), the corrections of relative size ||E||
-        for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
-            const int i = idx / W, j = idx % W;
-            double h = 0.0;
-            if (i < M && j < M && j >= i) {
-                T corr2 = T(0);
-                for (int k = i; k <= j; ++k) corr2 = fma(Sf[i * lda + k], Ct[k * lda + j], corr2);
-                h = __ldg(R1 + i * M + j) + double(Ct[i * lda + j] + corr2);
-            }
-            const T ht = T(h);
-            if (i < M && j < M) Hs[i * M + j] = double(ht);
-            Bout[j * W + i] = ht;
-        }
+        tri_mm_upper<T>(M, sf, [&](int k, int j) { return Ct[k * lda + j]; }, zero,
+                        [&](int i, int j, T corr2) {
+                            const double h = __ldg(R1 + i * M + j) + double(Ct[i * lda + j] + corr2);
+                            const T ht = T(h);
+                            Hs[i * M + j] = double(ht);
+                            Bout[j * W + i] = ht;
+                        });
         return;
     }
     // ---- general CholeskyQR pass
@@ -501,54 +620,59 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
         bool exact = !newton;
         if (newton) {
             // With S R = I - E (E upper triangular, of the order of the FP32 rounding),
-            // S^{-1} = R (I - E)^{-1} = R + R E + R E^2 + O(E^3): E is formed in FP64 from S
-            // and R (a fully parallel triangular product), the corrections in FP32.  When
+            // S^{-1} = R (I - E)^{-1} = R + R E + R E^2 + O(E^3): E is formed from S and R with
+            // a residual more precise than FP32 (pairs of floats when R is the FP32 factor,
+            // FP64 when the factorisation fell back to FP64), the corrections in FP32.  When
             // max |E_ij| >= 1e-3 the exact FP64 inverse below is used instead.
             __shared__ unsigned int emax_e;
+            float *Sff = reinterpret_cast<float *>(Sf);
+            // E goes to the Sd region (pair residual; S stays in Sf) or, with the FP64
+            // residual, which reads S from Sd, over S in Sf
+            float *Ef = factored ? reinterpret_cast<float *>(Sd) : Sff;
             if (threadIdx.x == 0) emax_e = 0u;
             for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
                 const int i = idx / M, j = idx % M;
-                Sd[i * lda + j] = (j >= i) ? double(Sf[i * lda + j]) : 0.0;
+                if (factored) {
+                    if (j < i) Ef[i * lda + j] = 0.f;
+                } else {
+                    Sd[i * lda + j] = (j >= i) ? double(Sff[i * lda + j]) : 0.0;
+                }
             }
             __syncthreads();
             unsigned int my = 0u;
-            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-                const int i = idx / M, j = idx % M;
-                float ef = 0.f;
-                if (j >= i) {
-                    double e = (i == j) ? 1.0 : 0.0;
-                    for (int k = i; k <= j; ++k) e = fma(-Sd[i * lda + k], A[k * lda + j], e);
-                    ef = float(e);
-                }
-                Sf[i * lda + j] = T(ef);
-                const unsigned int b = __float_as_uint(fabsf(ef));
-                my = b > my ? b : my;
+            auto put_e = [&](int i, int j, float ef) {
+                Ef[i * lda + j] = ef;
+                const unsigned int bits = __float_as_uint(fabsf(ef));
+                my = bits > my ? bits : my;
+            };
+            if (factored) {
+                tri_residual_df(Sff, Rf, lda, M, put_e);
+            } else {
+                tri_mm_upper<double>(
+                    M, [&](int i, int k) { return -Sd[i * lda + k]; }, [&](int k, int j) { return A[k * lda + j]; },
+                    [](int i, int j) { return i == j ? 1.0 : 0.0; },
+                    [&](int i, int j, double e) { put_e(i, j, float(e)); });
             }
             atomicMax(&emax_e, my);
             __syncthreads();
             if (__uint_as_float(emax_e) < 1e-3f) {
+                auto ef = [&](int k, int j) { return Ef[k * lda + j]; };
+                auto zero = [](int, int) { return 0.f; };
                 for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
                     const int i = idx / M, j = idx % M;
-                    float c = 0.f;
-                    if (j >= i)
-                        for (int k = i; k <= j; ++k) c = fmaf(Rf[i * lda + k], float(Sf[k * lda + j]), c);
-                    C1[i * lda + j] = c;
+                    if (j < i) C1[i * lda + j] = 0.f;
                 }
+                tri_mm_upper<float>(M, [&](int i, int k) { return Rf[i * lda + k]; }, ef, zero,
+                                    [&](int i, int j, float c) { C1[i * lda + j] = c; });
                 __syncthreads();
-                for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-                    const int i = idx / M, j = idx % M;
-                    if (j >= i) {
-                        float c2 = 0.f;
-                        for (int k = i; k <= j; ++k) c2 = fmaf(C1[i * lda + k], float(Sf[k * lda + j]), c2);
-                        A[i * lda + j] += double(C1[i * lda + j] + c2);
-                    }
-                }
+                tri_mm_upper<float>(M, [&](int i, int k) { return C1[i * lda + k]; }, ef, zero,
+                                    [&](int i, int j, float c2) { A[i * lda + j] += double(C1[i * lda + j] + c2); });
                 __syncthreads();
             } else {
                 exact = true;
                 for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
                     const int i = idx / M, j = idx % M;
-                    A[i * lda + j] = Sd[i * lda + j];
+                    A[i * lda + j] = factored ? ((j >= i) ? double(Sff[i * lda + j]) : 0.0) : Sd[i * lda + j];
                 }
                 __syncthreads();
             }
@@ -572,14 +696,18 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
         // recorded rounded to the basis precision, i.e. exactly as the next step subtracts it.
         for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
             const int i = idx / W, j = idx % W;
-            double h = 0.0;
-            if (i < M && j < M && j >= i) {
-                for (int k = i; k <= j; ++k) h = fma(A[i * lda + k], __ldg(R1 + k * M + j), h);
-            }
-            const T ht = T(h);
-            if (i < M && j < M) Hs[i * M + j] = double(ht);
-            Bout[j * W + i] = ht;
+            if (i < M && j < M && j >= i) continue;
+            if (i < M && j < M) Hs[i * M + j] = 0.0;
+            Bout[j * W + i] = T(0);
         }
+        tri_mm_upper<double>(
+            M, [&](int i, int k) { return A[i * lda + k]; }, [&](int k, int j) { return __ldg(R1 + k * M + j); },
+            [](int, int) { return 0.0; },
+            [&](int i, int j, double h) {
+                const T ht = T(h);
+                Hs[i * M + j] = double(ht);
+                Bout[j * W + i] = ht;
+            });
     }
 }
 
