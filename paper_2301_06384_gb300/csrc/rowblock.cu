@@ -81,7 +81,11 @@ struct Geo {
     static constexpr size_t smem_a = sizeof(typename Cmp<T>::type) * KC * LDA;
     static constexpr size_t smem_c = sizeof(typename Cmp<T>::type) * KC * W;
     static constexpr size_t smem_o = sizeof(typename Cmp<T>::type) * TR * LDO;
-    static constexpr size_t smem = smem_a + smem_c + 2 * smem_o;
+    // FP32 Gram of width 128: the cross-tile sums (64 per thread) live in shared memory, so
+    // that the kernel fits two CTAs per SM in the register file
+    static constexpr bool G2S = W == 128 && sizeof(typename Cmp<T>::type) == 4;
+    static constexpr size_t smem_g = G2S ? sizeof(float) * W * W : 0;
+    static constexpr size_t smem = smem_a + smem_c + 2 * smem_o + smem_g;
 };
 
 template <typename T, int W, int MODE>
@@ -102,6 +106,8 @@ k_rowblock(RowArgs<T> a) {
     C *sC = reinterpret_cast<C *>(smem_raw + G::smem_a);          // [KC][W]
     C *sO = reinterpret_cast<C *>(smem_raw + G::smem_a + G::smem_c);            // [TR][LDO]
     C *sQ = reinterpret_cast<C *>(smem_raw + G::smem_a + G::smem_c + G::smem_o);  // [TR][LDO]
+    C *sG = reinterpret_cast<C *>(smem_raw + G::smem_a + G::smem_c + 2 * G::smem_o); // [W][W] (G2S)
+    constexpr bool G2S = G::G2S;
 
     const int tid = threadIdx.x;
     // product mapping: consecutive threads share an output column group, so a warp covers
@@ -117,11 +123,15 @@ k_rowblock(RowArgs<T> a) {
     if (MODE == RB_ASM) nkb = a.ctrl ? min(a.ctrl->steps, a.nblk) : a.nblk;
     if (MODE == RB_ASMSUB) nkb = a.nblk;
 
-    C g1[GR][GR], g2[GR][GR];
+    C g1[GR][GR], g2[G2S ? 1 : GR][G2S ? 1 : GR];
 #pragma unroll
     for (int i = 0; i < GR; ++i)
 #pragma unroll
-        for (int j = 0; j < GR; ++j) { g1[i][j] = 0; g2[i][j] = 0; }
+        for (int j = 0; j < GR; ++j) {
+            g1[i][j] = 0;
+            if constexpr (G2S) sG[(gi0 + i) * W + gj0 + j] = 0;   // this thread's entries only
+            else g2[i][j] = 0;
+        }
 
     const int64_t ntiles = (a.n + TR - 1) / TR;
     unsigned long long my_rows = 0, my_units = 0;
@@ -311,14 +321,18 @@ k_rowblock(RowArgs<T> a) {
 #pragma unroll
                     for (int j = 0; j < GR; ++j) {
                         if (TWO) g1[i][j] = fma(av[i], bv[j], g1[i][j]);
-                        else g2[i][j] = fma(av[i], bv[j], g2[i][j]);
+                        else if constexpr (!G2S) g2[i][j] = fma(av[i], bv[j], g2[i][j]);
                     }
             }
             if (TWO) {
 #pragma unroll
                 for (int i = 0; i < GR; ++i)
 #pragma unroll
-                    for (int j = 0; j < GR; ++j) { g2[i][j] += g1[i][j]; g1[i][j] = 0; }
+                    for (int j = 0; j < GR; ++j) {
+                        if constexpr (G2S) sG[(gi0 + i) * W + gj0 + j] += g1[i][j];
+                        else g2[i][j] += g1[i][j];
+                        g1[i][j] = 0;
+                    }
             }
             __syncthreads();
         }
@@ -332,7 +346,10 @@ k_rowblock(RowArgs<T> a) {
 #pragma unroll
         for (int i = 0; i < GR; ++i)
 #pragma unroll
-            for (int j = 0; j < GR; ++j) p[(gi0 + i) * W + gj0 + j] = g2[i][j];
+            for (int j = 0; j < GR; ++j) {
+                if constexpr (G2S) p[(gi0 + i) * W + gj0 + j] = sG[(gi0 + i) * W + gj0 + j];
+                else p[(gi0 + i) * W + gj0 + j] = g2[i][j];
+            }
     }
 }
 
@@ -379,7 +396,8 @@ int launch_w(int mode, const RowArgs<T> &a, cudaStream_t s, int *grid_out) {
 template <typename T, int W>
 int max_grid_w() {
     int g = num_sms() * std::max({occupancy<T, W, RB_PROJ>(), occupancy<T, W, RB_UPD>(),
-                                  occupancy<T, W, RB_MULGRAM>(), occupancy<T, W, RB_MUL>()});
+                                  occupancy<T, W, RB_MULGRAM>(), occupancy<T, W, RB_MUL>(),
+                                  occupancy<T, W, RB_ASMSUB>()});
     if (std::is_same<T, float>::value && W == 64) g = std::max(g, rowblock_tc_max_grid());
     return g;
 }
@@ -389,26 +407,32 @@ template <typename P>
 __global__ void __launch_bounds__(1024) k_reduce(const P *__restrict__ parts, int nparts, int len,
                                                   double *__restrict__ out, const Ctrl *ctrl,
                                                   P *__restrict__ out_p) {
-    // 32 columns per CTA, 32 warps over the partials (two loads in flight per lane), then a
-    // fixed-order combination of the warps' sums by warp 0
+    // 32 columns per CTA, 32 warps over the partials (eight loads in flight per lane, each
+    // into its own accumulator, merged in a fixed order), then a fixed-order combination of
+    // the warps' sums by warp 0
     if (ctrl && ctrl->stop) return;
     __shared__ double s[32][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int e = blockIdx.x * 32 + lane;
+    constexpr int U = 8;
     if constexpr (std::is_same<P, float>::value) {
         // double-float accumulation on the FP32 pipe
-        DF a0{0.f, 0.f}, a1{0.f, 0.f};
+        DF a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] = DF{0.f, 0.f};
         if (e < len) {
             int p = warp;
-            for (; p + nw < nparts; p += 2 * nw) {
-                const float v0 = parts[int64_t(p) * len + e], v1 = parts[int64_t(p + nw) * len + e];
-                df_add(a0, v0);
-                df_add(a1, v1);
+            for (; p < nparts; p += U * nw) {
+                float v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) v[u] = p + u * nw < nparts ? parts[int64_t(p + u * nw) * len + e] : 0.f;
+#pragma unroll
+                for (int u = 0; u < U; ++u) df_add(a[u], v[u]);
             }
-            if (p < nparts) df_add(a0, parts[int64_t(p) * len + e]);
         }
-        df_merge(a0, a1);
-        reinterpret_cast<DF *>(&s[warp][0])[lane] = a0;
+#pragma unroll
+        for (int u = 1; u < U; ++u) df_merge(a[0], a[u]);
+        reinterpret_cast<DF *>(&s[warp][0])[lane] = a[0];
         __syncthreads();
         if (warp == 0 && e < len) {
             DF t = reinterpret_cast<const DF *>(&s[0][0])[lane];
@@ -418,9 +442,23 @@ __global__ void __launch_bounds__(1024) k_reduce(const P *__restrict__ parts, in
             if (out_p) out_p[e] = P(v);
         }
     } else {
-        double acc = 0.0;
-        if (e < len)
-            for (int p = warp; p < nparts; p += nw) acc += double(parts[int64_t(p) * len + e]);
+        double a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) a[u] = 0.0;
+        if (e < len) {
+            int p = warp;
+            for (; p < nparts; p += U * nw) {
+                double v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    v[u] = p + u * nw < nparts ? double(parts[int64_t(p + u * nw) * len + e]) : 0.0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) a[u] += v[u];
+            }
+        }
+        double acc = a[0];
+#pragma unroll
+        for (int u = 1; u < U; ++u) acc += a[u];
         s[warp][lane] = acc;
         __syncthreads();
         if (warp == 0 && e < len) {

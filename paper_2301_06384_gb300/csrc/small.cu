@@ -12,6 +12,7 @@
 //                   step of Algorithm 2; Section 3.3 with phi applied, reading A2).
 //  * element-wise   unit blocks E_W, node markers, column norms, scaled copies, the
 //                   diagonal assembly sum_k u_k Q_k, NaN fill on breakdown.
+#include <climits>
 #include <type_traits>
 
 #include "kb_internal.cuh"
@@ -93,17 +94,20 @@ __global__ void k_fill_nan(float *Y, int64_t n, int64_t ldy, int mo, const Ctrl 
 
 // ---------------------------------------------------------------- cbl small kernels
 template <typename T>
-__global__ void k_hkk(const double *G, int M, int W, double *Hd, T *C, const Ctrl *ctrl) {
+__global__ void k_hkk(const double *__restrict__ G, int M, int W, double *__restrict__ Hd,
+                      T *__restrict__ C, const Ctrl *ctrl) {
     if (ctrl->stop) return;
-    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
-        const int i = idx / W, j = idx % W;
-        double v = 0.0;
-        if (i < M && j < M) v = 0.5 * (G[i * W + j] + G[j * W + i]);
-        // recorded exactly as the update subtracts it (rounded to the basis precision)
-        const T vt = T(v);
-        if (i < M && j < M) Hd[i * M + j] = double(vt);
-        C[idx] = vt;
-    }
+    // rows by warp, columns by lane; both loads of an entry issued before any store
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < W; i += nw)
+        for (int j = lane; j < W; j += 32) {
+            double v = 0.0;
+            if (i < M && j < M) v = 0.5 * (__ldg(G + i * W + j) + __ldg(G + j * W + i));
+            // recorded exactly as the update subtracts it (rounded to the basis precision)
+            const T vt = T(v);
+            if (i < M && j < M) Hd[i * M + j] = double(vt);
+            C[i * W + j] = vt;
+        }
 }
 
 // In-place inverse of an upper triangular M x M matrix in shared memory (ld lda), column
@@ -189,12 +193,12 @@ __device__ void tri_inv_upper_blocked(S *A, int lda, int M, S *tmp) {
         }
     }
     __syncthreads();
-    for (int bs = 8; bs < M; bs *= 2) {
+    for (int lg = 3, bs = 8; bs < M; ++lg, bs *= 2) {
         // T_p = A_p^-1 B_p for every pair p (rows r0.., columns r0 + bs..)
         const int npairs = (M + 2 * bs - 1) / (2 * bs);
         const int per = bs * bs;
         for (int idx = threadIdx.x; idx < npairs * per; idx += blockDim.x) {
-            const int p = idx / per, i = (idx % per) / bs, c = idx % bs;
+            const int p = idx >> (2 * lg), i = (idx >> lg) & (bs - 1), c = idx & (bs - 1);
             const int r0 = p * 2 * bs, cb = min(bs, M - r0 - bs);
             if (cb <= 0 || c >= cb) continue;
             S acc = S(0);
@@ -204,7 +208,7 @@ __device__ void tri_inv_upper_blocked(S *A, int lda, int M, S *tmp) {
         __syncthreads();
         // B_p <- -T_p C_p^-1 (C^-1 upper triangular)
         for (int idx = threadIdx.x; idx < npairs * per; idx += blockDim.x) {
-            const int p = idx / per, i = (idx % per) / bs, c = idx % bs;
+            const int p = idx >> (2 * lg), i = (idx >> lg) & (bs - 1), c = idx & (bs - 1);
             const int r0 = p * 2 * bs, cb = min(bs, M - r0 - bs);
             if (cb <= 0 || c >= cb) continue;
             const int c0 = r0 + bs;
@@ -320,23 +324,76 @@ __device__ void tri_residual_df(const float *Sm, const float *Rm, int lda, int M
 }
 
 // Copy an M x M row-major matrix (leading dimension ldg) from global memory through
-// store(i, j, v), eight loads in flight per thread before their stores.
+// store(i, j, v): rows by warp, columns by lane (coalesced), eight rows in flight per warp
+// before their stores.
 template <typename FS>
 __device__ __forceinline__ void load_square(const double *g, int ldg, int M, const FS &store) {
-    const int MM = M * M;
-    for (int base = threadIdx.x; base < MM; base += 8 * blockDim.x) {
-        double v[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i0 = warp; i0 < M; i0 += 8 * nw)
+        for (int j = lane; j < M; j += 32) {
+            double v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int idx = base + u * blockDim.x;
-            v[u] = idx < MM ? __ldg(g + (idx / M) * ldg + idx % M) : 0.0;
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * nw;
+                v[u] = i < M ? __ldg(g + i * ldg + j) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * nw;
+                if (i < M) store(i, j, v[u]);
+            }
         }
+}
+
+// The same square-root-free factorisation of an M x M matrix (M <= 64, FP32) by one warp
+// with the matrix in registers: lane l holds columns l and l + 32 (64 rows each; beyond M the
+// matrix is extended by the identity, whose pivots are 1 and whose updates are exact no-ops).
+// Step j broadcasts the pivot d_j and then the pivot row u_j one entry at a time (a shuffle
+// from the lane that holds column a), and each lane updates its two columns,
+// A[a][c] -= u_j[a] (u_j[c] / d_j), for the rows a > j that lie on or above the diagonal of
+// its column set.  No block barrier is needed, so a column costs a few shuffles rather than
+// a barrier round trip.  The arithmetic of every entry is that of chol_upper_inplace.
+// Returns false on a pivot <= thr (warp-uniform); piv: 64 floats of shared scratch.
+__device__ bool chol_upper_warp64(float *A, int lda, int M, float thr, float *piv) {
+    const int lane = threadIdx.x & 31;
+    float ca[64], cb[64];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int idx = base + u * blockDim.x;
-            if (idx < MM) store(idx / M, idx % M, v[u]);
+    for (int r = 0; r < 64; ++r) {
+        const int c0 = lane, c1 = lane + 32;
+        ca[r] = (r < M && c0 < M) ? A[r * lda + c0] : (r == c0 ? 1.f : 0.f);
+        cb[r] = (r < M && c1 < M) ? A[r * lda + c1] : (r == c1 ? 1.f : 0.f);
+    }
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+        const float d = __shfl_sync(0xffffffffu, j < 32 ? ca[j] : cb[j], j & 31);
+        if (j < M && !(d > thr)) {
+            ok = false;
+            break;
+        }
+        if (lane == 0) piv[j] = d;
+        const float dinv = 1.0f / d;
+        const float sa = ca[j] * dinv, sb = cb[j] * dinv;
+#pragma unroll
+        for (int a = j + 1; a < 64; ++a) {
+            const float ua = __shfl_sync(0xffffffffu, a < 32 ? ca[j] : cb[j], a & 31);
+            if (a < 32) ca[a] = fmaf(-ua, sa, ca[a]);   // rows >= 32 of columns < 32: below the diagonal
+            cb[a] = fmaf(-ua, sb, cb[a]);
         }
     }
+    if (!ok) return false;
+    __syncwarp();
+    // R_jj = sqrt(d_j), R_jc = u_jc / sqrt(d_j), zeros below the diagonal
+#pragma unroll
+    for (int r = 0; r < 64; ++r) {
+        if (r >= M) break;
+        const float rd = sqrtf(piv[r]);
+        const float ri = 1.0f / rd;
+        const int c0 = lane, c1 = lane + 32;
+        if (c0 < M) A[r * lda + c0] = (c0 < r) ? 0.f : (c0 == r ? rd : ca[r] * ri);
+        if (c1 < M) A[r * lda + c1] = (c1 < r) ? 0.f : (c1 == r ? rd : cb[r] * ri);
+    }
+    return true;
 }
 
 // Cholesky G = R^T R of an M x M symmetric matrix in shared memory, upper R overwriting A
@@ -356,6 +413,17 @@ __device__ __forceinline__ void load_square(const double *g, int ldg, int M, con
 // leave at the same step).
 template <typename S>
 __device__ bool chol_upper_inplace(S *A, int lda, int M, S piv_rel2, S maxdiag, S *t, int *bad) {
+    if constexpr (std::is_same<S, float>::value) {
+        if (M <= 64) {
+            // one warp, registers and shuffles (chol_upper_warp64); the others wait
+            if (threadIdx.x < 32) {
+                const bool ok = chol_upper_warp64(A, lda, M, piv_rel2 * maxdiag, t);
+                if (threadIdx.x == 0) bad[0] = ok ? 0 : 1;
+            }
+            __syncthreads();
+            return bad[0] == 0;
+        }
+    }
     S *srow[2] = {t, t + M};   // u_j / d_j, double-buffered by the parity of j
     S *piv = t + 2 * M;        // d_j
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -514,17 +582,18 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
     if (bad) return;
     if (small) {
         // ---- pass 2, first order (FP32 path): S = I - Phi(E) applied; F = I - S exactly
-        for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
-            const int i = idx / W, j = idx % W;
-            T v = T(0);
-            if (i < M && j < M && j >= i) {
-                const double e = A[i * lda + j] - (i == j ? 1.0 : 0.0);
-                const double phi = (i == j) ? 0.5 * e : e;
-                v = T((i == j ? 1.0 : 0.0) - phi);
+        for (int i = threadIdx.x >> 5; i < W; i += blockDim.x >> 5)
+            for (int j = threadIdx.x & 31; j < W; j += 32) {
+                const int idx = i * W + j;
+                T v = T(0);
+                if (i < M && j < M && j >= i) {
+                    const double e = A[i * lda + j] - (i == j ? 1.0 : 0.0);
+                    const double phi = (i == j) ? 0.5 * e : e;
+                    v = T((i == j ? 1.0 : 0.0) - phi);
+                }
+                Rinv[idx] = v;
+                if (i < M && j < M) Sf[i * lda + j] = (j >= i) ? T((i == j ? 1.0 : 0.0) - double(v)) : T(0);
             }
-            Rinv[idx] = v;
-            if (i < M && j < M) Sf[i * lda + j] = (j >= i) ? T((i == j ? 1.0 : 0.0) - double(v)) : T(0);
-        }
         __syncthreads();
         // A is free now: R1 rounded to T, and C = F R1 (both upper triangular, zeros below)
         T *R1t = reinterpret_cast<T *>(A);
@@ -539,12 +608,12 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
         tri_mm_upper<T>(M, sf, [&](int k, int j) { return R1t[k * lda + j]; }, zero,
                         [&](int i, int j, T c) { Ct[i * lda + j] = c; });
         // entries of Hs and B outside H's upper triangle are zero
-        for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
-            const int i = idx / W, j = idx % W;
-            if (i < M && j < M && j >= i) continue;
-            if (i < M && j < M) Hs[i * M + j] = 0.0;
-            Bout[j * W + i] = T(0);
-        }
+        for (int i = threadIdx.x >> 5; i < W; i += blockDim.x >> 5)
+            for (int j = threadIdx.x & 31; j < W; j += 32) {
+                if (i < M && j < M && j >= i) continue;
+                if (i < M && j < M) Hs[i * M + j] = 0.0;
+                Bout[j * W + i] = T(0);
+            }
         __syncthreads();
         // H = (I + F + F^2) R1 = R1 + (C + F C), the corrections of relative size ||E||
         tri_mm_upper<T>(M, sf, [&](int k, int j) { return Ct[k * lda + j]; }, zero,
@@ -568,16 +637,16 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
     if (sizeof(T) == 4 && pass == 1) {
         float *Af = reinterpret_cast<float *>(Sf);   // Sf is free until the inverse below
         float *tf = reinterpret_cast<float *>(t);
-        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-            const int i = idx / M, j = idx % M;
-            Af[i * lda + j] = float(A[i * lda + j]);
-        }
+        for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
+            for (int j = threadIdx.x & 31; j < M; j += 32) {
+                Af[i * lda + j] = float(A[i * lda + j]);
+            }
         __syncthreads();
         if (chol_upper_inplace<float>(Af, lda, M, 1e-5f, float(maxdiag), tf, pivot_bad)) {
-            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-                const int i = idx / M, j = idx % M;
-                A[i * lda + j] = (j >= i) ? double(Af[i * lda + j]) : 0.0;
-            }
+            for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
+                for (int j = threadIdx.x & 31; j < M; j += 32) {
+                    A[i * lda + j] = (j >= i) ? double(Af[i * lda + j]) : 0.0;
+                }
             factored = true;
         }
         __syncthreads();
@@ -600,21 +669,22 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
     double *Sd = t + 3 * M + 2;                               // [M][M+1] (newton only)
     float *Rf = reinterpret_cast<float *>(Sd + M * lda);      // [M][M+1]
     float *C1 = Rf + M * lda;                                 // [M][M+1]
-    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-        const int i = idx / M, j = idx % M;
-        Sf[i * lda + j] = T(A[i * lda + j]);
-        if (newton) Rf[i * lda + j] = float(Sf[i * lda + j]);
-    }
+    for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
+        for (int j = threadIdx.x & 31; j < M; j += 32) {
+            Sf[i * lda + j] = T(A[i * lda + j]);
+            if (newton) Rf[i * lda + j] = float(Sf[i * lda + j]);
+        }
     __syncthreads();
     {
         // scratch after the Newton region (launch_chol sizes it)
         unsigned char *after = reinterpret_cast<unsigned char *>(t + 3 * M + 2) + (newton ? 16 * size_t(M) * lda : 0);
         tri_inv_upper_blocked<T>(Sf, lda, M, reinterpret_cast<T *>(after));
     }
-    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
-        const int i = idx / W, j = idx % W;
-        Rinv[idx] = (i < M && j < M && j >= i) ? Sf[i * lda + j] : T(0);
-    }
+    for (int i = threadIdx.x >> 5; i < W; i += blockDim.x >> 5)
+        for (int j = threadIdx.x & 31; j < W; j += 32) {
+            const int idx = i * W + j;
+            Rinv[idx] = (i < M && j < M && j >= i) ? Sf[i * lda + j] : T(0);
+        }
     if (sizeof(T) == 4) {
         // R := the FP64 inverse of the applied FP32 inverse S.
         bool exact = !newton;
@@ -630,14 +700,14 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
             // residual, which reads S from Sd, over S in Sf
             float *Ef = factored ? reinterpret_cast<float *>(Sd) : Sff;
             if (threadIdx.x == 0) emax_e = 0u;
-            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-                const int i = idx / M, j = idx % M;
-                if (factored) {
-                    if (j < i) Ef[i * lda + j] = 0.f;
-                } else {
-                    Sd[i * lda + j] = (j >= i) ? double(Sff[i * lda + j]) : 0.0;
+            for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
+                for (int j = threadIdx.x & 31; j < M; j += 32) {
+                    if (factored) {
+                        if (j < i) Ef[i * lda + j] = 0.f;
+                    } else {
+                        Sd[i * lda + j] = (j >= i) ? double(Sff[i * lda + j]) : 0.0;
+                    }
                 }
-            }
             __syncthreads();
             unsigned int my = 0u;
             auto put_e = [&](int i, int j, float ef) {
@@ -658,10 +728,10 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
             if (__uint_as_float(emax_e) < 1e-3f) {
                 auto ef = [&](int k, int j) { return Ef[k * lda + j]; };
                 auto zero = [](int, int) { return 0.f; };
-                for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-                    const int i = idx / M, j = idx % M;
-                    if (j < i) C1[i * lda + j] = 0.f;
-                }
+                for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
+                    for (int j = threadIdx.x & 31; j < M; j += 32) {
+                        if (j < i) C1[i * lda + j] = 0.f;
+                    }
                 tri_mm_upper<float>(M, [&](int i, int k) { return Rf[i * lda + k]; }, ef, zero,
                                     [&](int i, int j, float c) { C1[i * lda + j] = c; });
                 __syncthreads();
@@ -670,36 +740,37 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
                 __syncthreads();
             } else {
                 exact = true;
-                for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-                    const int i = idx / M, j = idx % M;
-                    A[i * lda + j] = factored ? ((j >= i) ? double(Sff[i * lda + j]) : 0.0) : Sd[i * lda + j];
-                }
+                for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
+                    for (int j = threadIdx.x & 31; j < M; j += 32) {
+                        A[i * lda + j] = factored ? ((j >= i) ? double(Sff[i * lda + j]) : 0.0) : Sd[i * lda + j];
+                    }
                 __syncthreads();
             }
         } else {
-            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-                const int i = idx / M, j = idx % M;
-                A[i * lda + j] = (j >= i) ? double(Sf[i * lda + j]) : 0.0;
-            }
+            for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
+                for (int j = threadIdx.x & 31; j < M; j += 32) {
+                    A[i * lda + j] = (j >= i) ? double(Sf[i * lda + j]) : 0.0;
+                }
             __syncthreads();
         }
         if (exact) tri_inv_upper_inplace<double>(A, lda, M, t);
     }
     // (FP64 basis: the inverse is applied in FP64, R needs no correction)
     if (pass == 1) {
-        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-            const int i = idx / M, j = idx % M;
-            R1[idx] = (j >= i) ? A[i * lda + j] : 0.0;
-        }
+        for (int i = threadIdx.x >> 5; i < M; i += blockDim.x >> 5)
+            for (int j = threadIdx.x & 31; j < M; j += 32) {
+                const int idx = i * M + j;
+                R1[idx] = (j >= i) ? A[i * lda + j] : 0.0;
+            }
     } else {
         // H_{k+1,k} = R2 R1 (upper triangular); B = H^T for the next three-term step.  H is
         // recorded rounded to the basis precision, i.e. exactly as the next step subtracts it.
-        for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
-            const int i = idx / W, j = idx % W;
-            if (i < M && j < M && j >= i) continue;
-            if (i < M && j < M) Hs[i * M + j] = 0.0;
-            Bout[j * W + i] = T(0);
-        }
+        for (int i = threadIdx.x >> 5; i < W; i += blockDim.x >> 5)
+            for (int j = threadIdx.x & 31; j < W; j += 32) {
+                if (i < M && j < M && j >= i) continue;
+                if (i < M && j < M) Hs[i * M + j] = 0.0;
+                Bout[j * W + i] = T(0);
+            }
         tri_mm_upper<double>(
             M, [&](int i, int k) { return A[i * lda + k]; }, [&](int k, int j) { return __ldg(R1 + k * M + j); },
             [](int, int) { return 0.0; },
@@ -715,34 +786,48 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
 // Reduce [nparts][W] partials per column (fixed order) into s[W].  df: the partials are
 // double-float pairs (FP32 arithmetic), combined on the FP32 pipe; else doubles.
 __device__ void reduce_cols(const double *parts, int nparts, int W, double *s, int df) {
-    // one warp per strided subset of the partials (up to 32 warps), two loads in flight
-    // per lane, then a fixed-order combination of the warps' sums
+    // one warp per strided subset of the partials (up to 32 warps), eight loads in flight per
+    // lane (each into its own accumulator, merged in a fixed order), then a fixed-order
+    // combination of the warps' sums
     __shared__ double tmp[32][128];
+    constexpr int U = 8;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int c0 = 0; c0 < W; c0 += 32) {
         const int c = c0 + lane;
         if (c >= W) continue;
         if (df) {
             const DF *pp = reinterpret_cast<const DF *>(parts);
-            DF a0{0.f, 0.f}, a1{0.f, 0.f};
+            DF a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) a[u] = DF{0.f, 0.f};
             int p = warp;
-            for (; p + nw < nparts; p += 2 * nw) {
-                const DF v0 = pp[int64_t(p) * W + c], v1 = pp[int64_t(p + nw) * W + c];
-                df_merge(a0, v0);
-                df_merge(a1, v1);
+            for (; p < nparts; p += U * nw) {
+                DF v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    v[u] = p + u * nw < nparts ? pp[int64_t(p + u * nw) * W + c] : DF{0.f, 0.f};
+#pragma unroll
+                for (int u = 0; u < U; ++u) df_merge(a[u], v[u]);
             }
-            if (p < nparts) df_merge(a0, pp[int64_t(p) * W + c]);
-            df_merge(a0, a1);
-            reinterpret_cast<DF *>(&tmp[warp][0])[c] = a0;
+#pragma unroll
+            for (int u = 1; u < U; ++u) df_merge(a[0], a[u]);
+            reinterpret_cast<DF *>(&tmp[warp][0])[c] = a[0];
         } else {
-            double a0 = 0.0, a1 = 0.0;
+            double a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) a[u] = 0.0;
             int p = warp;
-            for (; p + nw < nparts; p += 2 * nw) {
-                a0 += parts[int64_t(p) * W + c];
-                a1 += parts[int64_t(p + nw) * W + c];
+            for (; p < nparts; p += U * nw) {
+                double v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) v[u] = p + u * nw < nparts ? parts[int64_t(p + u * nw) * W + c] : 0.0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) a[u] += v[u];
             }
-            if (p < nparts) a0 += parts[int64_t(p) * W + c];
-            tmp[warp][c] = a0 + a1;
+            double t = a[0];
+#pragma unroll
+            for (int u = 1; u < U; ++u) t += a[u];
+            tmp[warp][c] = t;
         }
     }
     __syncthreads();
@@ -1431,40 +1516,63 @@ __global__ void __launch_bounds__(256) k_frontier_expand_listed(GraphDev g, uint
     }
 }
 
-// Stream compaction of the active 32-row tiles in tile order: each thread counts a contiguous
-// range, a block-wide exclusive scan gives its output offset, then it writes its range.
+// Stream compaction of the active 32-row tiles in tile order.  Each warp owns a contiguous
+// range of 32-entry groups and reads them coalesced, eight groups in flight; a ballot gives
+// each group's active lanes, so the warp's count and, in the second pass, each active
+// entry's position (the active lanes below it) come from population counts.  A block-wide
+// exclusive scan of the warp counts gives each warp's output offset; the second pass reads
+// the 4-byte-per-tile array again from cache.
 __global__ void __launch_bounds__(1024) k_frontier_list(const int32_t *__restrict__ tgen, int64_t nact,
                                                         int limit, int32_t *__restrict__ list,
                                                         int32_t *__restrict__ count) {
-    __shared__ int wsum[32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t per = (nact + blockDim.x - 1) / blockDim.x;
-    const int64_t a0 = int64_t(tid) * per;
-    const int64_t a1 = a0 + per < nact ? a0 + per : nact;
+    __shared__ int wsum[33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t ngrp = (nact + 31) / 32;
+    const int64_t gper = (ngrp + nw - 1) / nw;
+    const int64_t g0 = int64_t(warp) * gper;
+    const int64_t g1 = g0 + gper < ngrp ? g0 + gper : ngrp;
     int c = 0;
-#pragma unroll 8
-    for (int64_t a = a0; a < a1; ++a) c += __ldg(tgen + a) <= limit ? 1 : 0;
-    int incl = c;
-    for (int off = 1; off < 32; off <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += v;
+    for (int64_t g = g0; g < g1; g += 8) {
+        int32_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t a = (g + u) * 32 + lane;
+            v[u] = (g + u < g1 && a < nact) ? __ldg(tgen + a) : INT_MAX;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) c += __popc(__ballot_sync(0xffffffffu, v[u] <= limit));
     }
-    if (lane == 31) wsum[warp] = incl;
+    if (lane == 0) wsum[warp] = c;
     __syncthreads();
     if (warp == 0) {
-        int v = lane < int(blockDim.x >> 5) ? wsum[lane] : 0;
+        const int own = lane < nw ? wsum[lane] : 0;
+        int incl = own;
         for (int off = 1; off < 32; off <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, v, off);
-            if (lane >= off) v += u;
+            const int u = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += u;
         }
-        wsum[lane] = v;
+        wsum[lane] = incl - own;               // exclusive offset of warp `lane`
+        if (lane == 31) wsum[32] = incl;       // total
     }
     __syncthreads();
-    int pos = (warp > 0 ? wsum[warp - 1] : 0) + incl - c;
-#pragma unroll 8
-    for (int64_t a = a0; a < a1; ++a)
-        if (__ldg(tgen + a) <= limit) list[pos++] = int32_t(a);
-    if (tid == int(blockDim.x) - 1) *count = pos;
+    int pos = wsum[warp];
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t g = g0; g < g1; g += 8) {
+        int32_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t a = (g + u) * 32 + lane;
+            v[u] = (g + u < g1 && a < nact) ? __ldg(tgen + a) : INT_MAX;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool on = v[u] <= limit;
+            const unsigned mask = __ballot_sync(0xffffffffu, on);
+            if (on) list[pos + __popc(mask & below)] = int32_t((g + u) * 32 + lane);
+            pos += __popc(mask);
+        }
+    }
+    if (threadIdx.x == 0) *count = wsum[32];
 }
 
 int launch_frontier_list(const int32_t *tgen, int64_t n, int limit, int32_t *list, int32_t *count,
@@ -1498,7 +1606,7 @@ int launch_fill_nan(float *Y, int64_t n, int64_t ldy, int mo, const Ctrl *ctrl, 
 template <typename T>
 int launch_hkk(const double *G, int M, int W, double *Hd, T *C, const Ctrl *ctrl, cudaStream_t s) {
     prof_begin(KernelClass::SMALL, s);
-    k_hkk<T><<<1, 256, 0, s>>>(G, M, W, Hd, C, ctrl);
+    k_hkk<T><<<1, 1024, 0, s>>>(G, M, W, Hd, C, ctrl);
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::SMALL, s, 0, 0);
     return 0;
