@@ -353,7 +353,7 @@ __device__ __forceinline__ void load_square(const double *g, int ldg, int M, con
 // A[a][c] -= u_j[a] (u_j[c] / d_j), for the rows a > j that lie on or above the diagonal of
 // its column set.  No block barrier is needed, so a column costs a few shuffles rather than
 // a barrier round trip.  The arithmetic of every entry is that of chol_upper_inplace.
-// Returns false on a pivot <= thr (warp-uniform); piv: 64 floats of shared scratch.
+// Returns false on a pivot <= thr (warp-uniform); piv: M floats of shared scratch.
 __device__ bool chol_upper_warp64(float *A, int lda, int M, float thr, float *piv) {
     const int lane = threadIdx.x & 31;
     float ca[64], cb[64];
@@ -371,7 +371,7 @@ __device__ bool chol_upper_warp64(float *A, int lda, int M, float thr, float *pi
             ok = false;
             break;
         }
-        if (lane == 0) piv[j] = d;
+        if (lane == 0 && j < M) piv[j] = d;   // the padded pivots (1) are not stored
         const float dinv = 1.0f / d;
         const float sa = ca[j] * dinv, sb = cb[j] * dinv;
 #pragma unroll

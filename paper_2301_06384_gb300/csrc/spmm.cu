@@ -162,8 +162,9 @@ struct SpmmOcc {
     static constexpr int value = sizeof(typename Cmp<T>::type) == 8 ? 3 : (DOT ? KB_SPMM_OCC_DOT : KB_SPMM_OCC);
 };
 
-// WGT: the graph stores edge weights (false: unit weights, w_ij = 1)
-template <typename T, int W, bool DOT, bool WGT>
+// WGT: the graph stores edge weights (false: unit weights, w_ij = 1).  LST: the launch walks
+// the active-tile list (frontier restriction with a list of the active 32-row tiles).
+template <typename T, int W, bool DOT, bool WGT, bool LST>
 __global__ void __launch_bounds__(SPMM_THREADS, (SpmmOcc<T, DOT>::value))
 k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
     using G = SpmmGeo<W>;
@@ -216,8 +217,13 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
     const int64_t ntiles = (g.n + TR - 1) / TR;
     // with the active-tile list, the unit of work is one listed 32-row tile instead of a
     // TR-row tile: the few active rows of an early step spread over all CTAs
-    const bool listed = e.alist && e.tgen && !e.zero_inactive;
+    constexpr bool listed = LST;
     const int64_t nloop = listed ? int64_t(*e.acount) : ntiles;
+    // A listed unit is one chunk of 32 rows: its lane groups read their row pointers and
+    // column indices straight from global memory, with no shared staging and no barrier, so
+    // the warps of a CTA move through their units independently.  The coefficients set above
+    // are ordered here.
+    if constexpr (listed) __syncthreads();
 
     for (int64_t it = blockIdx.x; it < nloop; it += gridDim.x) {
         const int64_t r0 = listed ? int64_t(__ldg(e.alist + it)) * ACT_ROWS : it * TR;
@@ -235,10 +241,12 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
             }
             continue;
         }
-        // ask L2 for the tile's own dense rows now (x_i at the row start, y / z in the
-        // epilogue) and for the next tile's row pointers, so that those loads, issued later,
-        // do not wait on DRAM
-        {
+        int base = 0;
+        bool staged = false;
+        if constexpr (!listed) {
+            // ask L2 for the tile's own dense rows now (x_i at the row start, y / z in the
+            // epilogue) and for the next tile's row pointers, so that those loads, issued
+            // later, do not wait on DRAM
             const char *xb = reinterpret_cast<const char *>(x + r0 * W);
             const int64_t tile_bytes = int64_t(rows) * W * int64_t(sizeof(T));
             constexpr int64_t row_bytes = int64_t(W) * int64_t(sizeof(T));
@@ -252,20 +260,20 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
             const int64_t nr0 = r0 + int64_t(gridDim.x) * TR;
             if (threadIdx.x < (TR + 1 + 31) / 32 && nr0 + threadIdx.x * 32 <= g.n)
                 prefetch_l2(g.rowptr + nr0 + threadIdx.x * 32);
-        }
-        __syncthreads();   // previous tile done with the shared arrays
-        for (int i = threadIdx.x; i <= rows; i += blockDim.x) s_rp[i] = __ldg(g.rowptr + r0 + i);
-        __syncthreads();
-        const int base = s_rp[0];
-        const int cnt = s_rp[rows] - base;
-        const bool staged = cnt <= CAP;
-        if (staged) {
-            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-                s_col[i] = __ldg(g.col + base + i);
-                if (WGT) s_w[i] = __ldg(g.w + base + i);
+            __syncthreads();   // previous tile done with the shared arrays
+            for (int i = threadIdx.x; i <= rows; i += blockDim.x) s_rp[i] = __ldg(g.rowptr + r0 + i);
+            __syncthreads();
+            base = s_rp[0];
+            const int cnt = s_rp[rows] - base;
+            staged = cnt <= CAP;
+            if (staged) {
+                for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                    s_col[i] = __ldg(g.col + base + i);
+                    if (WGT) s_w[i] = __ldg(g.w + base + i);
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
 #pragma unroll 1
         for (int rr = 0; rr < RPG; ++rr) {
             // rows rr*NG .. rr*NG+NG-1 of the tile (one lane group each); with the frontier
@@ -285,7 +293,7 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                 for (int q = 0; q < RPW; ++q)
                     if (wr0 + q < rows && int(__ldg(e.gen + r0 + wr0 + q)) <= e.limit) any = true;
                 skip_rows = !any;
-            } else if (!skip_rows && threadIdx.x == 0) {
+            } else if (!skip_rows && threadIdx.x == 0 && !listed) {
                 s_cnt[0] += unsigned(crows);
                 s_cnt[1] += unsigned(s_rp[c0r + crows] - s_rp[c0r]);
             }
@@ -310,14 +318,16 @@ k_spmm(GraphDev g, const T *__restrict__ x, LinEpi<T> e, int64_t ldo, int mo) {
                 const int wr0 = c0r + warp * RPW;
                 const int wr1 = wr0 + RPW < rows ? wr0 + RPW : rows;
                 if (wr1 > wr0) {
+                    const int nz = listed ? __ldg(g.rowptr + r0 + wr1) - __ldg(g.rowptr + r0 + wr0)
+                                          : s_rp[wr1] - s_rp[wr0];
                     atomicAdd(&s_cnt[0], (unsigned long long)(wr1 - wr0));
-                    atomicAdd(&s_cnt[1], (unsigned long long)(s_rp[wr1] - s_rp[wr0]));
+                    atomicAdd(&s_cnt[1], (unsigned long long)nz);
                 }
             }
             if (lrow >= rows) continue;
             const int64_t row = r0 + lrow;
-            const int beg = s_rp[lrow] - base;
-            const int end = s_rp[lrow + 1] - base;
+            const int beg = listed ? __ldg(g.rowptr + row) : s_rp[lrow] - base;
+            const int end = listed ? __ldg(g.rowptr + row + 1) : s_rp[lrow + 1] - base;
             V4<T> xi[VPL];
             C acc[VPL][4];
 #pragma unroll
@@ -512,7 +522,7 @@ int occupancy_spmm() {
     // function-local static: computed once, thread-safe (several serving workers)
     static const int per_sm = [] {
         int v = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmm<T, W, DOT, true>, SPMM_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_spmm<T, W, DOT, true, false>, SPMM_THREADS, 0);
         return v < 1 ? 1 : v;
     }();
     return per_sm;
@@ -525,8 +535,14 @@ int launch_wd(const GraphDev &g, const T *x, const LinEpi<T> &e, int64_t ldo, in
     int grid = int(std::min<int64_t>(ntiles, int64_t(num_sms()) * occupancy_spmm<T, W, DOT>()));
     if (grid < 1) grid = 1;
     if (grid_out) *grid_out = grid;
-    if (g.w) k_spmm<T, W, DOT, true><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
-    else k_spmm<T, W, DOT, false><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
+    const bool lst = e.alist && e.tgen && !e.zero_inactive;
+    if (g.w) {
+        if (lst) k_spmm<T, W, DOT, true, true><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
+        else k_spmm<T, W, DOT, true, false><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
+    } else {
+        if (lst) k_spmm<T, W, DOT, false, true><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
+        else k_spmm<T, W, DOT, false, false><<<grid, SPMM_THREADS, 0, s>>>(g, x, e, ldo, mo);
+    }
     return 0;
 }
 
