@@ -223,15 +223,15 @@ __device__ __forceinline__ double group_sum(double v, int tpc) {
     return v;
 }
 
-// rhs_in_u: U already holds the right-hand side (steps blocks); else U starts as F_1.
+// Block Cholesky factorisation eps I + H = L L^T of the block tridiagonal Lanczos matrix (L
+// block lower bidiagonal: lower triangular diagonal blocks Ld_r, sub-diagonal blocks Ls_r).
 // One CTA of 1024 threads.  The dense block products (the Schur complement update of each
-// diagonal block, and the coupling terms of the substitutions) run over all threads, one
-// output each; the triangular solves (the sub-diagonal factor rows, and forward / backward
-// substitution per right-hand-side column) give each row or column a lane group, so their
-// dependent chains are TPC times shorter than with one thread per column.
+// diagonal block) run over all threads, one output each; the triangular solves of the
+// sub-diagonal factor rows give each row a lane group, so their dependent chains are TPC
+// times shorter than with one thread per row.
 __global__ void __launch_bounds__(1024)
-k_bt_spline(const double *Hd, const double *Hs, int M, double eps, int s_int, double *Ld,
-            double *Ls, double *Yw, double *U, const Ctrl *ctrl, int rhs_in_u) {
+k_bt_spline_factor(const double *Hd, const double *Hs, int M, double eps, double *Ld, double *Ls,
+                   const Ctrl *ctrl) {
     const int steps = ctrl->steps;
     const int64_t MM = int64_t(M) * M;
     const int tpc = tpc_for(M);
@@ -269,67 +269,123 @@ k_bt_spline(const double *Hd, const double *Hs, int M, double eps, int s_int, do
         }
         __syncthreads();
     }
-    // U = F_1 (unless it holds the right-hand side), then s_int times U <- (eps I + H)^{-1} U
-    if (!rhs_in_u) {
-        for (int idx = threadIdx.x; idx < steps * M * M; idx += blockDim.x) {
-            const int64_t blk = idx / MM;
-            const int i = int((idx / M) % M), j = int(idx % M);
-            U[idx] = (blk == 0 && i == j) ? 1.0 : 0.0;
-        }
-    }
-    __syncthreads();
+}
+
+// s_int times U <- (eps I + H)^{-1} U with the factors of k_bt_spline_factor, by forward and
+// backward block substitution; U starts as F_1 = [I; 0; ...] unless rhs_in_u (U already holds
+// the right-hand side, steps blocks).  The right-hand-side columns are independent: one warp
+// per column, BTS_COLS columns per CTA, the CTAs side by side (FP64 runs at a small fraction
+// of the FP32 rate on this part, so the columns are spread over as many SMs as there are).  A
+// warp keeps its column of the current block in registers (lane l: rows l, l + 32, l + 64,
+// l + 96; M <= 128), takes the coupling term Ls y from the previous block's column (broadcast
+// by shuffles) and solves the triangular system column-oriented: y_i /= d_ii, then
+// y_k -= d_ki y_i for the rows k below (k above in the backward solve with D^T), one shuffle
+// per row.  No block barrier is used.  Yw holds the forward solutions Y_r for the backward
+// pass.
+constexpr int BTS_COLS = 1;
+constexpr int BTS_R = 4;   // rows per lane
+__global__ void __launch_bounds__(32 * BTS_COLS)
+k_bt_spline_subst(const double *__restrict__ Ld, const double *__restrict__ Ls, int M, int s_int,
+                  double *__restrict__ Yw, double *__restrict__ U, const Ctrl *ctrl, int rhs_in_u) {
+    const int steps = ctrl->steps;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * BTS_COLS + (threadIdx.x >> 5);
+    if (c >= M) return;   // whole warps: nothing below synchronises the block
+    const int64_t MM = int64_t(M) * M;
+    double y[BTS_R], yp[BTS_R], rd[BTS_R];
     for (int rep = 0; rep < s_int; ++rep) {
         // forward: Y_r = D_r^{-1} (U_r - Ls_{r-1} Y_{r-1})
         for (int r = 0; r < steps; ++r) {
             const double *D = Ld + r * MM;
-            double *Y = Yw + r * MM;
-            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-                const int i = idx / M, c = idx % M;
-                double v = U[r * MM + idx];
-                if (r > 0) {
-                    const double *P = Ls + (r - 1) * MM;
-                    const double *Yp = Yw + (r - 1) * MM;
-                    for (int k = 0; k < M; ++k) v = fma(-P[i * M + k], Yp[k * M + c], v);
+#pragma unroll
+            for (int q = 0; q < BTS_R; ++q) {
+                const int i = lane + 32 * q;
+                double v = 0.0, d = 1.0;
+                if (i < M) {
+                    v = (rep == 0 && !rhs_in_u) ? ((r == 0 && i == c) ? 1.0 : 0.0) : U[r * MM + int64_t(i) * M + c];
+                    d = D[int64_t(i) * M + i];
                 }
-                Y[idx] = v;
+                y[q] = v;
+                rd[q] = 1.0 / d;
             }
-            for (int i = threadIdx.x; i < M; i += blockDim.x) rd[i] = 1.0 / D[i * M + i];
-            __syncthreads();
-            for (int i = 0; i < M; ++i) {
-                double part = 0.0;
-                if (gact)
-                    for (int k = sub; k < i; k += tpc) part = fma(D[i * M + k], Y[k * M + grp], part);
-                part = group_sum(part, tpc);
-                if (gact && sub == 0) Y[i * M + grp] = (Y[i * M + grp] - part) * rd[i];
-                __syncwarp();
+            if (r > 0) {
+                const double *P = Ls + (r - 1) * MM;
+#pragma unroll
+                for (int kq = 0; kq < BTS_R; ++kq)
+                    for (int kl = 0; kl < 32; ++kl) {
+                        const int k = 32 * kq + kl;
+                        if (k >= M) break;
+                        const double ypk = __shfl_sync(0xffffffffu, yp[kq], kl);
+#pragma unroll
+                        for (int q = 0; q < BTS_R; ++q) {
+                            const int i = lane + 32 * q;
+                            if (i < M) y[q] = fma(-P[int64_t(i) * M + k], ypk, y[q]);
+                        }
+                    }
             }
-            __syncthreads();
+#pragma unroll
+            for (int iq = 0; iq < BTS_R; ++iq)
+                for (int il = 0; il < 32; ++il) {
+                    const int i = 32 * iq + il;
+                    if (i >= M) break;
+                    const double yi = __shfl_sync(0xffffffffu, y[iq], il) * __shfl_sync(0xffffffffu, rd[iq], il);
+                    if (lane == il) y[iq] = yi;
+#pragma unroll
+                    for (int q = 0; q < BTS_R; ++q) {
+                        const int k = lane + 32 * q;
+                        if (k > i && k < M) y[q] = fma(-D[int64_t(k) * M + i], yi, y[q]);
+                    }
+                }
+#pragma unroll
+            for (int q = 0; q < BTS_R; ++q) {
+                const int i = lane + 32 * q;
+                if (i < M) Yw[r * MM + int64_t(i) * M + c] = y[q];
+                yp[q] = y[q];
+            }
         }
         // backward: U_r = D_r^{-T} (Y_r - Ls_r^T U_{r+1})
         for (int r = steps - 1; r >= 0; --r) {
             const double *D = Ld + r * MM;
-            double *Ur = U + r * MM;
-            for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-                const int i = idx / M, c = idx % M;
-                double v = Yw[r * MM + idx];
-                if (r + 1 < steps) {
-                    const double *P = Ls + r * MM;
-                    const double *Un = U + (r + 1) * MM;
-                    for (int k = 0; k < M; ++k) v = fma(-P[k * M + i], Un[k * M + c], v);
+#pragma unroll
+            for (int q = 0; q < BTS_R; ++q) {
+                const int i = lane + 32 * q;
+                y[q] = i < M ? Yw[r * MM + int64_t(i) * M + c] : 0.0;
+                rd[q] = 1.0 / (i < M ? D[int64_t(i) * M + i] : 1.0);
+            }
+            if (r + 1 < steps) {
+                const double *P = Ls + r * MM;
+#pragma unroll
+                for (int kq = 0; kq < BTS_R; ++kq)
+                    for (int kl = 0; kl < 32; ++kl) {
+                        const int k = 32 * kq + kl;
+                        if (k >= M) break;
+                        const double unk = __shfl_sync(0xffffffffu, yp[kq], kl);
+#pragma unroll
+                        for (int q = 0; q < BTS_R; ++q) {
+                            const int i = lane + 32 * q;
+                            if (i < M) y[q] = fma(-P[int64_t(k) * M + i], unk, y[q]);
+                        }
+                    }
+            }
+#pragma unroll
+            for (int iq = BTS_R - 1; iq >= 0; --iq)
+                for (int il = 31; il >= 0; --il) {
+                    const int i = 32 * iq + il;
+                    if (i >= M) continue;
+                    const double ui = __shfl_sync(0xffffffffu, y[iq], il) * __shfl_sync(0xffffffffu, rd[iq], il);
+                    if (lane == il) y[iq] = ui;
+#pragma unroll
+                    for (int q = 0; q < BTS_R; ++q) {
+                        const int k = lane + 32 * q;
+                        if (k < i) y[q] = fma(-D[int64_t(i) * M + k], ui, y[q]);
+                    }
                 }
-                Ur[idx] = v;
+#pragma unroll
+            for (int q = 0; q < BTS_R; ++q) {
+                const int i = lane + 32 * q;
+                if (i < M) U[r * MM + int64_t(i) * M + c] = y[q];
+                yp[q] = y[q];
             }
-            for (int i = threadIdx.x; i < M; i += blockDim.x) rd[i] = 1.0 / D[i * M + i];
-            __syncthreads();
-            for (int i = M - 1; i >= 0; --i) {
-                double part = 0.0;
-                if (gact)
-                    for (int k = i + 1 + sub; k < M; k += tpc) part = fma(D[k * M + i], Ur[k * M + grp], part);
-                part = group_sum(part, tpc);
-                if (gact && sub == 0) Ur[i * M + grp] = (Ur[i * M + grp] - part) * rd[i];
-                __syncwarp();
-            }
-            __syncthreads();
         }
     }
 }
@@ -508,13 +564,19 @@ int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double ep
             k_quad_accumulate<<<std::max(acc_grid, 1), 256, 0, s>>>(qscr, M, m, nb, *q, j0, U, ctrl);
             launches += 2;
         }
-        if (s_int > 0) k_bt_spline<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, s_int, Ld, Ls, Yw, U, ctrl, 1);
-        else --launches;
+        if (s_int > 0) {
+            k_bt_spline_factor<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, Ld, Ls, ctrl);
+            k_bt_spline_subst<<<(M + BTS_COLS - 1) / BTS_COLS, 32 * BTS_COLS, 0, s>>>(Ld, Ls, M, s_int, Yw, U, ctrl, 1);
+            ++launches;
+        } else {
+            --launches;
+        }
     } else {
         // (blocks past the steps stay zero: the bound check reads all m of them)
         zero_if_active(U, int64_t(m) * M * M, ctrl, s);
-        k_bt_spline<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, s_int, Ld, Ls, Yw, U, ctrl, 0);
-        ++launches;
+        k_bt_spline_factor<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, Ld, Ls, ctrl);
+        k_bt_spline_subst<<<(M + BTS_COLS - 1) / BTS_COLS, 32 * BTS_COLS, 0, s>>>(Ld, Ls, M, s_int, Yw, U, ctrl, 0);
+        launches += 2;
     }
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::PROJECTED, s, 0, 0, launches);

@@ -407,32 +407,26 @@ template <typename P>
 __global__ void __launch_bounds__(1024) k_reduce(const P *__restrict__ parts, int nparts, int len,
                                                   double *__restrict__ out, const Ctrl *ctrl,
                                                   P *__restrict__ out_p) {
-    // 32 columns per CTA, 32 warps over the partials (eight loads in flight per lane, each
-    // into its own accumulator, merged in a fixed order), then a fixed-order combination of
-    // the warps' sums by warp 0
+    // 32 columns per CTA, 32 warps over the partials (two loads in flight per lane), then a
+    // fixed-order combination of the warps' sums by warp 0
     if (ctrl && ctrl->stop) return;
     __shared__ double s[32][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int e = blockIdx.x * 32 + lane;
-    constexpr int U = 8;
     if constexpr (std::is_same<P, float>::value) {
         // double-float accumulation on the FP32 pipe
-        DF a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) a[u] = DF{0.f, 0.f};
+        DF a0{0.f, 0.f}, a1{0.f, 0.f};
         if (e < len) {
             int p = warp;
-            for (; p < nparts; p += U * nw) {
-                float v[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) v[u] = p + u * nw < nparts ? parts[int64_t(p + u * nw) * len + e] : 0.f;
-#pragma unroll
-                for (int u = 0; u < U; ++u) df_add(a[u], v[u]);
+            for (; p + nw < nparts; p += 2 * nw) {
+                const float v0 = parts[int64_t(p) * len + e], v1 = parts[int64_t(p + nw) * len + e];
+                df_add(a0, v0);
+                df_add(a1, v1);
             }
+            if (p < nparts) df_add(a0, parts[int64_t(p) * len + e]);
         }
-#pragma unroll
-        for (int u = 1; u < U; ++u) df_merge(a[0], a[u]);
-        reinterpret_cast<DF *>(&s[warp][0])[lane] = a[0];
+        df_merge(a0, a1);
+        reinterpret_cast<DF *>(&s[warp][0])[lane] = a0;
         __syncthreads();
         if (warp == 0 && e < len) {
             DF t = reinterpret_cast<const DF *>(&s[0][0])[lane];
@@ -442,23 +436,9 @@ __global__ void __launch_bounds__(1024) k_reduce(const P *__restrict__ parts, in
             if (out_p) out_p[e] = P(v);
         }
     } else {
-        double a[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) a[u] = 0.0;
-        if (e < len) {
-            int p = warp;
-            for (; p < nparts; p += U * nw) {
-                double v[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    v[u] = p + u * nw < nparts ? double(parts[int64_t(p + u * nw) * len + e]) : 0.0;
-#pragma unroll
-                for (int u = 0; u < U; ++u) a[u] += v[u];
-            }
-        }
-        double acc = a[0];
-#pragma unroll
-        for (int u = 1; u < U; ++u) acc += a[u];
+        double acc = 0.0;
+        if (e < len)
+            for (int p = warp; p < nparts; p += nw) acc += double(parts[int64_t(p) * len + e]);
         s[warp][lane] = acc;
         __syncthreads();
         if (warp == 0 && e < len) {

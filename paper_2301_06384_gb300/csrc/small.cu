@@ -345,57 +345,6 @@ __device__ __forceinline__ void load_square(const double *g, int ldg, int M, con
         }
 }
 
-// The same square-root-free factorisation of an M x M matrix (M <= 64, FP32) by one warp
-// with the matrix in registers: lane l holds columns l and l + 32 (64 rows each; beyond M the
-// matrix is extended by the identity, whose pivots are 1 and whose updates are exact no-ops).
-// Step j broadcasts the pivot d_j and then the pivot row u_j one entry at a time (a shuffle
-// from the lane that holds column a), and each lane updates its two columns,
-// A[a][c] -= u_j[a] (u_j[c] / d_j), for the rows a > j that lie on or above the diagonal of
-// its column set.  No block barrier is needed, so a column costs a few shuffles rather than
-// a barrier round trip.  The arithmetic of every entry is that of chol_upper_inplace.
-// Returns false on a pivot <= thr (warp-uniform); piv: M floats of shared scratch.
-__device__ bool chol_upper_warp64(float *A, int lda, int M, float thr, float *piv) {
-    const int lane = threadIdx.x & 31;
-    float ca[64], cb[64];
-#pragma unroll
-    for (int r = 0; r < 64; ++r) {
-        const int c0 = lane, c1 = lane + 32;
-        ca[r] = (r < M && c0 < M) ? A[r * lda + c0] : (r == c0 ? 1.f : 0.f);
-        cb[r] = (r < M && c1 < M) ? A[r * lda + c1] : (r == c1 ? 1.f : 0.f);
-    }
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < 64; ++j) {
-        const float d = __shfl_sync(0xffffffffu, j < 32 ? ca[j] : cb[j], j & 31);
-        if (j < M && !(d > thr)) {
-            ok = false;
-            break;
-        }
-        if (lane == 0 && j < M) piv[j] = d;   // the padded pivots (1) are not stored
-        const float dinv = 1.0f / d;
-        const float sa = ca[j] * dinv, sb = cb[j] * dinv;
-#pragma unroll
-        for (int a = j + 1; a < 64; ++a) {
-            const float ua = __shfl_sync(0xffffffffu, a < 32 ? ca[j] : cb[j], a & 31);
-            if (a < 32) ca[a] = fmaf(-ua, sa, ca[a]);   // rows >= 32 of columns < 32: below the diagonal
-            cb[a] = fmaf(-ua, sb, cb[a]);
-        }
-    }
-    if (!ok) return false;
-    __syncwarp();
-    // R_jj = sqrt(d_j), R_jc = u_jc / sqrt(d_j), zeros below the diagonal
-#pragma unroll
-    for (int r = 0; r < 64; ++r) {
-        if (r >= M) break;
-        const float rd = sqrtf(piv[r]);
-        const float ri = 1.0f / rd;
-        const int c0 = lane, c1 = lane + 32;
-        if (c0 < M) A[r * lda + c0] = (c0 < r) ? 0.f : (c0 == r ? rd : ca[r] * ri);
-        if (c1 < M) A[r * lda + c1] = (c1 < r) ? 0.f : (c1 == r ? rd : cb[r] * ri);
-    }
-    return true;
-}
-
 // Cholesky G = R^T R of an M x M symmetric matrix in shared memory, upper R overwriting A
 // and the lower part zeroed.  Square-root-free form: step j needs the pivot d_j (the
 // diagonal of the current Schur complement) and one reciprocal; the Schur complement update
@@ -413,17 +362,6 @@ __device__ bool chol_upper_warp64(float *A, int lda, int M, float thr, float *pi
 // leave at the same step).
 template <typename S>
 __device__ bool chol_upper_inplace(S *A, int lda, int M, S piv_rel2, S maxdiag, S *t, int *bad) {
-    if constexpr (std::is_same<S, float>::value) {
-        if (M <= 64) {
-            // one warp, registers and shuffles (chol_upper_warp64); the others wait
-            if (threadIdx.x < 32) {
-                const bool ok = chol_upper_warp64(A, lda, M, piv_rel2 * maxdiag, t);
-                if (threadIdx.x == 0) bad[0] = ok ? 0 : 1;
-            }
-            __syncthreads();
-            return bad[0] == 0;
-        }
-    }
     S *srow[2] = {t, t + M};   // u_j / d_j, double-buffered by the parity of j
     S *piv = t + 2 * M;        // d_j
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
