@@ -194,27 +194,43 @@ __device__ void tri_inv_upper_blocked(S *A, int lda, int M, S *tmp) {
     }
     __syncthreads();
     for (int lg = 3, bs = 8; bs < M; ++lg, bs *= 2) {
-        // T_p = A_p^-1 B_p for every pair p (rows r0.., columns r0 + bs..)
+        // T_p = A_p^-1 B_p for every pair p (rows r0.., columns r0 + bs..); each thread four
+        // consecutive columns of one row (four independent FMA chains sharing the A loads)
         const int npairs = (M + 2 * bs - 1) / (2 * bs);
         const int per = bs * bs;
-        for (int idx = threadIdx.x; idx < npairs * per; idx += blockDim.x) {
-            const int p = idx >> (2 * lg), i = (idx >> lg) & (bs - 1), c = idx & (bs - 1);
+        const int lq = lg - 2;   // log2(bs / 4)
+        for (int idx = threadIdx.x; idx < npairs * (per >> 2); idx += blockDim.x) {
+            const int p = idx >> (2 * lg - 2), i = (idx >> lq) & (bs - 1), c = (idx & ((bs >> 2) - 1)) << 2;
             const int r0 = p * 2 * bs, cb = min(bs, M - r0 - bs);
             if (cb <= 0 || c >= cb) continue;
-            S acc = S(0);
-            for (int k = i; k < bs; ++k) acc = fma(A[(r0 + i) * lda + r0 + k], A[(r0 + k) * lda + r0 + bs + c], acc);
-            tmp[p * per + i * bs + c] = acc;
+            S acc[4] = {S(0), S(0), S(0), S(0)};
+            for (int k = i; k < bs; ++k) {
+                const S a = A[(r0 + i) * lda + r0 + k];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c + q < cb) acc[q] = fma(a, A[(r0 + k) * lda + r0 + bs + c + q], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tmp[p * per + i * bs + c + q] = acc[q];
         }
         __syncthreads();
-        // B_p <- -T_p C_p^-1 (C^-1 upper triangular)
-        for (int idx = threadIdx.x; idx < npairs * per; idx += blockDim.x) {
-            const int p = idx >> (2 * lg), i = (idx >> lg) & (bs - 1), c = idx & (bs - 1);
+        // B_p <- -T_p C_p^-1 (C^-1 upper triangular: the terms k > c are exact zeros)
+        for (int idx = threadIdx.x; idx < npairs * (per >> 2); idx += blockDim.x) {
+            const int p = idx >> (2 * lg - 2), i = (idx >> lq) & (bs - 1), c = (idx & ((bs >> 2) - 1)) << 2;
             const int r0 = p * 2 * bs, cb = min(bs, M - r0 - bs);
             if (cb <= 0 || c >= cb) continue;
             const int c0 = r0 + bs;
-            S acc = S(0);
-            for (int k = 0; k <= c; ++k) acc = fma(tmp[p * per + i * bs + k], A[(c0 + k) * lda + c0 + c], acc);
-            A[(r0 + i) * lda + c0 + c] = -acc;
+            S acc[4] = {S(0), S(0), S(0), S(0)};
+            const int kend = min(c + 4, cb);
+            for (int k = 0; k < kend; ++k) {
+                const S t = tmp[p * per + i * bs + k];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c + q < cb) acc[q] = fma(t, A[(c0 + k) * lda + c0 + c + q], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (c + q < cb) A[(r0 + i) * lda + c0 + c + q] = -acc[q];
         }
         __syncthreads();
     }
@@ -383,26 +399,62 @@ __device__ bool chol_upper_inplace(S *A, int lda, int M, S piv_rel2, S maxdiag, 
         const S *sr = srow[j & 1];
         if (warp == 0) {
             if (j + 1 < M) {
-                // the next pivot row: A[j+1][c] -= u_{j,j+1} u_{j,c} / d_j, c >= j+1
+                // the next pivot row: A[j+1][c] -= u_{j,j+1} u_{j,c} / d_j, c >= j+1, held in
+                // registers (lane l: c = j+1+l+32q); its pivot comes from lane 0 by a shuffle
                 const S ujn = A[j * lda + j + 1];
-                for (int c = j + 1 + lane; c < M; c += 32) A[(j + 1) * lda + c] -= ujn * sr[c];
-                __syncwarp();
-                const S d = A[(j + 1) * lda + j + 1];
+                S v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = j + 1 + lane + 32 * q;
+                    v[q] = c < M ? fma(-ujn, sr[c], A[(j + 1) * lda + c]) : S(0);
+                }
+                const S d = __shfl_sync(0xffffffffu, v[0], 0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int c = j + 1 + lane + 32 * q;
+                    if (c < M) A[(j + 1) * lda + c] = v[q];
+                }
                 if (!(d > thr)) {
                     if (lane == 0) bad[(j + 1) & 1] = 1;
                 } else {
                     const S dinv = chol_recip(d);
                     S *sn = srow[(j + 1) & 1];
-                    for (int c = j + 2 + lane; c < M; c += 32) sn[c] = A[(j + 1) * lda + c] * dinv;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = j + 1 + lane + 32 * q;
+                        if (c >= j + 2 && c < M) sn[c] = v[q] * dinv;
+                    }
                     if (lane == 0) piv[j + 1] = d;
                 }
             }
         } else {
-            // rows j+2.. of the trailing upper triangle: one warp per row, lanes along it
+            // rows j+2.. of the trailing upper triangle: rows by warp, columns by lane (c =
+            // lane + 32q); four rows' loads are issued before any of their stores
             const int nw = (blockDim.x >> 5) - 1;
-            for (int ra = j + 1 + warp; ra < M; ra += nw) {
-                const S uja = A[j * lda + ra];
-                for (int rb = ra + lane; rb < M; rb += 32) A[ra * lda + rb] -= uja * sr[rb];
+            S srv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) srv[q] = lane + 32 * q < M ? sr[lane + 32 * q] : S(0);
+            for (int ra0 = j + 1 + warp; ra0 < M; ra0 += 4 * nw) {
+                S u[4], a[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int ra = ra0 + r * nw;
+                    u[r] = ra < M ? A[j * lda + ra] : S(0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = lane + 32 * q;
+                        a[r][q] = (ra < M && c >= ra && c < M) ? A[ra * lda + c] : S(0);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int ra = ra0 + r * nw;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int c = lane + 32 * q;
+                        if (ra < M && c >= ra && c < M) A[ra * lda + c] = fma(-u[r], srv[q], a[r][q]);
+                    }
+                }
             }
         }
         __syncthreads();
@@ -523,14 +575,14 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
         for (int i = threadIdx.x >> 5; i < W; i += blockDim.x >> 5)
             for (int j = threadIdx.x & 31; j < W; j += 32) {
                 const int idx = i * W + j;
+                // one FP64 subtraction per entry (E is small: the rest is exact or FP32-level)
                 T v = T(0);
                 if (i < M && j < M && j >= i) {
-                    const double e = A[i * lda + j] - (i == j ? 1.0 : 0.0);
-                    const double phi = (i == j) ? 0.5 * e : e;
-                    v = T((i == j ? 1.0 : 0.0) - phi);
+                    const float e = float(A[i * lda + j] - (i == j ? 1.0 : 0.0));
+                    v = (i == j) ? T(1.f - 0.5f * e) : T(-e);
                 }
                 Rinv[idx] = v;
-                if (i < M && j < M) Sf[i * lda + j] = (j >= i) ? T((i == j ? 1.0 : 0.0) - double(v)) : T(0);
+                if (i < M && j < M) Sf[i * lda + j] = (j >= i) ? T((i == j ? 1.f : 0.f) - float(v)) : T(0);
             }
         __syncthreads();
         // A is free now: R1 rounded to T, and C = F R1 (both upper triangular, zeros below)
