@@ -134,14 +134,15 @@ int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
 // q->n == 0).  Non-integer s: the quadrature rule q gives the fractional factor
 // sum_k W_k (sigma_k I + H_m)^{-1} F_1, one block Cholesky factorisation and solve per node
 // (qbatch nodes at a time, one CTA each, in qscr: qbatch * bt_quad_node_doubles(M, m)
-// doubles), then s_int solves with eps I + H_m.
+// doubles), then s_int solves with eps I + H_m.  kmax: a host-side bound on ctrl->steps (the
+// factorisation is launched block by block up to it; 0 means m).
 __host__ __device__ inline size_t bt_quad_node_doubles(int M, int m) {
     return 3 * size_t(m) * M * M + size_t(m) * M;   // Ld, Ls, Y blocks and reciprocal diagonals
 }
 int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double eps, int s_int,
                      double *Ld, double *Ls, double *Yw, double *U, const Ctrl *ctrl,
                      cudaStream_t s, const QuadRule *q = nullptr, double *qscr = nullptr,
-                     int qbatch = 0);
+                     int qbatch = 0, int kmax = 0);
 
 // Graph utilities.
 int launch_gershgorin(const GraphDev &g, double *out, cudaStream_t s);

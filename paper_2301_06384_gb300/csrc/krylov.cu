@@ -397,7 +397,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                     KB_TRY(launch_cheb_bt(b.Hd, b.Hs, M, m, lam_p, d, b.V0, b.V1, b.V2, Ucur, b.ctrl_chk, c.s, b.Hdf));
                 } else {
                     KB_TRY(launch_bt_spline(b.Hd, b.Hs, M, m, c.p.eps, c.s_int, b.V0, b.V1, b.V2, Ucur,
-                                            b.ctrl_chk, c.s, c.quad, b.qscr, qbatch));
+                                            b.ctrl_chk, c.s, c.quad, b.qscr, qbatch, k));
                 }
                 KB_TRY(launch_conv_check(Ucur, Uprev, M, b.ctrl_chk, b.chk_prev, c.p.tol, b.ctrl, c.s, nchk % 2));
                 ++nchk;

@@ -189,89 +189,96 @@ k_cheb_bt_iter_df(const dfl *__restrict__ Hd, const dfl *__restrict__ Hs, const 
 // ---------------------------------------------------------------- block Cholesky (spline)
 // One CTA; all scratch in global memory (L1/L2 resident for the sizes used).
 __device__ void chol_lower_inplace(double *A, int M) {
-    // A = L L^T, lower L overwrites A (upper part left as is)
-    __shared__ double piv;
+    // A = L L^T, lower L overwrites A (upper part left as is); the trailing update runs rows
+    // by warp and columns by lane (no index division, no idle half)
+    __shared__ double piv, rpiv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = 0; j < M; ++j) {
         if (threadIdx.x == 0) {
             double d = A[j * M + j];
             piv = sqrt(fmax(d, 1e-300));
+            rpiv = 1.0 / piv;
             A[j * M + j] = piv;
         }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < M; i += blockDim.x) A[i * M + j] /= piv;
+        for (int i = j + 1 + threadIdx.x; i < M; i += blockDim.x) A[i * M + j] *= rpiv;
         __syncthreads();
-        const int L = M - j - 1;
-        for (int idx = threadIdx.x; idx < L * L; idx += blockDim.x) {
-            const int a = j + 1 + idx / L, b = j + 1 + idx % L;
-            if (b <= a) A[a * M + b] -= A[a * M + j] * A[b * M + j];
+        for (int a = j + 1 + warp; a < M; a += nw) {
+            const double laj = A[a * M + j];
+            for (int b = j + 1 + lane; b <= a; b += 32) A[a * M + b] -= laj * A[b * M + j];
         }
         __syncthreads();
     }
-}
-
-// Lane groups for the triangular solves of k_bt_spline: a group of TPC consecutive lanes
-// (a power of two dividing 32) works on one row or column, each lane taking every TPC-th term
-// of the dot product; the group's partial sums meet by shuffles.  All threads run the same
-// loop bounds (idle groups on zeros), so the full-warp shuffles are uniform.
-__device__ __forceinline__ int tpc_for(int M) {
-    int t = 1;
-    while (t < 32 && 2 * t * M <= 1024) t *= 2;
-    return t;
-}
-__device__ __forceinline__ double group_sum(double v, int tpc) {
-    for (int off = 1; off < tpc; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
 }
 
 // Block Cholesky factorisation eps I + H = L L^T of the block tridiagonal Lanczos matrix (L
-// block lower bidiagonal: lower triangular diagonal blocks Ld_r, sub-diagonal blocks Ls_r).
-// One CTA of 1024 threads.  The dense block products (the Schur complement update of each
-// diagonal block) run over all threads, one output each; the triangular solves of the
-// sub-diagonal factor rows give each row a lane group, so their dependent chains are TPC
-// times shorter than with one thread per row.
-__global__ void __launch_bounds__(1024)
-k_bt_spline_factor(const double *Hd, const double *Hs, int M, double eps, double *Ld, double *Ls,
-                   const Ctrl *ctrl) {
-    const int steps = ctrl->steps;
+// block lower bidiagonal: lower triangular diagonal blocks Ld_r, sub-diagonal blocks Ls_r),
+// block by block, three launches per block (FP64 runs at a small fraction of the FP32 rate
+// on this part, so the dense parts are spread over as many SMs as there are rows):
+//   k_bt_dupdate  D_r = eps I + H_rr - Ls_{r-1} Ls_{r-1}^T (lower triangle), one CTA per row
+//   k_bt_dchol    D_r = Ld_r Ld_r^T in place, one CTA
+//   k_bt_lsolve   Ls_r = H_{r+1,r} Ld_r^{-T}, one warp per row
+// Each launch does nothing when its block lies past ctrl->steps.
+__global__ void __launch_bounds__(128)
+k_bt_dupdate(const double *__restrict__ Hd, const double *__restrict__ Ls, int M, double eps, int r,
+             double *__restrict__ Ld, const Ctrl *ctrl) {
+    if (r >= ctrl->steps) return;
+    const int i = blockIdx.x;
     const int64_t MM = int64_t(M) * M;
-    const int tpc = tpc_for(M);
-    const int grp = threadIdx.x / tpc, sub = threadIdx.x % tpc;
-    const bool gact = grp < M;                 // this lane group has a row / column
-    __shared__ double rd[128];                 // reciprocal diagonal of the current D block
-    // factor eps I + H = L L^T, L block lower bidiagonal (Ld diagonal, Ls sub-diagonal blocks)
-    for (int r = 0; r < steps; ++r) {
-        double *D = Ld + r * MM;
-        for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-            const int i = idx / M, j = idx % M;
-            double v = Hd[r * MM + idx] + (i == j ? eps : 0.0);
-            if (r > 0 && j <= i) {
-                const double *P = Ls + (r - 1) * MM;
-                for (int k = 0; k < M; ++k) v = fma(-P[i * M + k], P[j * M + k], v);
-            }
-            D[idx] = v;
-        }
-        __syncthreads();
-        chol_lower_inplace(D, M);
-        if (r + 1 < steps) {
-            // Ls_r = H_{r+1,r} D^{-T}: row i solves D x = H_{r+1,r}[i,:]^T (lane group per row)
-            for (int i = threadIdx.x; i < M; i += blockDim.x) rd[i] = 1.0 / D[i * M + i];
-            __syncthreads();
-            const double *Hsub = Hs + r * MM;
-            double *P = Ls + r * MM;
-            for (int j = 0; j < M; ++j) {
-                double part = 0.0;
-                if (gact)
-                    for (int k = sub; k < j; k += tpc) part = fma(D[j * M + k], P[grp * M + k], part);
-                part = group_sum(part, tpc);
-                if (gact && sub == 0) P[grp * M + j] = (Hsub[grp * M + j] - part) * rd[j];
-                __syncwarp();
-            }
-        }
-        __syncthreads();
+    const double *P = r > 0 ? Ls + (r - 1) * MM : nullptr;
+    double *D = Ld + r * MM;
+    for (int j = threadIdx.x; j <= i; j += blockDim.x) {
+        double v = Hd[r * MM + int64_t(i) * M + j] + (i == j ? eps : 0.0);
+        if (P)
+            for (int k = 0; k < M; ++k) v = fma(-P[int64_t(i) * M + k], P[int64_t(j) * M + k], v);
+        D[int64_t(i) * M + j] = v;
     }
 }
 
-// s_int times U <- (eps I + H)^{-1} U with the factors of k_bt_spline_factor, by forward and
+__global__ void __launch_bounds__(1024) k_bt_dchol(double *Ld, int M, int r, const Ctrl *ctrl) {
+    if (r >= ctrl->steps) return;
+    chol_lower_inplace(Ld + r * int64_t(M) * M, M);
+}
+
+// Row i of Ls_r solves Ld_r x = (row i of H_{r+1,r})^T by column-oriented forward substitution
+// with x in registers (lane l: entries l, l + 32, l + 64, l + 96; M <= 128): x_j = y_j / d_jj,
+// then y_k -= d_kj x_j for the rows k below, one shuffle per row.
+__global__ void __launch_bounds__(32)
+k_bt_lsolve(const double *__restrict__ Hs, const double *__restrict__ Ld, int M, int r,
+            double *__restrict__ Ls, const Ctrl *ctrl) {
+    if (r + 1 >= ctrl->steps) return;
+    const int i = blockIdx.x, lane = threadIdx.x;
+    const int64_t MM = int64_t(M) * M;
+    const double *D = Ld + r * MM;
+    const double *h = Hs + r * MM + int64_t(i) * M;
+    double y[4], rd[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = lane + 32 * q;
+        y[q] = j < M ? h[j] : 0.0;
+        rd[q] = 1.0 / (j < M ? D[int64_t(j) * M + j] : 1.0);
+    }
+#pragma unroll
+    for (int jq = 0; jq < 4; ++jq)
+        for (int jl = 0; jl < 32; ++jl) {
+            const int j = 32 * jq + jl;
+            if (j >= M) break;
+            const double xj = __shfl_sync(0xffffffffu, y[jq], jl) * __shfl_sync(0xffffffffu, rd[jq], jl);
+            if (lane == jl) y[jq] = xj;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = lane + 32 * q;
+                if (k > j && k < M) y[q] = fma(-D[int64_t(k) * M + j], xj, y[q]);
+            }
+        }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = lane + 32 * q;
+        if (j < M) Ls[r * MM + int64_t(i) * M + j] = y[q];
+    }
+}
+
+// s_int times U <- (eps I + H)^{-1} U with the factors Ld, Ls (k_bt_dupdate / dchol / lsolve), by forward and
 // backward block substitution; U starts as F_1 = [I; 0; ...] unless rhs_in_u (U already holds
 // the right-hand side, steps blocks).  The right-hand-side columns are independent: one warp
 // per column, BTS_COLS columns per CTA, the CTAs side by side (FP64 runs at a small fraction
@@ -549,11 +556,23 @@ int launch_cheb_bt(const double *Hd, const double *Hs, int M, int m, double lam,
     return 0;
 }
 
+// The block factorisation, launched block by block up to kmax; returns the launch count.
+static int bt_factor(const double *Hd, const double *Hs, int M, int kmax, double eps, double *Ld,
+                     double *Ls, const Ctrl *ctrl, cudaStream_t s) {
+    for (int r = 0; r < kmax; ++r) {
+        k_bt_dupdate<<<M, 128, 0, s>>>(Hd, Ls, M, eps, r, Ld, ctrl);
+        k_bt_dchol<<<1, 1024, 0, s>>>(Ld, M, r, ctrl);
+        if (r + 1 < kmax) k_bt_lsolve<<<M, 32, 0, s>>>(Hs, Ld, M, r, Ls, ctrl);
+    }
+    return 3 * kmax - 1;
+}
+
 int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double eps, int s_int,
                      double *Ld, double *Ls, double *Yw, double *U, const Ctrl *ctrl,
-                     cudaStream_t s, const QuadRule *q, double *qscr, int qbatch) {
+                     cudaStream_t s, const QuadRule *q, double *qscr, int qbatch, int kmax) {
+    if (kmax <= 0 || kmax > m) kmax = m;
     prof_begin(KernelClass::PROJECTED, s);
-    int launches = 1;
+    int launches = 1;   // zero_if_active
     if (q && q->n > 0) {
         if (!qscr || qbatch < 1) return fail(KB_ERR_ARG, "spline quadrature without scratch");
         zero_if_active(U, int64_t(m) * M * M, ctrl, s);
@@ -565,18 +584,15 @@ int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double ep
             launches += 2;
         }
         if (s_int > 0) {
-            k_bt_spline_factor<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, Ld, Ls, ctrl);
+            launches += bt_factor(Hd, Hs, M, kmax, eps, Ld, Ls, ctrl, s) + 1;
             k_bt_spline_subst<<<(M + BTS_COLS - 1) / BTS_COLS, 32 * BTS_COLS, 0, s>>>(Ld, Ls, M, s_int, Yw, U, ctrl, 1);
-            ++launches;
-        } else {
-            --launches;
         }
     } else {
         // (blocks past the steps stay zero: the bound check reads all m of them)
         zero_if_active(U, int64_t(m) * M * M, ctrl, s);
-        k_bt_spline_factor<<<1, 1024, 0, s>>>(Hd, Hs, M, eps, Ld, Ls, ctrl);
+        launches += bt_factor(Hd, Hs, M, kmax, eps, Ld, Ls, ctrl, s);
         k_bt_spline_subst<<<(M + BTS_COLS - 1) / BTS_COLS, 32 * BTS_COLS, 0, s>>>(Ld, Ls, M, s_int, Yw, U, ctrl, 0);
-        launches += 2;
+        ++launches;
     }
     KB_CUDA_TRY(cudaGetLastError());
     prof_end(KernelClass::PROJECTED, s, 0, 0, launches);
