@@ -78,6 +78,10 @@ def parse():
     ap.add_argument("--schedule", default="lpt", choices=["lpt", "rr"],
                     help="assignment of the independent solves of a step to the streams: "
                          "longest first onto the least loaded stream, or round robin")
+    ap.add_argument("--no-priority", action="store_true",
+                    help="all solve streams at the same priority (default: the streams holding "
+                         "the costliest solves, which form the step's critical path, get the "
+                         "highest stream priority)")
     return ap.parse_args()
 
 
@@ -112,6 +116,7 @@ def workload_config(a):
             "graph_seed": a.graph_seed, "node_seed": a.node_seed, "basis": a.basis,
             "l2": "256 MiB flush write between steps; per-solve working set > L2",
             "streams": a.streams, "schedule": a.schedule,
+            "stream_priority": "uniform" if a.no_priority else "critical path first",
             "rowblock": "tcgen05 bf16x6" if a.tensor_cores else "simt fp32",
             "frontier": not a.no_frontier}
 
@@ -507,28 +512,40 @@ def main():
     tg0 = time.perf_counter()
     G = kb.Graph.from_csr(g, stream=stream)   # host validation + upload + Gershgorin bound
     graph_create_ms = (time.perf_counter() - tg0) * 1e3
-    streams = [stream] + [torch.cuda.Stream() for _ in range(max(1, a.streams) - 1)]
     solves = [(mth, t) for mth in methods for t in ts]
     Ys = [torch.empty((a.n, a.M), dtype=torch.float32, device="cuda") for _ in solves]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     params = {t: kb.make_params(basis=a.basis, no_frontier=int(a.no_frontier), reorth=a.reorth,
                                 **phi_kwargs(a, t)) for t in ts}
 
-    where, order = assign_streams(solves, len(streams), a.schedule)
+    nstreams = max(1, a.streams)
+    where, order = assign_streams(solves, nstreams, a.schedule)
+    # the streams holding the costliest solve of the step (the critical path) get the highest
+    # priority, so that their kernels are scheduled first and the cheaper solves fill the SMs
+    # around them
+    top = max(SOLVE_COST.get(m_, 1.0) for m_, _ in solves)
+    hot = {where[i] for i, (m_, _) in enumerate(solves) if SOLVE_COST.get(m_, 1.0) == top}
+    if nstreams == 1:
+        streams = [stream]
+    else:
+        streams = [torch.cuda.Stream(priority=(-5 if (j in hot and not a.no_priority) else 0))
+                   for j in range(nstreams)]
 
     def step(pr=params):
         # independent solves spread over the streams; every stream joins the main one
         ev = torch.cuda.Event()
         ev.record(stream)
-        for s2 in streams[1:]:
-            s2.wait_event(ev)
+        for s2 in streams:
+            if s2 is not stream:
+                s2.wait_event(ev)
         for i in order:
             mth, t = solves[i]
             kb.kb_krylov_apply(G, mth, a.phi, pr[t], nodes, a.M, a.m, Ys[i], stream=streams[where[i]])
-        for s2 in streams[1:]:
-            e2 = torch.cuda.Event()
-            e2.record(s2)
-            stream.wait_event(e2)
+        for s2 in streams:
+            if s2 is not stream:
+                e2 = torch.cuda.Event()
+                e2.record(s2)
+                stream.wait_event(e2)
 
     for _ in range(a.warmup):
         flush.zero_()
