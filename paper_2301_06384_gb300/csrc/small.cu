@@ -161,7 +161,11 @@ __device__ __forceinline__ double recip_newton(double d) {
 }
 
 __device__ __forceinline__ double chol_recip(double d) { return recip_newton(d); }
-__device__ __forceinline__ float chol_recip(float d) { return 1.0f / d; }
+// the correctly rounded reciprocal (the same value as 1.0f / d, without the division sequence)
+__device__ __forceinline__ float chol_recip(float d) { return __frcp_rn(d); }
+// 1 / d rounded to nearest in either precision
+__device__ __forceinline__ float recip_rn(float d) { return __frcp_rn(d); }
+__device__ __forceinline__ double recip_rn(double d) { return 1.0 / d; }
 
 // Scratch of tri_inv_upper_blocked: (P/2)^2 values, P the power of two >= M.
 __host__ __device__ inline int tri_inv_tmp_elems(int M) {
@@ -183,7 +187,7 @@ __device__ void tri_inv_upper_blocked(S *A, int lda, int M, S *tmp) {
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         const int r0 = b * 8, r1 = min(r0 + 8, M);
         for (int j = r0; j < r1; ++j) {
-            const S ajj = S(1) / A[j * lda + j];
+            const S ajj = recip_rn(A[j * lda + j]);
             for (int i = r0; i < j; ++i) {
                 S acc = S(0);
                 for (int k = i; k < j; ++k) acc = fma(A[i * lda + k], A[k * lda + j], acc);
@@ -378,7 +382,7 @@ __device__ __forceinline__ void load_square(const double *g, int ldg, int M, con
 // leave at the same step).
 template <typename S>
 __device__ bool chol_upper_inplace(S *A, int lda, int M, S piv_rel2, S maxdiag, S *t, int *bad) {
-    S *srow[2] = {t, t + M};   // u_j / d_j, double-buffered by the parity of j
+    S *const srow0 = t, *const srow1 = t + M;   // u_j / d_j, double-buffered by the parity of j
     S *piv = t + 2 * M;        // d_j
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const S thr = piv_rel2 * maxdiag;
@@ -389,14 +393,14 @@ __device__ bool chol_upper_inplace(S *A, int lda, int M, S piv_rel2, S maxdiag, 
             if (lane == 0) bad[0] = 1;
         } else {
             const S dinv = chol_recip(d);
-            for (int c = 1 + lane; c < M; c += 32) srow[0][c] = A[c] * dinv;
+            for (int c = 1 + lane; c < M; c += 32) srow0[c] = A[c] * dinv;
             if (lane == 0) piv[0] = d;
         }
     }
     __syncthreads();
     for (int j = 0; j < M; ++j) {
         if (bad[j & 1]) return false;
-        const S *sr = srow[j & 1];
+        const S *sr = (j & 1) ? srow1 : srow0;
         if (warp == 0) {
             if (j + 1 < M) {
                 // the next pivot row: A[j+1][c] -= u_{j,j+1} u_{j,c} / d_j, c >= j+1, held in
@@ -418,7 +422,7 @@ __device__ bool chol_upper_inplace(S *A, int lda, int M, S piv_rel2, S maxdiag, 
                     if (lane == 0) bad[(j + 1) & 1] = 1;
                 } else {
                     const S dinv = chol_recip(d);
-                    S *sn = srow[(j + 1) & 1];
+                    S *sn = ((j + 1) & 1) ? srow1 : srow0;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int c = j + 1 + lane + 32 * q;
@@ -462,19 +466,19 @@ __device__ bool chol_upper_inplace(S *A, int lda, int M, S piv_rel2, S maxdiag, 
     // (no pivot is examined during the last step: the flags are final here)
     if (bad[0] | bad[1]) return false;
     // R_jj = sqrt(d_j), R_jc = u_jc / sqrt(d_j)
-    S *rinv = srow[0];
+    S *rinv = srow0;
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const S r = sqrt(piv[j]);
         piv[j] = r;
-        rinv[j] = S(1) / r;
+        rinv[j] = recip_rn(r);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < M * M; idx += blockDim.x) {
-        const int i = idx / M, j = idx % M;
-        if (j < i) A[i * lda + j] = S(0);
-        else if (j == i) A[i * lda + j] = piv[i];
-        else A[i * lda + j] *= rinv[i];
-    }
+    for (int i = warp; i < M; i += blockDim.x >> 5)
+        for (int j = lane; j < M; j += 32) {
+            if (j < i) A[i * lda + j] = S(0);
+            else if (j == i) A[i * lda + j] = piv[i];
+            else A[i * lda + j] *= rinv[i];
+        }
     __syncthreads();
     return true;
 }
@@ -1508,16 +1512,19 @@ __global__ void __launch_bounds__(256) k_frontier_expand_listed(GraphDev g, uint
 
 // Stream compaction of the active 32-row tiles in tile order.  Each warp owns a contiguous
 // range of 32-entry groups and reads them coalesced, eight groups in flight; a ballot gives
-// each group's active lanes, so the warp's count and, in the second pass, each active
-// entry's position (the active lanes below it) come from population counts.  A block-wide
-// exclusive scan of the warp counts gives each warp's output offset; the second pass reads
-// the 4-byte-per-tile array again from cache.
+// each group's active lanes, kept in shared memory (up to LIST_MASKS groups, i.e. 2^18 tiles
+// of 32 rows; beyond that the second pass reads the array again).  The warp's count and, in
+// the second pass, each active entry's position (the active lanes below it) come from
+// population counts; a block-wide exclusive scan of the warp counts gives each warp's offset.
+constexpr int LIST_MASKS = 8192;
 __global__ void __launch_bounds__(1024) k_frontier_list(const int32_t *__restrict__ tgen, int64_t nact,
                                                         int limit, int32_t *__restrict__ list,
                                                         int32_t *__restrict__ count) {
     __shared__ int wsum[33];
+    __shared__ unsigned s_mask[LIST_MASKS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t ngrp = (nact + 31) / 32;
+    const bool cached = ngrp <= LIST_MASKS;
     const int64_t gper = (ngrp + nw - 1) / nw;
     const int64_t g0 = int64_t(warp) * gper;
     const int64_t g1 = g0 + gper < ngrp ? g0 + gper : ngrp;
@@ -1530,7 +1537,11 @@ __global__ void __launch_bounds__(1024) k_frontier_list(const int32_t *__restric
             v[u] = (g + u < g1 && a < nact) ? __ldg(tgen + a) : INT_MAX;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) c += __popc(__ballot_sync(0xffffffffu, v[u] <= limit));
+        for (int u = 0; u < 8; ++u) {
+            const unsigned mask = __ballot_sync(0xffffffffu, v[u] <= limit);
+            if (cached && lane == 0 && g + u < g1) s_mask[g + u] = mask;
+            c += __popc(mask);
+        }
     }
     if (lane == 0) wsum[warp] = c;
     __syncthreads();
@@ -1548,18 +1559,24 @@ __global__ void __launch_bounds__(1024) k_frontier_list(const int32_t *__restric
     int pos = wsum[warp];
     const unsigned below = (1u << lane) - 1u;
     for (int64_t g = g0; g < g1; g += 8) {
-        int32_t v[8];
+        unsigned mk[8];
+        if (cached) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int64_t a = (g + u) * 32 + lane;
-            v[u] = (g + u < g1 && a < nact) ? __ldg(tgen + a) : INT_MAX;
+            for (int u = 0; u < 8; ++u) mk[u] = g + u < g1 ? s_mask[g + u] : 0u;
+        } else {
+            int32_t v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t a = (g + u) * 32 + lane;
+                v[u] = (g + u < g1 && a < nact) ? __ldg(tgen + a) : INT_MAX;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mk[u] = __ballot_sync(0xffffffffu, v[u] <= limit);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const bool on = v[u] <= limit;
-            const unsigned mask = __ballot_sync(0xffffffffu, on);
-            if (on) list[pos + __popc(mask & below)] = int32_t((g + u) * 32 + lane);
-            pos += __popc(mask);
+            if ((mk[u] >> lane) & 1u) list[pos + __popc(mk[u] & below)] = int32_t((g + u) * 32 + lane);
+            pos += __popc(mk[u]);
         }
     }
     if (threadIdx.x == 0) *count = wsum[32];
