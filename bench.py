@@ -142,6 +142,13 @@ def assign_streams(solves, nstreams, policy):
     return where, order
 
 
+def critical_streams(solves, where):
+    """Streams holding a solve of the largest cost of the step: its critical path, given the
+    highest stream priority so that the cheaper solves fill the SMs around it."""
+    top = max(SOLVE_COST.get(m_, 1.0) for m_, _ in solves)
+    return {where[i] for i, (m_, _) in enumerate(solves) if SOLVE_COST.get(m_, 1.0) == top}
+
+
 # ----------------------------------------------------------------------------- small config
 def small_config(kb, torch):
     """CPU-baseline leg for the 32 x 32 grid (n = 1024), 16 nodes, e^{-L}, cbl m = 20: the
@@ -520,11 +527,7 @@ def main():
 
     nstreams = max(1, a.streams)
     where, order = assign_streams(solves, nstreams, a.schedule)
-    # the streams holding the costliest solve of the step (the critical path) get the highest
-    # priority, so that their kernels are scheduled first and the cheaper solves fill the SMs
-    # around them
-    top = max(SOLVE_COST.get(m_, 1.0) for m_, _ in solves)
-    hot = {where[i] for i, (m_, _) in enumerate(solves) if SOLVE_COST.get(m_, 1.0) == top}
+    hot = critical_streams(solves, where)
     if nstreams == 1:
         streams = [stream]
     else:

@@ -77,3 +77,16 @@ def test_stream_assignment_balances_the_solves():
     # one stream: everything in order on stream 0
     one, _ = bench.assign_streams(solves, 1, "lpt")
     assert one == [0] * 10
+
+
+def test_critical_path_streams_hold_the_costliest_solves():
+    import bench
+    solves = [(m, t) for m in ["cbl", "gbl", "sbl", "cheb", "cheb2"] for t in (0.5, 2.0)]
+    where, _ = bench.assign_streams(solves, 5, "lpt")
+    hot = bench.critical_streams(solves, where)
+    assert hot == {where[i] for i, (m, _) in enumerate(solves) if m == "cbl"}
+    assert len(hot) == 2
+    # no cbl in the step: the next costliest method marks the critical path
+    s2 = [("cheb", 0.5), ("gbl", 2.0), ("cheb2", 1.0)]
+    w2, _ = bench.assign_streams(s2, 3, "lpt")
+    assert bench.critical_streams(s2, w2) == {w2[1]}
