@@ -1285,19 +1285,34 @@ __global__ void k_frontier_seed(uint8_t *gen, int32_t *tgen, NodeChunk ch) {
 }
 
 // One hop: rows at distance k-1 mark their unreached neighbours with distance k.
+// Marks the unreached neighbours of one frontier row (stored nonzeros beg..end) with
+// distance k, eight at a time: their indices, then their marks, loaded before any store (a
+// mark read as unset that another thread sets meanwhile only repeats the same store).
+__device__ __forceinline__ void expand_row(const GraphDev &g, uint8_t *gen, int32_t *tgen, int k,
+                                           int beg, int end) {
+    for (int p = beg; p < end; p += 8) {
+        int jj[8];
+        uint8_t gj[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) jj[u] = p + u < end ? __ldg(g.col + p + u) : -1;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) gj[u] = jj[u] >= 0 ? gen[jj[u]] : uint8_t(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (gj[u] == 255) {
+                gen[jj[u]] = uint8_t(k);
+                atomicMin(tgen + jj[u] / ACT_ROWS, k);
+            }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_frontier_expand(GraphDev g, uint8_t *gen, int32_t *tgen, int k) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < g.n;
          i += int64_t(gridDim.x) * blockDim.x) {
         if (__ldg(tgen + i / ACT_ROWS) > k - 1) continue;
         if (gen[i] != uint8_t(k - 1)) continue;
         const int beg = __ldg(g.rowptr + i), end = __ldg(g.rowptr + i + 1);
-        for (int p = beg; p < end; ++p) {
-            const int j = __ldg(g.col + p);
-            if (gen[j] == 255) {
-                gen[j] = uint8_t(k);
-                atomicMin(tgen + j / ACT_ROWS, k);
-            }
-        }
+        expand_row(g, gen, tgen, k, beg, end);
     }
 }
 
@@ -1500,13 +1515,7 @@ __global__ void __launch_bounds__(256) k_frontier_expand_listed(GraphDev g, uint
         const int64_t i = int64_t(__ldg(alist + idx / ACT_ROWS)) * ACT_ROWS + idx % ACT_ROWS;
         if (i >= g.n || gen[i] != uint8_t(k - 1)) continue;
         const int beg = __ldg(g.rowptr + i), end = __ldg(g.rowptr + i + 1);
-        for (int p = beg; p < end; ++p) {
-            const int j = __ldg(g.col + p);
-            if (gen[j] == 255) {
-                gen[j] = uint8_t(k);
-                atomicMin(tgen + j / ACT_ROWS, k);
-            }
-        }
+        expand_row(g, gen, tgen, k, beg, end);
     }
 }
 
