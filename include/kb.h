@@ -43,7 +43,7 @@ enum {
     KB_ERR_NODES = -3,        /* node set has an out-of-range or repeated node                  */
     KB_ERR_CUDA = -4,         /* a CUDA runtime call failed (message in kb_last_error)          */
     KB_ERR_NOMEM = -5,        /* device memory exhausted                                         */
-    KB_ERR_BREAKDOWN = -6,    /* a Lanczos block became rank deficient (reading A6)              */
+    KB_ERR_BREAKDOWN = -6,    /* a Lanczos block became rank deficient (not deflated)            */
     KB_ERR_UNSUPPORTED = -7,  /* combination not implemented (see kb_krylov_apply)               */
     KB_ERR_BUSY = -8,         /* serving queue full (kb_server_submit)                           */
     KB_ERR_ORTHOGONALITY = -9,/* the projected matrix left [0, Lambda]: the Lanczos basis lost
@@ -62,8 +62,8 @@ typedef struct {
     double eps;         /* spline shift eps > 0 (KB_PHI_SPLINE)                                    */
     double s;           /* spline exponent s > 0 (KB_PHI_SPLINE)                                   */
     double lambda_max;  /* spectral bound Lambda used by KB_CHEB/KB_CHEB2; <= 0 selects the
-                           graph's Gershgorin bound max_i sum_j |L_ij| (reading A5)               */
-    int32_t reorth;     /* KB_CBL only (not in the paper; reading A10): 0 = none (Algorithm 1
+                           graph's Gershgorin bound max_i sum_j |L_ij|                            */
+    int32_t reorth;     /* KB_CBL only (not in the paper): 0 = none (Algorithm 1
                            as printed); 1 = full: each new block is orthogonalised against all
                            earlier blocks, classical Gram-Schmidt applied twice; 2 = local: a
                            second Gram-Schmidt pass against the two previous blocks, which keeps
@@ -123,8 +123,7 @@ typedef struct kb_graph kb_graph;   /* opaque; owned by the library */
  *           I - D^{-1/2} A D^{-1/2} of the graph instead: A = the off-diagonal weights w_ij,
  *           D = diag of the weighted degrees; the given diagonal is ignored; nodes without
  *           edges get a zero row; Lambda = min(Gershgorin, 2) since the spectrum lies in
- *           [0, 2].  The paper uses this Laplacian in Section 8 without defining it;
- *           reading A7).
+ *           [0, 2].  The paper uses this Laplacian in Section 8 without defining it.)
  *   stream  stream for the upload and the Lambda reduction; the call synchronises it.
  *   out     receives the handle.
  *
@@ -149,7 +148,7 @@ int kb_graph_info(const kb_graph *g, int64_t *n, int64_t *nnz_offdiag, double *l
                   int32_t *standard_unit);
 
 /* Spectral upper bounds of the graph (host values, no GPU work): gershgorin =
- * max_i sum_j |L_ij| (the Lambda of the Chebyshev methods, reading A5); projected = the bound
+ * max_i sum_j |L_ij| (the Lambda of the Chebyshev methods); projected = the bound
  * the Lanczos methods use for their projected e^{-tH} series (Algorithms 1 and 2 need
  * phi(H_m), whose spectrum lies in [0, lambda_max(L)]): for the unit-weight standard
  * Laplacian D - A the edge bound max over edges (d_i + d_j) of Anderson and Morley when
@@ -161,7 +160,7 @@ int kb_graph_lambda_bounds(const kb_graph *g, double *gershgorin, double *projec
  * kb_krylov_apply -- Y ~ phi(L) E_W by one block Krylov method.   (Section 3; Algorithms 1, 2)
  *
  *   method  kb_method.  phi: kb_phi with parameters in *params.
- *   nodes   host, M distinct node indices in [0, n) (0-based; reading A11).
+ *   nodes   host, M distinct node indices in [0, n) (0-based).
  *   M       block width N of the paper, 1 <= M <= 128 for KB_CBL and KB_GBL; any M >= 1
  *           for KB_SBL, KB_CHEB, KB_CHEB2 (columns are independent and processed in
  *           groups of at most 128).
@@ -262,7 +261,7 @@ int kb_version(void);
 /* Coefficients c_0..c_m of the degree-m Chebyshev-Lobatto interpolant of phi (or of
  * sqrt(phi) when sqrt_phi != 0) on [0, lam], Eq. (chebcoeff) read as
  * c_k = (2/m) sum''_{j=0..m} phi(lam/2 (1 - cos(pi j/m))) cos(pi j k/m) (endpoint terms
- * halved, reading A3); the interpolant is sum''_k c_k T_k(1 - 2 lambda/lam) with c_0 and
+ * halved); the interpolant is sum''_k c_k T_k(1 - 2 lambda/lam) with c_0 and
  * c_m halved.  c: host array of m+1 doubles.  Errors: KB_ERR_ARG. */
 int kb_cheb_lobatto_coeffs(kb_phi phi, const kb_params *params, int32_t m, double lam,
                            int32_t sqrt_phi, double *c);

@@ -4,7 +4,7 @@ Theorem 4.2: for the three Lanczos methods the error of the degree-p approximant
 most 2 sqrt(N) E_p(phi); for the Chebyshev interpolant of degree m it is at most
 sqrt(N) (2 + (2/pi) log(m+1)) E_m(phi).  Example 4.5, Eq. (boundapproximation), bounds
 E_m(e^{-t lambda}) on [0, Lambda] explicitly (constants b and d as printed there; the
-foci typo {0, Gamma} in Example 4.4 is read as {0, Lambda}, reading A12).
+foci typo {0, Gamma} in Example 4.4 is read as {0, Lambda}).
 """
 from __future__ import annotations
 

@@ -53,7 +53,7 @@ def laplacian_dense(n: int, rowptr, col, val) -> np.ndarray:
 def normalized_laplacian_dense(L: np.ndarray) -> np.ndarray:
     """I - D^{-1/2} A D^{-1/2} from a dense Laplacian (A = minus its off-diagonal part,
     D = weighted degrees; rows without edges stay zero).  The paper uses this Laplacian in
-    Section 8 without a definition (reading A7); its spectrum lies in [0, 2]."""
+    Section 8 without a definition (read as the symmetric normalized Laplacian); its spectrum lies in [0, 2]."""
     A = -(L - np.diag(np.diag(L)))
     d = A.sum(axis=1)
     s = np.where(d > 0, 1.0 / np.sqrt(np.where(d > 0, d, 1.0)), 0.0)

@@ -22,7 +22,8 @@ from .dense import unit_block
 
 
 class Breakdown(RuntimeError):
-    """A block of the Lanczos process became rank deficient (reading A6)."""
+    """A block of the Lanczos process became rank deficient.  The paper assumes full rank; a
+    rank-deficient block is reported, not deflated."""
 
 
 @dataclass
@@ -41,8 +42,8 @@ def laplacian(n: int, rowptr, col, val) -> sp.csr_matrix:
 
 
 def gershgorin_bound(L: sp.csr_matrix) -> float:
-    """Lambda = max_i sum_j |L_ij|, an upper bound of the spectrum (reading A5 of the
-    'assumed' Lambda of Section 2.1; equals 2 max degree for D - A)."""
+    """Lambda = max_i sum_j |L_ij|, an upper bound of the spectrum (Section 2.1 assumes a
+    known bound Lambda; the Gershgorin bound is taken; it equals 2 max degree for D - A)."""
     return float(np.max(np.asarray(abs(L).sum(axis=1)).ravel()))
 
 
@@ -55,7 +56,7 @@ def matrix_function_sym(H: np.ndarray, f, F: np.ndarray) -> np.ndarray:
 
 
 def _three_term(L, Qk, Qprev, Hprev_k):
-    """Algorithm 1, three-term product: X = L Q_k - Q_{k-1} H_{k-1,k}, H_{k-1,k} = H_{k,k-1}^T (A1)."""
+    """Algorithm 1, three-term product: X = L Q_k - Q_{k-1} H_{k-1,k}, H_{k-1,k} = H_{k,k-1}^T (the symmetric block tridiagonal form)."""
     return L @ Qk - Qprev @ Hprev_k
 
 
@@ -70,7 +71,7 @@ def _subtract(X, Qk, Hkk):
 
 
 def _reorthogonalise(X, Q):
-    """Full reorthogonalisation (not in the paper; reading A10): classical Gram-Schmidt of
+    """Full reorthogonalisation (not in the paper): classical Gram-Schmidt of
     X against every stored block Q_1..Q_k, X = X - [Q_1..Q_k]([Q_1..Q_k]^T X), applied twice
     (one pass leaves a component of relative size u * ||X_in|| / ||X_out|| along the basis
     when X is nearly inside its span; the second pass removes it)."""
@@ -82,7 +83,7 @@ def _reorthogonalise(X, Q):
 
 def _reduced_qr(X):
     """Algorithm 1, reduced QR: X = Q_{k+1} H_{k+1,k}, H_{k+1,k} upper triangular.  The
-    factor is fixed to a non-negative diagonal (the QR is unique only up to signs; A8)."""
+    factor is fixed to a non-negative diagonal (the QR is unique only up to signs)."""
     Q, R = np.linalg.qr(X, mode="reduced")
     sgn = np.where(np.diag(R) < 0, -1.0, 1.0)
     return Q * sgn[None, :], R * sgn[:, None]
@@ -95,11 +96,11 @@ def cbl(L: sp.csr_matrix, nodes, m: int, f, reorth: bool = False,
 
     Q_1 = E_W; for k = 1..m: X = L Q_k - Q_{k-1} H_{k,k-1}^T; H_kk = Q_k^T X;
     X -= Q_k H_kk; (k < m) X = Q_{k+1} H_{k+1,k}.  Then U = phi(H_m) F_1 and
-    Y = [Q_1..Q_m] U.  The QR at k = m is skipped because Q_{m+1} is unused (A9).
+    Y = [Q_1..Q_m] U.  The QR at k = m is skipped because Q_{m+1} is unused.
 
-    ``reorth`` (not in the paper; reading A10): True or "full" subtracts Q_{1:k}(Q_{1:k}^T X)
+    ``reorth`` (not in the paper): True or "full" subtracts Q_{1:k}(Q_{1:k}^T X)
     twice, right after the diagonal block is subtracted; "local" subtracts Q_k(Q_k^T X) + Q_{k-1}(Q_{k-1}^T X) once more
-    (a second Gram-Schmidt pass against the two blocks of the three-term recurrence).  Breakdown (A6): if X vanishes (||X||_F <= tol * Lambda * sqrt(N)) the block
+    (a second Gram-Schmidt pass against the two blocks of the three-term recurrence).  Breakdown: if X vanishes (||X||_F <= tol * Lambda * sqrt(N)) the block
     Krylov space is invariant, the process stops and H of the reached size is used (the
     result is then exact); a rank-deficient but non-zero X raises Breakdown.
     """
@@ -154,7 +155,7 @@ def gbl(L: sp.csr_matrix, nodes, m: int, f, tol: float = 1e-12) -> KrylovResult:
     Q_1 = E_W / sqrt(N); X = L Q_k - h_{k-1,k} Q_{k-1}; h_kk = tr(Q_k^T X);
     X -= h_kk Q_k; h_{k+1,k} = ||X||_F; Q_{k+1} = X / h_{k+1,k}.
     u = sqrt(N) phi(H_m) f_1 and Y = sum_k u_k Q_k.  A vanishing X stops the process
-    (invariant space; A6)."""
+    (invariant space)."""
     n = L.shape[0]
     E = unit_block(n, nodes)
     N = E.shape[1]
@@ -191,7 +192,7 @@ def gbl(L: sp.csr_matrix, nodes, m: int, f, tol: float = 1e-12) -> KrylovResult:
 def sbl(L: sp.csr_matrix, nodes, m: int, f, tol: float = 1e-12) -> KrylovResult:
     """Sequential Lanczos (Section 3.3): an ordinary Lanczos run (Algorithm 1 or 2 with
     N = 1) on each column e_{w_i}; column i of the result is
-    [q_1..q_m] phi(H_m^{(w_i)}) f_1 (the printed formula omits phi; reading A2).  H is the
+    [q_1..q_m] phi(H_m^{(w_i)}) f_1 (the printed formula omits phi; it is applied here).  H is the
     block diagonal diag(H^{(w_1)}, ..., H^{(w_N)})."""
     nodes = np.asarray(nodes)
     cols, Hs = [], []
@@ -211,7 +212,7 @@ def lobatto_nodes(m: int, Lam: float) -> np.ndarray:
 
 
 def cheb_coefficients(f, m: int, Lam: float) -> np.ndarray:
-    """c_k(phi), k = 0..m, Eq. (chebcoeff) read as Lobatto interpolation (A3):
+    """c_k(phi), k = 0..m, Eq. (chebcoeff) read as interpolation at the Chebyshev-Lobatto points:
     c_k = (2/m) sum_{j=0..m}'' phi(lambda_j) cos(pi j k / m), the sum halving the j = 0
     and j = m terms (equivalently the printed endpoint term with a minus sign)."""
     if m < 1:
@@ -226,7 +227,7 @@ def cheb_coefficients(f, m: int, Lam: float) -> np.ndarray:
 
 
 def cheb_series_weights(m: int) -> np.ndarray:
-    """Weights of Eq. (apprchebyshevseries) under A3: c_0 and c_m enter halved."""
+    """Weights of Eq. (apprchebyshevseries) under the Lobatto reading: c_0 and c_m enter halved."""
     w = np.ones(m + 1)
     w[0] = w[m] = 0.5
     return w
@@ -243,7 +244,7 @@ def cheb_eval_scalar(c: np.ndarray, Lam: float, lam) -> np.ndarray:
 
 def cheb_apply(L: sp.csr_matrix, B: np.ndarray, c: np.ndarray, Lam: float) -> np.ndarray:
     """sum_k'' c_k T_k(I - 2L/Lambda) B by the three-term recurrence
-    T_{k+1} = 2 A T_k - T_{k-1}, T_0 = B, T_1 = A B (A4), A = I - (2/Lambda) L."""
+    T_{k+1} = 2 A T_k - T_{k-1}, T_0 = B, T_1 = A B (the recurrence applied to the block), A = I - (2/Lambda) L."""
     m = c.size - 1
     w = cheb_series_weights(m) * c
     A = lambda X: X - (2.0 / Lam) * (L @ X)

@@ -83,8 +83,8 @@ extern "C" int kb_cheb_apply_fixed_scratch(kb_graph *g, kb_phi phi, const kb_par
     for (int i = 0; i < 3; ++i) bufs[i] = reinterpret_cast<float *>(static_cast<char *>(base) + i * blk);
     int32_t *marker = reinterpret_cast<int32_t *>(static_cast<char *>(base) + 3 * blk);
 
-    // Lobatto interpolation coefficients of phi on [0, Lambda] (Eq. (chebcoeff), reading
-    // A3), computed by the routine KB_CHEB uses, into fixed host arrays; the series weights
+    // Lobatto interpolation coefficients of phi on [0, Lambda] (Eq. (chebcoeff)), computed by
+    // the routine KB_CHEB uses, into fixed host arrays; the series weights
     // halve c_0 and c_m.
     const double lam = params->lambda_max > 0 ? params->lambda_max : g->lambda;
     double f[MAX_M_STEPS + 1], w[MAX_M_STEPS + 1];

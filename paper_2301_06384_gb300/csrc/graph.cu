@@ -4,7 +4,7 @@
 //
 // Section 2.1, Eq. (generalizedLaplacian): L symmetric, L_ij < 0 exactly on edges,
 // L_ij = 0 off the graph, any diagonal.  Lambda is the Gershgorin bound
-// max_i sum_j |L_ij| of the "assumed" spectral bound (reading A5).
+// max_i sum_j |L_ij| (Section 2.1 assumes a known spectral bound; this one is computable).
 #include "kb_internal.cuh"
 #include "kb_kernels.cuh"
 
@@ -201,7 +201,7 @@ extern "C" int kb_graph_create(int64_t n, const int32_t *rowptr, const int32_t *
                 }
             }
         }
-        // normalized Laplacian I - D^{-1/2} A D^{-1/2} (reading A7): weighted degrees first
+        // normalized Laplacian I - D^{-1/2} A D^{-1/2} (the one Section 8 uses): weighted degrees first
         const bool normalized = (flags & KB_GRAPH_NORMALIZED) != 0;
         std::vector<double> deg(normalized ? n : 0, 0.0);
         if (normalized) {

@@ -66,7 +66,7 @@ static double phi_value(kb_phi phi, const kb_params &p, double lam, bool sqrt_ph
     return std::pow(p.eps + lam, -(sqrt_phi ? 0.5 * p.s : p.s));
 }
 
-// Eq. (chebcoeff) read as Lobatto interpolation (reading A3):
+// Eq. (chebcoeff) read as interpolation at the Chebyshev-Lobatto points:
 //   c_k = (2/m) sum_{j=0..m}'' f(lambda_j) cos(pi j k / m),  lambda_j = lam/2 (1 - cos(pi j/m)),
 // the double prime halving the j = 0 and j = m terms.  The series sum_k'' c_k T_k (c_0 and
 // c_m halved) interpolates f on the grid.
@@ -320,7 +320,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             KB_TRY(launch_rowblock<T>(RB_PROJ, W, pa, c.s, &grid, M));
             KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
             KB_TRY(launch_hkk<C>(b.Gsum, M, W, b.Hd + size_t(k - 1) * M * M, Cb, b.ctrl, c.s));
-            if (k == m) break;   // Q_{m+1} is never used (reading A9)
+            if (k == m) break;   // Q_{m+1} is never used
             // three-term update: X = L Q_k - Q_{k-1} H_{k-1,k} - Q_k H_kk, then Gram X^T X
             T *X = blk(k);
             RowArgs<T> ua;
@@ -330,7 +330,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
             KB_TRY(launch_rowblock<T>(RB_UPD, W, ua, c.s, &grid, M));
             KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
             if (c.p.reorth == 2) {
-                // local reorthogonalisation (not in the paper, reading A10): a second
+                // local reorthogonalisation (not in the paper): a second
                 // classical Gram-Schmidt pass against Q_k and Q_{k-1},
                 // X -= Q_k (Q_k^T X) + Q_{k-1} (Q_{k-1}^T X); it keeps the three-term
                 // orthogonality that FP32 rounding erodes when Ritz values converge
@@ -351,7 +351,7 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                 KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
             }
             if (c.p.reorth == 1) {
-                // full reorthogonalisation (not in the paper, reading A10): classical
+                // full reorthogonalisation (not in the paper): classical
                 // Gram-Schmidt against all stored blocks, X -= Q_{1:k} (Q_{1:k}^T X), twice;
                 // the second subtraction also forms the Gram X^T X for the QR
                 for (int pass = 0; pass < 2; ++pass) {
@@ -682,7 +682,7 @@ int cheb_pass(Common &c, const std::vector<double> &coef, double lam, int W, int
               const int32_t *marker, const int32_t *nodes, int Mc, const T *Zsrc, T *bufs[3],
               T *out, float *yout, int64_t ldo, int mo, int64_t M_alg, uint8_t *gen,
               int32_t *tgen, int hop0, int32_t *alist, int32_t *acount) {
-    // weights of sum_k'' c_k T_k (reading A3)
+    // weights of sum_k'' c_k T_k (Lobatto interpolation: c_0 and c_m halved)
     const int h = int(coef.size()) - 1;
     std::vector<double> w(coef);
     w[0] *= 0.5;

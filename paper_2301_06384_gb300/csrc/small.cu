@@ -1,15 +1,16 @@
 // Small dense FP64 kernels and element-wise kernels of the Krylov drivers.
 //
 //  * k_hkk          symmetrised diagonal block H_kk (Algorithm 1).
-//  * k_chol         reduced QR of the new block by CholeskyQR, FP64 Cholesky factor and its
-//                   inverse (the reduced QR of Algorithm 1); the second pass forms H_{k+1,k} = R2 R1
+//  * k_chol         reduced QR of the new block by CholeskyQR (the reduced QR of Algorithm 1):
+//                   Cholesky factor (FP32 first, FP64 fallback), its inverse and the FP64
+//                   factor consistent with the applied inverse; the second pass forms H_{k+1,k} = R2 R1
 //                   and the transposed block used by the next three-term step (Algorithm 1,
-//                   reading A1).  Invariant subspaces stop the process, rank-deficient
-//                   blocks report a breakdown (reading A6).
+//                   with H_{k-1,k} = H_{k,k-1}^T).  Invariant subspaces stop the process,
+//                   rank-deficient blocks report a breakdown (the paper assumes full rank).
 //  * k_lanczos_*    scalar recurrences of the global (Algorithm 2) and sequential
 //                   (Section 3.3) Lanczos methods: h_kk, h_{k+1,k}, 1/h.
 //  * k_tridiag_phi  u = phi(H_m) f_1 for the tridiagonal Lanczos matrices (the projected
-//                   step of Algorithm 2; Section 3.3 with phi applied, reading A2).
+//                   step of Algorithm 2; Section 3.3 with phi applied, which its formula omits).
 //  * element-wise   unit blocks E_W, node markers, column norms, scaled copies, the
 //                   diagonal assembly sum_k u_k Q_k, NaN fill on breakdown.
 #include <climits>

@@ -426,7 +426,7 @@ def test_local_reorth_is_a_no_op_in_exact_arithmetic():
 
 
 # ----------------------------------------------------------------------------- full reorthogonalisation
-# reorth=True is not in the paper (reading A10): X -= Q_{1:k}(Q_{1:k}^T X), twice.  It is
+# reorth=True is not in the paper: X -= Q_{1:k}(Q_{1:k}^T X), twice.  It is
 # pinned by what it must achieve: it changes nothing in exact arithmetic (the Lanczos blocks
 # are orthonormal, Theorem 3.1's setting), its output is the orthogonal projection of X onto
 # the complement of the basis (orthogonal to the basis, and differing from X by an element of
