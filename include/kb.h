@@ -65,7 +65,9 @@ typedef struct {
                            graph's Gershgorin bound max_i sum_j |L_ij|                            */
     int32_t reorth;     /* KB_CBL only (not in the paper): 0 = none (Algorithm 1
                            as printed); 1 = full: each new block is orthogonalised against all
-                           earlier blocks, classical Gram-Schmidt applied twice; 2 = local: a
+                           earlier blocks by classical Gram-Schmidt, a second pass only when the
+                           first removed more than half of some column's squared norm (Kahan's
+                           "twice is enough"); 2 = local: a
                            second Gram-Schmidt pass against the two previous blocks, which keeps
                            the FP32 process on the FP64 one where Ritz values converge fast     */
     int32_t basis;      /* kb_dtype of the stored Krylov blocks: KB_F32 (FP32 arithmetic),

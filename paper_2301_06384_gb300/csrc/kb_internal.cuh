@@ -239,6 +239,7 @@ struct RowArgs {
     const int32_t *acount = nullptr;  // row of its output)
     int kbase = 0;                    // ASM: index of the first block (frontier reach)
     int accumulate = 0;               // ASM: y += product (the accumulator starts from y)
+    const int32_t *skip = nullptr;    // the launch does nothing when *skip != 0 (device flag)
     ProfCount prof;
 };
 template <typename T>
@@ -263,9 +264,9 @@ void lobatto_coeffs_into(kb_phi phi, const kb_params &p, int m, double lam, bool
 int validate_phi(kb_phi phi, const kb_params &p);
 
 // Deterministic FP64 reduction of [nparts][len] partials into out[len]; when out_p is set
-// the sums are also written there rounded to P.
+// the sums are also written there rounded to P.  Nothing is done when *skip != 0.
 template <typename P>
 int launch_reduce(const P *parts, int nparts, int len, double *out, cudaStream_t s,
-                  const Ctrl *ctrl, P *out_p = nullptr);
+                  const Ctrl *ctrl, P *out_p = nullptr, const int32_t *skip = nullptr);
 
 }  // namespace kb

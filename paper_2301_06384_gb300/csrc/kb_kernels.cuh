@@ -144,6 +144,12 @@ int launch_bt_spline(const double *Hd, const double *Hs, int M, int m, double ep
                      cudaStream_t s, const QuadRule *q = nullptr, double *qscr = nullptr,
                      int qbatch = 0, int kmax = 0);
 
+// Full reorthogonalisation: save the diagonal of the Gram of X before the first pass; after
+// it, *skip = 1 when every column kept at least half of its squared norm (the second pass is
+// then not needed).
+int launch_reorth_save(const double *G, int M, int W, double *d0, cudaStream_t s);
+int launch_reorth_decide(const double *G, const double *d0, int M, int W, int32_t *skip, cudaStream_t s);
+
 // Graph utilities.
 int launch_gershgorin(const GraphDev &g, double *out, cudaStream_t s);
 

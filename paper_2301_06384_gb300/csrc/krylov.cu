@@ -202,6 +202,8 @@ struct CblBufs {
     double *qscr;        // projected step with non-integer s: per-node block solves
     double *Hdf;         // projected e^{-tH} F_1 in double-float: H split into float pairs
     int32_t *chk_prev;   // steps of the previous check (0: none yet)
+    double *reo_d0;      // full reorthogonalisation: squared column norms before the first pass
+    int32_t *reo_skip;   // ... and the flag that skips the second pass
     Ctrl *ctrl, *ctrl2, *ctrl_chk;
     uint8_t *gen;
     int32_t *tgen;
@@ -234,6 +236,8 @@ void plan_cbl(Arena &ar, CblBufs<T> &b, int64_t n, int M, int W, int m, int rb_g
     b.qscr = qbatch > 0 ? ar.take<double>(size_t(qbatch) * bt_quad_node_doubles(M, m)) : nullptr;
     b.Hdf = sizeof(typename Cmp<T>::type) == 4 ? ar.take<double>(size_t(2) * m * M * M) : nullptr;
     b.chk_prev = ar.take<int32_t>(1);
+    b.reo_d0 = ar.take<double>(size_t(W));
+    b.reo_skip = ar.take<int32_t>(1);
     b.ctrl = ar.take<Ctrl>(1);
     b.ctrl2 = ar.take<Ctrl>(1);
     b.ctrl_chk = ar.take<Ctrl>(1);
@@ -351,25 +355,30 @@ int run_cbl(Common &c, const int32_t *nodes, int M, int m, float *Y, int64_t ldy
                 KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
             }
             if (c.p.reorth == 1) {
-                // full reorthogonalisation (not in the paper): classical
-                // Gram-Schmidt against all stored blocks, X -= Q_{1:k} (Q_{1:k}^T X), twice;
-                // the second subtraction also forms the Gram X^T X for the QR
+                // full reorthogonalisation (not in the paper): classical Gram-Schmidt against all
+                // stored blocks, X -= Q_{1:k} (Q_{1:k}^T X); the second pass runs only when the
+                // first removed more than half of some column's squared norm (Kahan's "twice
+                // is enough"; the device decides, the host launches both passes); the last
+                // subtraction that runs also forms the Gram X^T X for the QR
+                KB_TRY(launch_reorth_save(b.Gsum, M, W, b.reo_d0, c.s));
                 for (int pass = 0; pass < 2; ++pass) {
+                    const int32_t *skip = pass == 1 ? b.reo_skip : nullptr;
                     for (int j = 0; j < k; ++j) {
                         RowArgs<T> ra;
                         ra.n = n; ra.x = X; ra.qa = b.basis + j * bs; ra.partials = b.parts;
-                        ra.ctrl = b.ctrl;
+                        ra.ctrl = b.ctrl; ra.skip = skip;
                         ra.tgen = tg; ra.limit = k; ra.alist = tg ? b.alist : nullptr; ra.acount = b.acount;
                         KB_TRY(launch_rowblock<T>(RB_PROJ, W, ra, c.s, &grid, M));
                         KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl,
-                                                b.Cstk + size_t(j) * W * W));
+                                                b.Cstk + size_t(j) * W * W, skip));
                     }
                     RowArgs<T> sa;
                     sa.n = n; sa.x = X; sa.basis = b.basis; sa.block_stride = bs; sa.nblk = k;
-                    sa.ca = b.Cstk; sa.out = X; sa.partials = b.parts; sa.ctrl = b.ctrl;
+                    sa.ca = b.Cstk; sa.out = X; sa.partials = b.parts; sa.ctrl = b.ctrl; sa.skip = skip;
                     sa.tgen = tg; sa.limit = k; sa.alist = tg ? b.alist : nullptr; sa.acount = b.acount;
                     KB_TRY(launch_rowblock<T>(RB_ASMSUB, W, sa, c.s, &grid, M));
-                    KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl));
+                    KB_TRY(launch_reduce<C>(b.parts, grid, W * W, b.Gsum, c.s, b.ctrl, nullptr, skip));
+                    if (pass == 0) KB_TRY(launch_reorth_decide(b.Gsum, b.reo_d0, M, W, b.reo_skip, c.s));
                 }
             }
             // reduced QR: X = Q_{k+1} H_{k+1,k} by CholeskyQR2

@@ -100,6 +100,7 @@ k_rowblock(RowArgs<T> a) {
     using C = typename Cmp<T>::type;   // arithmetic / shared-memory type
     constexpr bool TWO = sizeof(C) == 4;
     if (MODE != RB_ASM && a.ctrl && a.ctrl->stop) return;
+    if (a.skip && *a.skip) return;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sA = reinterpret_cast<C *>(smem_raw);                      // [KC][LDA]
@@ -406,10 +407,10 @@ int max_grid_w() {
 template <typename P>
 __global__ void __launch_bounds__(1024) k_reduce(const P *__restrict__ parts, int nparts, int len,
                                                   double *__restrict__ out, const Ctrl *ctrl,
-                                                  P *__restrict__ out_p) {
+                                                  P *__restrict__ out_p, const int32_t *skip) {
     // 32 columns per CTA, 32 warps over the partials (two loads in flight per lane), then a
     // fixed-order combination of the warps' sums by warp 0
-    if (ctrl && ctrl->stop) return;
+    if ((ctrl && ctrl->stop) || (skip && *skip)) return;
     __shared__ double s[32][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int e = blockIdx.x * 32 + lane;
@@ -471,7 +472,9 @@ int launch_rowblock(int mode, int W, const RowArgs<T> &a, cudaStream_t s, int *g
     aa.prof = prof_begin(cls, s);
     int rc = 0;
     bool tc = false;
-    if constexpr (std::is_same<T, float>::value) tc = rowblock_tc_supported(mode, W) && rowblock_tc_enabled();
+    // (launches under a device skip flag take the SIMT kernels, which read the flag)
+    if constexpr (std::is_same<T, float>::value)
+        tc = !a.skip && rowblock_tc_supported(mode, W) && rowblock_tc_enabled();
     if (tc) {
         // FP32 blocks of width 64: tensor-core kernel (rowblock_tc.cu)
         if constexpr (std::is_same<T, float>::value)
@@ -531,9 +534,9 @@ int rowblock_max_grid(int W) {
 
 template <typename P>
 int launch_reduce(const P *parts, int nparts, int len, double *out, cudaStream_t s,
-                  const Ctrl *ctrl, P *out_p) {
+                  const Ctrl *ctrl, P *out_p, const int32_t *skip) {
     prof_begin(KernelClass::REDUCE, s);
-    k_reduce<P><<<(len + 31) / 32, 1024, 0, s>>>(parts, nparts, len, out, ctrl, out_p);
+    k_reduce<P><<<(len + 31) / 32, 1024, 0, s>>>(parts, nparts, len, out, ctrl, out_p, skip);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "k_reduce launch");
     prof_end(KernelClass::REDUCE, s, double(nparts) * len * sizeof(P), 0);
@@ -546,7 +549,9 @@ template int rowblock_max_grid<float>(int);
 template int rowblock_max_grid<double>(int);
 template int launch_rowblock<__nv_bfloat16>(int, int, const RowArgs<__nv_bfloat16> &, cudaStream_t, int *, int64_t);
 template int rowblock_max_grid<__nv_bfloat16>(int);
-template int launch_reduce<float>(const float *, int, int, double *, cudaStream_t, const Ctrl *, float *);
-template int launch_reduce<double>(const double *, int, int, double *, cudaStream_t, const Ctrl *, double *);
+template int launch_reduce<float>(const float *, int, int, double *, cudaStream_t, const Ctrl *, float *,
+                                  const int32_t *);
+template int launch_reduce<double>(const double *, int, int, double *, cudaStream_t, const Ctrl *, double *,
+                                   const int32_t *);
 
 }  // namespace kb

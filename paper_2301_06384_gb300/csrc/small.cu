@@ -777,6 +777,36 @@ __global__ void __launch_bounds__(256) k_chol(const double *G, int M, int W, int
     }
 }
 
+// ---------------------------------------------------------------- full reorthogonalisation
+// "Twice is enough" (Kahan's criterion, as given in Parlett's The Symmetric Eigenvalue
+// Problem): after one classical Gram-Schmidt pass x_1 = x_0 - Q Q^T x_0, x_1 is orthogonal to
+// Q to working precision when ||x_1|| >= ||x_0|| / sqrt(2); otherwise a second pass is
+// needed.  Applied column by column to the block: the squared column norms of X before the
+// first pass (the diagonal of its Gram) are saved, and after the pass the second one is
+// skipped (*skip = 1) when every column kept at least half of its squared norm.
+__global__ void k_reorth_save(const double *G, int M, int W, double *d0) {
+    for (int i = threadIdx.x; i < M; i += blockDim.x) d0[i] = G[int64_t(i) * W + i];
+}
+__global__ void k_reorth_decide(const double *G, const double *d0, int M, int W, int32_t *skip) {
+    bool ok = true;
+    for (int i = threadIdx.x; i < M; i += 32) ok = ok && G[int64_t(i) * W + i] >= 0.5 * d0[i];
+    ok = __all_sync(0xffffffffu, ok);
+    if (threadIdx.x == 0) *skip = ok ? 1 : 0;
+}
+
+int launch_reorth_save(const double *G, int M, int W, double *d0, cudaStream_t s) {
+    k_reorth_save<<<1, 128, 0, s>>>(G, M, W, d0);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+int launch_reorth_decide(const double *G, const double *d0, int M, int W, int32_t *skip, cudaStream_t s) {
+    k_reorth_decide<<<1, 32, 0, s>>>(G, d0, M, W, skip);
+    count_launches(1);
+    KB_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
 // ---------------------------------------------------------------- gbl / sbl scalars
 // Reduce [nparts][W] partials per column (fixed order) into s[W].  df: the partials are
 // double-float pairs (FP32 arithmetic), combined on the FP32 pipe; else doubles.
